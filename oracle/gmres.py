@@ -1,0 +1,134 @@
+"""Restarted, right-preconditioned GMRES in complex128.
+
+Eq. 7 right-preconditions the system: H P^-1 z = f with u = P^-1 z. GMRES
+(Saad and Schultz, the method the paper uses) minimises the residual of
+that system over the Krylov space. The flexible form keeps
+z_j = P^-1 v_j, so the update is u = u0 + Z y. With a fixed P this is
+plain right-preconditioned GMRES. A preconditioner that changes from one
+step to the next (an inexact V-cycle) is also allowed.
+
+Readings where the paper says nothing: x0 = 0; modified Gram-Schmidt;
+complex Givens rotations with a real cosine; stop when the least-squares
+residual estimate falls to tol * ||f||, then check the true residual and
+restart from the current iterate if it is still above tol.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["givens", "arnoldi", "gmres_right"]
+
+
+def givens(a: complex, b: complex):
+    """Rotation (c, s), with c real, that maps (a, b) to (r, 0).
+
+    The rotation is [[c, s], [-conj(s), c]]. Also returns r.
+    """
+    aa, bb = abs(a), abs(b)
+    if aa == 0.0:
+        return 0.0, 1.0 + 0j, b
+    rho = np.hypot(aa, bb)
+    c = aa / rho
+    s = (a / aa) * np.conj(b) / rho
+    return c, s, (a / aa) * rho
+
+
+def arnoldi(A, Pinv, v1, m):
+    """m steps of Arnoldi with modified Gram-Schmidt on A P^-1.
+
+    Returns V (N x (k+1)), Z (N x k) and Hbar ((k+1) x k), where k <= m is
+    the number of steps taken (fewer on breakdown). A Z = V Hbar holds.
+    """
+    N = v1.shape[0]
+    V = np.zeros((N, m + 1), dtype=np.complex128)
+    Z = np.zeros((N, m), dtype=np.complex128)
+    Hb = np.zeros((m + 1, m), dtype=np.complex128)
+    V[:, 0] = v1 / np.linalg.norm(v1)
+    for j in range(m):
+        Z[:, j] = Pinv(V[:, j])
+        w = A(Z[:, j])
+        for i in range(j + 1):
+            Hb[i, j] = np.vdot(V[:, i], w)
+            w = w - Hb[i, j] * V[:, i]
+        Hb[j + 1, j] = np.linalg.norm(w)
+        if Hb[j + 1, j] == 0.0:
+            return V[:, :j + 2], Z[:, :j + 1], Hb[:j + 2, :j + 1]
+        V[:, j + 1] = w / Hb[j + 1, j]
+    return V, Z, Hb
+
+
+def gmres_right(A, f, tol, restart, maxiter, Pinv=None, x0=None):
+    """Solve A x = f with GMRES(restart), right-preconditioned by Pinv.
+
+    ``A`` and ``Pinv`` are callables on 1D complex128 vectors (Pinv = None
+    means no preconditioner). Returns a dict with x, the number of inner
+    iterations, restarts, the residual estimate after every iteration
+    (relative to ||f||), the true relative residual after every cycle and
+    ``converged``.
+    """
+    f = np.asarray(f, dtype=np.complex128).ravel()
+    N = f.shape[0]
+    if Pinv is None:
+        Pinv = lambda v: v.copy()  # noqa: E731
+    x = np.zeros(N, dtype=np.complex128) if x0 is None else np.array(x0, np.complex128).ravel()
+    fnorm = np.linalg.norm(f)
+    out = {"history": [], "true_residuals": [], "iterations": 0, "restarts": 0,
+           "converged": False}
+    if fnorm == 0.0:
+        out.update(x=x, converged=True)
+        return out
+    its = 0
+    while its < maxiter:
+        r = f - A(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * fnorm:
+            out["converged"] = True
+            break
+        m = restart
+        V = np.zeros((N, m + 1), dtype=np.complex128)
+        Z = np.zeros((N, m), dtype=np.complex128)
+        R = np.zeros((m + 1, m), dtype=np.complex128)
+        cs = np.zeros(m)
+        sn = np.zeros(m, dtype=np.complex128)
+        g = np.zeros(m + 1, dtype=np.complex128)
+        g[0] = beta
+        V[:, 0] = r / beta
+        k = 0
+        for j in range(m):
+            Z[:, j] = Pinv(V[:, j])
+            w = A(Z[:, j])
+            for i in range(j + 1):
+                R[i, j] = np.vdot(V[:, i], w)
+                w = w - R[i, j] * V[:, i]
+            hn = np.linalg.norm(w)
+            R[j + 1, j] = hn
+            if hn != 0.0:
+                V[:, j + 1] = w / hn
+            # earlier rotations on the new column
+            for i in range(j):
+                a, b = R[i, j], R[i + 1, j]
+                R[i, j] = cs[i] * a + sn[i] * b
+                R[i + 1, j] = -np.conj(sn[i]) * a + cs[i] * b
+            cs[j], sn[j], R[j, j] = givens(R[j, j], R[j + 1, j])
+            R[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(sn[j]) * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            k = j + 1
+            out["history"].append(abs(g[j + 1]) / fnorm)
+            if abs(g[j + 1]) <= tol * fnorm or hn == 0.0 or its >= maxiter:
+                break
+        # least squares: upper-triangular R[:k,:k] y = g[:k]
+        y = np.zeros(k, dtype=np.complex128)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - R[i, i + 1:k] @ y[i + 1:k]) / R[i, i]
+        x = x + Z[:, :k] @ y
+        out["restarts"] += 1
+        rt = np.linalg.norm(f - A(x)) / fnorm
+        out["true_residuals"].append(rt)
+        if rt <= tol:
+            out["converged"] = True
+            break
+    out["x"] = x
+    out["iterations"] = its
+    return out

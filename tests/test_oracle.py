@@ -1,0 +1,409 @@
+"""Pins for the CPU oracle (no GPU).
+
+Each test checks the oracle against something other than its own formulas:
+closed forms, convergence under refinement, an independent Kronecker-sum
+construction, dense brute force, invariants, and the paper's spectral
+claim (Example section, Fig. 2).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import closed_form as cf
+from oracle import direct, gmres
+from oracle import multigrid as mg
+from oracle import operator as op
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- 1D closed forms (K1, K2)
+
+@pytest.mark.parametrize("n,s,c", [(101, 40, 2000.0), (64, 10, 1500.0), (257, 200, 3500.0)])
+def test_discrete_1d_closed_form(n, s, c):
+    """The sparse LU solution equals the exact solution of the recurrence."""
+    h, om, al = 5.0, 2 * np.pi * 10.0, 0.01
+    m = np.full(n, 1.0 / c)
+    f = np.zeros(n, complex)
+    f[s] = 1.0 / h
+    u = direct.lu_solve((n,), h, m, om, al, f)
+    ue = cf.discrete_1d(n, h, op.kappa(om, m, al)[0], s, 1.0 / h)
+    assert np.abs(u - ue).max() / np.abs(ue).max() < 1e-12
+
+
+def test_green_function_second_order():
+    """Point-source solutions converge to exp(-j k|x-xs|)/(2jk) at O(h^2)."""
+    om, al, L = 2 * np.pi * 10.0, 0.01, 2000.0
+    errs = []
+    for n in (201, 401, 801, 1601):
+        h = L / (n - 1)
+        m = np.full(n, 1.0 / 2000.0)
+        s = (n - 1) // 2
+        f = np.zeros(n, complex)
+        f[s] = 1.0 / h
+        u = direct.lu_solve((n,), h, m, om, al, f)
+        G = cf.green_1d(np.arange(n) * h, s * h, op.kappa(om, m, al)[0])
+        errs.append(np.abs(u - G).max() / np.abs(G).max())
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all((ratios > 3.8) & (ratios < 4.2)), ratios
+
+
+def test_green_function_rejects_wrong_boundary_sign():
+    """With the opposite sign in the boundary term the error does not shrink.
+
+    This is what makes the outgoing reading of the absorbing condition
+    checkable: the incoming version reflects and stays O(1) away from G.
+    """
+    om, al, L, n = 2 * np.pi * 10.0, 0.01, 2000.0, 801
+    h = L / (n - 1)
+    m = np.full(n, 1.0 / 2000.0)
+    kap = op.kappa(om, m, al)
+    s = (n - 1) // 2
+    f = np.zeros(n, complex)
+    f[s] = 1.0 / h
+    bad = op.laplacian_bc((n,), h, -np.conj(kap)) - sp.diags(op.sigma_H(om, m, al))
+    u = spla.spsolve(bad.tocsc(), f)
+    G = cf.green_1d(np.arange(n) * h, s * h, kap[0])
+    assert np.abs(u - G).max() / np.abs(G).max() > 0.1
+
+
+# ---------------------------------------------------------------- manufactured solution (K3)
+
+def _manufactured_errors(d, ks):
+    om, al = 2 * np.pi * 8.0, 0.01
+    lengths = (2000.0, 1000.0, 1500.0)[:d]
+    errs = []
+    for k in ks:
+        n = tuple(int(round(L / lengths[1] * k)) + 1 for L in lengths)
+        h = lengths[1] / k
+        ms = cf.Manufactured(lengths, om, al)
+        H = op.assemble_H(n, h, ms.slowness(n), om, al)
+        u = spla.spsolve(H.tocsc(), ms.rhs(n).ravel())
+        errs.append(np.abs(u - ms.u(n).ravel()).max())
+    return np.array(errs)
+
+
+def test_manufactured_2d_second_order():
+    e = _manufactured_errors(2, (16, 32, 64, 128))
+    order = np.log2(e[:-1] / e[1:])
+    assert np.all(order[-2:] > 1.8) and np.all(order[-2:] < 2.3), order
+
+
+def test_manufactured_3d_second_order():
+    e = _manufactured_errors(3, (6, 12, 24))
+    order = np.log2(e[:-1] / e[1:])
+    assert order[-1] > 1.7 and order[-1] < 2.4, order
+
+
+# ---------------------------------------------------------------- brute force (K4)
+
+def _k1d(n, h, kap):
+    """1D -d2/dx2 with absorbing ends, written row by row."""
+    K = np.zeros((n, n), complex)
+    for i in range(n):
+        K[i, i] = 2.0 / h ** 2
+        if i == 0:
+            K[i, i] += 2j * kap / h
+            K[i, 1] = -2.0 / h ** 2
+        elif i == n - 1:
+            K[i, i] += 2j * kap / h
+            K[i, n - 2] = -2.0 / h ** 2
+        else:
+            K[i, i - 1] = K[i, i + 1] = -1.0 / h ** 2
+    return K
+
+
+@pytest.mark.parametrize("n", [(64,), (8, 8), (4, 4, 4), (5, 3), (3, 4, 2)])
+def test_kronecker_sum_and_dense_solve(n):
+    """Constant medium: H equals a Kronecker sum of 1D operators, and splu
+    equals a dense solve."""
+    h, om, al, c = 7.0, 2 * np.pi * 12.0, 0.05, 1800.0
+    m = np.full(n[::-1], 1.0 / c)
+    kap = op.kappa(om, 1.0 / c, al)
+    H = op.assemble_H(n, h, m, om, al).toarray()
+    N = int(np.prod(n))
+    K = np.zeros((N, N), complex)
+    for a in range(len(n)):
+        left = np.eye(int(np.prod(n[a + 1:])))
+        right = np.eye(int(np.prod(n[:a])))
+        K += np.kron(left, np.kron(_k1d(n[a], h, kap), right))
+    K -= np.eye(N) * om ** 2 / c ** 2 * (1 - 1j * al)
+    assert np.abs(H - K).max() <= 1e-12 * np.abs(K).max()
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    u1 = np.linalg.solve(K, f)
+    u2 = spla.splu(sp.csc_matrix(H)).solve(f)
+    assert np.linalg.norm(u1 - u2) <= 1e-12 * np.linalg.norm(u1)
+
+
+# ---------------------------------------------------------------- invariants (K5)
+
+def test_H_minus_M_is_diagonal_and_DH_symmetric():
+    rng = np.random.default_rng(3)
+    n, h, om, al, b1, b2 = (9, 7), 10.0, 2 * np.pi * 10, 0.01, 1.0, 0.5
+    m = 1.0 / rng.uniform(1500, 4500, size=n[::-1])
+    H = op.assemble_H(n, h, m, om, al)
+    M = op.assemble_M(n, h, m, om, al, b1, b2)
+    Dm = (H - M).toarray()
+    expected = -om ** 2 * m.ravel() ** 2 * ((1 - 1j * al) - (b1 - 1j * b2))
+    assert np.abs(Dm - np.diag(expected)).max() < 1e-9 * np.abs(expected).max()
+    D = sp.diags(op.boundary_weights(n))
+    DH = (D @ H).toarray()
+    assert np.abs(DH - DH.T).max() < 1e-12 * np.abs(DH).max()
+    # damping and the outgoing boundary both give Im(D H) >= 0 on the diagonal
+    assert np.all(np.diag(DH).imag > 0)
+
+
+def test_paper_shift_is_M_with_negated_beta1():
+    """P = -Lap + beta k^2 (Eq. 6) equals M(beta1 = -b1, beta2 = b2)."""
+    n, h, om, al = (6, 5), 10.0, 2 * np.pi * 9, 0.02
+    m = np.full(n[::-1], 1 / 2100.0)
+    L = op.laplacian_bc(n, h, op.kappa(om, m, al))
+    for b1, b2 in [(1.0, 1.0), (0.5, 0.3)]:
+        P = L + sp.diags((b1 + 1j * b2) * om ** 2 * m.ravel() ** 2)
+        M = op.assemble_M(n, h, m, om, al, -b1, b2)
+        assert abs(P - M).max() < 1e-12 * abs(P).max()
+
+
+# ---------------------------------------------------------------- spectrum (K6, Fig. 2)
+
+def _paper_params():
+    with open(os.path.join(GOLDEN, "paper_parameters.json")) as fh:
+        return json.load(fh)
+
+
+def test_dirichlet_spectrum_on_circle():
+    """Constant k, Dirichlet, no damping, beta1 = 1: the eigenvalues of M^-1 H
+    are s/(s + j beta2 k^2) for real s, so |lambda - 1/2| = 1/2 exactly."""
+    n, h, k2 = 30, 1.0 / 31, 300.0
+    T = (np.diag(np.full(n, 2.0)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)) / h ** 2
+    I = np.eye(n)
+    Lap = np.kron(T, I) + np.kron(I, T)
+    for b2 in (0.5, 1.0):
+        H = Lap - k2 * np.eye(n * n)
+        M = Lap - (1.0 - 1j * b2) * k2 * np.eye(n * n)
+        lam = np.linalg.eigvals(np.linalg.solve(M, H))
+        assert np.abs(np.abs(lam - 0.5) - 0.5).max() < 1e-10
+
+
+def test_absorbing_spectrum_in_disc_paper_fig2():
+    """The paper's 1D spectral experiment (30 Hz, layered well, Fig. 2).
+
+    With the (beta1 - j beta2) reading, the eigenvalues of M^-1 H for the
+    paper's beta = (1, 1) and for (1, 0.5) lie in the disc |lambda - 1/2| <=
+    1/2 and have positive real parts: they move off the origin and the
+    negative real axis, as the paper states. The literal sign of Eq. 6
+    (P = -Lap + beta k^2) puts eigenvalues at negative real parts, which
+    contradicts that statement; this is why the build takes the other
+    reading.
+    """
+    p = _paper_params()
+    om = 2 * np.pi * p["spectrum_frequency_hz"]["value"]
+    b1, b2 = p["shift_beta"]["value"]
+    n, h, al = 201, 5.0, 0.01
+    i = np.arange(n)
+    m = 1.0 / np.where(i < n // 3, 1500.0, np.where(i < 2 * n // 3, 2500.0, 3500.0))
+    H = op.assemble_H((n,), h, m, om, al).toarray()
+    for beta in ((b1, b2), (1.0, 0.5)):
+        M = op.assemble_M((n,), h, m, om, al, *beta).toarray()
+        lam = np.linalg.eigvals(np.linalg.solve(M, H))
+        assert np.abs(lam - 0.5).max() <= 0.5 + 1e-9
+        assert lam.real.min() > 0.0
+    lam_H = np.linalg.eigvals(H)
+    assert lam_H.real.min() < 0.0          # H itself is indefinite
+    P_literal = op.assemble_M((n,), h, m, om, al, -b1, b2).toarray()
+    lam = np.linalg.eigvals(np.linalg.solve(P_literal, H))
+    assert lam.real.min() < -0.1
+
+
+# ---------------------------------------------------------------- GMRES (Eq. 7)
+
+def test_givens_zeroes_second_component():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        a, b = rng.standard_normal(2) + 1j * rng.standard_normal(2)
+        c, s, r = gmres.givens(a, b)
+        G = np.array([[c, s], [-np.conj(s), c]])
+        out = G @ np.array([a, b])
+        assert abs(out[1]) < 1e-14 * abs(r) and abs(out[0] - r) < 1e-14 * abs(r)
+        assert abs(np.linalg.det(G) - 1) < 1e-14 and np.allclose(G.conj().T @ G, np.eye(2))
+    c, s, r = gmres.givens(0.0, 2.0 + 1j)
+    assert c == 0.0 and abs(r - (2 + 1j)) < 1e-15
+
+
+def _small_system(n=(9, 7), seed=5, f_hz=12.0):
+    rng = np.random.default_rng(seed)
+    h, al = 10.0, 0.01
+    om = 2 * np.pi * f_hz
+    m = 1.0 / rng.uniform(1500, 4500, size=n[::-1])
+    H = op.assemble_H(n, h, m, om, al)
+    M = op.assemble_M(n, h, m, om, al, 1.0, 0.5)
+    N = int(np.prod(n))
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    return H, M, f
+
+
+def test_arnoldi_relation():
+    H, M, f = _small_system()
+    luM = spla.splu(M.tocsc())
+    V, Z, Hb = gmres.arnoldi(lambda x: H @ x, luM.solve, f, 8)
+    assert np.abs(H @ Z - V @ Hb).max() < 1e-12 * np.abs(Hb).max()
+    # modified Gram-Schmidt keeps the leading vectors orthonormal to rounding;
+    # later ones lose orthogonality in proportion to the condition number
+    G = V[:, :3].conj().T @ V[:, :3]
+    assert np.abs(G - np.eye(3)).max() < 1e-10
+    assert np.abs(np.linalg.norm(V, axis=0) - 1.0).max() < 1e-13
+
+
+def test_gmres_matches_lu_and_residual_decreases():
+    H, M, f = _small_system()
+    luM = spla.splu(M.tocsc())
+    u_lu = spla.splu(H.tocsc()).solve(f)
+    r = gmres.gmres_right(lambda x: H @ x, f, 1e-12, 10, 500, Pinv=luM.solve)
+    assert r["converged"]
+    assert np.linalg.norm(r["x"] - u_lu) < 1e-9 * np.linalg.norm(u_lu)
+    assert direct.true_relative_residual(H, f, r["x"]) <= 1e-12
+    hist = np.array(r["history"])
+    # within each cycle of 10 the least-squares residual never grows
+    for c0 in range(0, len(hist), 10):
+        seg = hist[c0:c0 + 10]
+        assert np.all(np.diff(seg) <= 1e-14)
+
+
+def test_full_gmres_terminates_in_N_steps():
+    H, M, f = _small_system(n=(6, 5))
+    N = f.shape[0]
+    r = gmres.gmres_right(lambda x: H @ x, f, 1e-10, N, N)
+    assert r["converged"] and r["iterations"] <= N
+
+
+def test_preconditioning_cuts_iterations_1d_well():
+    """Example section: plain GMRES converges slowly, shifted-Laplace GMRES fast."""
+    n, h, om, al = 401, 5.0, 2 * np.pi * 10.0, 0.01
+    i = np.arange(n)
+    m = 1.0 / np.where(i < n // 3, 1500.0, np.where(i < 2 * n // 3, 2500.0, 3500.0))
+    H = op.assemble_H((n,), h, m, om, al)
+    M = op.assemble_M((n,), h, m, om, al, 1.0, 0.5)
+    f = np.zeros(n, complex)
+    f[n // 2] = 1 / h
+    luM = spla.splu(M.tocsc())
+    rp = gmres.gmres_right(lambda x: H @ x, f, 1e-8, 50, 2000, Pinv=luM.solve)
+    r0 = gmres.gmres_right(lambda x: H @ x, f, 1e-8, 50, 400)
+    assert rp["converged"] and rp["iterations"] < 100
+    assert not r0["converged"]
+
+
+# ---------------------------------------------------------------- multigrid pieces
+
+def test_level_sizes_of_reference_grids():
+    def dims(n):
+        out = [tuple(n)]
+        while int(np.prod(n)) > 1500 and mg.can_coarsen(n):
+            n = tuple((k + 1) // 2 for k in n)
+            out.append(n)
+        return out
+    assert dims((401, 201))[-1] == (51, 26)
+    assert dims((801, 401))[-1] == (51, 26)
+    assert dims((257, 129))[-1] == (33, 17)
+    assert dims((257, 257, 193))[-1] == (9, 9, 7)
+    m = np.full((26, 51), 1 / 2000.0)
+    lv = mg.build_levels((51, 26), 80.0, m, 60.0, 0.01, 1.0, 0.5)
+    assert len(lv) == 1
+
+
+@pytest.mark.parametrize("nc", [(5,), (4, 3), (3, 4, 2)])
+def test_prolongation_exact_on_multilinear(nc):
+    nf = tuple(2 * k - 1 for k in nc)
+    rng = np.random.default_rng(0)
+    coef = rng.standard_normal(2 ** len(nc)) + 1j * rng.standard_normal(2 ** len(nc))
+
+    def multilinear(n, step):
+        X = np.meshgrid(*[np.arange(k) * step for k in n[::-1]], indexing="ij")[::-1]
+        out = np.zeros(X[0].shape, complex)
+        for mask in range(2 ** len(n)):
+            term = np.ones(X[0].shape)
+            for a in range(len(n)):
+                if mask >> a & 1:
+                    term = term * X[a]
+            out += coef[mask] * term
+        return out.ravel()
+    assert np.allclose(mg.prolong(nc, multilinear(nc, 2.0)), multilinear(nf, 1.0), atol=1e-12)
+
+
+def _as_matrix(fn, n_in):
+    N = int(np.prod(n_in))
+    cols = [fn(np.eye(N)[:, k]) for k in range(N)]
+    return np.array(cols).T
+
+
+@pytest.mark.parametrize("nc", [(4,), (3, 4), (3, 3, 2)])
+def test_restriction_is_scaled_adjoint_of_prolongation(nc):
+    """R = Dc^-1 P^T D / 2^d, with D the boundary-halving weights."""
+    nf = tuple(2 * k - 1 for k in nc)
+    P = _as_matrix(lambda e: mg.prolong(nc, e), nc)
+    R = _as_matrix(lambda r: mg.restrict(nf, r), nf)
+    D = np.diag(op.boundary_weights(nf))
+    Dc = np.diag(op.boundary_weights(nc))
+    assert np.abs(R - np.linalg.inv(Dc) @ P.T @ D / 2 ** len(nc)).max() < 1e-14
+    assert np.allclose(R @ np.ones(R.shape[1]), 1.0)
+
+
+def test_jacobi_fixed_point_and_first_sweep():
+    rng = np.random.default_rng(2)
+    n = (9, 5)
+    m = 1 / rng.uniform(1500, 4500, size=n[::-1])
+    lv = mg.build_levels(n, 10.0, m, 60.0, 0.01, 1.0, 0.5)
+    L = lv[0]
+    b = rng.standard_normal(L.M.shape[0]) + 0j
+    u = spla.spsolve(L.M.tocsc(), b)
+    assert np.allclose(mg.jacobi(L, u, b, 0.8), u, rtol=0, atol=1e-12 * np.abs(u).max())
+    assert np.allclose(mg.jacobi(L, 0 * b, b, 0.8), 0.8 * b / L.M.diagonal())
+
+
+def test_single_level_vcycle_is_exact_solve():
+    rng = np.random.default_rng(4)
+    n = (10, 6)
+    m = 1 / rng.uniform(1500, 4500, size=n[::-1])
+    lv = mg.build_levels(n, 10.0, m, 60.0, 0.01, 1.0, 0.5)
+    assert len(lv) == 1
+    b = rng.standard_normal(60) + 1j * rng.standard_normal(60)
+    assert np.allclose(lv[0].M @ mg.vcycle(lv, b), b, atol=1e-12 * np.abs(b).max())
+
+
+@pytest.mark.parametrize("freq", [0.5, 10.0])
+def test_vcycle_contraction(freq):
+    """V(1,1) error contraction on the shifted Laplacian, by power iteration.
+
+    Textbook damped-Jacobi / full-weighting / bilinear multigrid contracts by
+    about 0.35 per cycle near the Laplace limit; it must stay well below 1
+    at 10 Hz.
+    """
+    n, h = (129, 65), 10.0
+    m = np.full(n[::-1], 1 / 2000.0)
+    lv = mg.build_levels(n, h, m, 2 * np.pi * freq, 0.01, 1.0, 0.5)
+    M = lv[0].M
+    e = np.random.default_rng(0).standard_normal(M.shape[0]) + 0j
+    for _ in range(25):
+        e2 = e - mg.vcycle(lv, M @ e, 1, 1, 0.8)
+        rho = np.linalg.norm(e2) / np.linalg.norm(e)
+        e = e2 / np.linalg.norm(e2)
+    assert rho < 0.45
+
+
+def test_vcycle_fgmres_matches_lu_small_2d():
+    from workloads import workload
+    w = workload("2d_smooth_small")
+    m = w.slowness()
+    om = w.omega()
+    H = op.assemble_H(w.n, w.h, m, om, w.alpha)
+    f = w.rhs().ravel()
+    u_lu = spla.splu(H.tocsc()).solve(f)
+    lv = mg.build_levels(w.n, w.h, m, om, w.alpha, *w.beta)
+    r = gmres.gmres_right(lambda x: H @ x, f, 1e-8, 30, 500,
+                          Pinv=lambda v: mg.vcycle(lv, v, 1, 1, 0.8))
+    assert r["converged"] and r["true_residuals"][-1] <= 1e-8
+    assert np.linalg.norm(r["x"] - u_lu) <= 1e-6 * np.linalg.norm(u_lu)
