@@ -1,0 +1,187 @@
+/*
+ * helm.h -- C ABI of libhelm, a GB300 (sm_103a) solver for the heterogeneous
+ * Helmholtz equation, right-preconditioned by the shifted Laplacian.
+ *
+ * Method (Kazemi, "Application of shifted-Laplace preconditioners for
+ * heterogenous Helmholtz equation, part 1: Data modelling"):
+ *   Eq. 2   -Lap u - omega^2 m^2 (1 - j alpha) u = f, m = 1/c the slowness,
+ *           first-order absorbing boundary on every face (Summary, Eq. 1).
+ *   Eq. 3   H u = f, the discrete system.
+ *   Eq. 6   shifted Laplacian, written here as
+ *           M = -Lap - (beta1 - j beta2) omega^2 m^2 (same boundary rows as H).
+ *           The paper's P = -Lap + beta k^2 with beta = b1 + j b2 is
+ *           M with (beta1, beta2) = (-b1, b2).
+ *   Eq. 7   H M^-1 z = f, u = M^-1 z, solved by restarted flexible GMRES.
+ *
+ * Discretisation: second-order finite differences on a node grid; every
+ * node is an unknown. Boundary rows use a centred ghost node for
+ * dn u + j kappa u = 0 with kappa = omega m sqrt(1 - j alpha).
+ *
+ * Layout of every field: x fastest, index (iz * ny + iy) * nx + ix (2D:
+ * iz * nx + ix), complex values interleaved (re, im) as helm_c128, i.e. the
+ * memory layout of double2 / cuDoubleComplex / numpy complex128.
+ *
+ * Pointers: every array argument may be a host pointer or a CUDA device
+ * pointer of the current device; the library tells them apart with
+ * cudaPointerGetAttributes. Host arrays are staged through library-owned
+ * device buffers; device arrays are read and written in place on the grid's
+ * stream. The caller keeps ownership of every array it passes. The library
+ * owns the grid and all its device memory (model, multigrid hierarchy,
+ * Krylov basis) until helm_destroy_grid.
+ *
+ * Errors: every call returns a helm_status. On failure helm_last_error()
+ * returns a message for the calling thread. A grid is not thread-safe;
+ * distinct grids may be used from distinct threads.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_grid helm_grid;               /* opaque, library-owned */
+typedef struct { double re, im; } helm_c128;      /* == double2 */
+
+typedef enum {
+    HELM_OK = 0,
+    HELM_ERR_ARG = 1,            /* bad argument (null, size, range)               */
+    HELM_ERR_NOMEM = 2,          /* device allocation failed                         */
+    HELM_ERR_CUDA = 3,           /* a CUDA call failed                               */
+    HELM_ERR_NOT_CONVERGED = 4,  /* iteration cap reached; u holds the last iterate  */
+    HELM_ERR_BREAKDOWN = 5,      /* Arnoldi produced a non-finite or zero pivot      */
+    HELM_ERR_NONFINITE = 6,      /* input contains NaN or Inf                         */
+    HELM_ERR_STATE = 7,          /* call order violated (e.g. solve before model)    */
+    HELM_ERR_UNSUPPORTED = 8     /* option or grid shape the build cannot handle      */
+} helm_status;
+
+/* How M^-1 is applied inside the Krylov loop. */
+typedef enum {
+    HELM_PRECOND_MG = 0,     /* one geometric-multigrid V-cycle (default)            */
+    HELM_PRECOND_EXACT = 1,  /* dense inverse of M (grids up to 4096 nodes)            */
+    HELM_PRECOND_NONE = 2    /* M = I: plain GMRES, the paper's comparison arm        */
+} helm_precond;
+
+/* Arithmetic of the preconditioner. The outer FGMRES (Arnoldi, Givens,
+ * solution update, true residual) is always complex128. */
+typedef enum {
+    HELM_PREC_F64 = 0,       /* V-cycle in complex128                                 */
+    HELM_PREC_MIXED = 1      /* V-cycle in complex64, stored z in complex64           */
+} helm_precision;
+
+typedef struct {
+    int restart;             /* Krylov dimension m per cycle (1..256); default 30     */
+    int max_iters;           /* cap on inner iterations over all cycles; default 5000 */
+    int precond;             /* helm_precond                                          */
+    int precision;           /* helm_precision                                        */
+    int nu1, nu2;            /* damped-Jacobi sweeps before / after coarse correction */
+    double omega_jacobi;     /* Jacobi damping weight, (0, 1]; default 0.8            */
+    int coarse_max;          /* coarsen while a level has more nodes than this         */
+    int reorth;              /* 1: classical Gram-Schmidt twice (default); 0: once     */
+} helm_options;
+
+/* Fills *opt with the defaults listed above. */
+void helm_default_options(helm_options *opt);
+
+/* Creates a grid of n[0] x n[1] x n[2] nodes (unused axes: 1) with spacing
+ * h > 0 in metres. dim is 1, 2 or 3; every used axis needs >= 2 nodes.
+ * Device memory for the fine-level vectors is allocated here.
+ * Errors: HELM_ERR_ARG, HELM_ERR_NOMEM, HELM_ERR_CUDA. */
+helm_status helm_create_grid(int dim, const int64_t n[3], double h, helm_grid **out);
+
+/* Releases every device buffer of the grid. Null is ignored. */
+void helm_destroy_grid(helm_grid *g);
+
+/* Sets the CUDA stream (a cudaStream_t, may be 0) for all later work. */
+helm_status helm_set_stream(helm_grid *g, void *stream);
+
+/* Replaces the solver options. Takes effect at the next solve; a change of
+ * coarse_max, precond or precision rebuilds the hierarchy.
+ * Errors: HELM_ERR_ARG on an out-of-range field. */
+helm_status helm_set_options(helm_grid *g, const helm_options *opt);
+helm_status helm_get_options(const helm_grid *g, helm_options *opt);
+
+/* Eq. 2: sets the medium and frequency. m: slowness 1/c in s/m, one real
+ * double per node (host or device), all finite and > 0. omega: angular
+ * frequency in rad/s (> 0). alpha: damping (>= 0). The library copies m.
+ * Invalidates the preconditioner; it is rebuilt at the next solve or
+ * helm_set_shift. Errors: HELM_ERR_ARG, HELM_ERR_NONFINITE, HELM_ERR_CUDA. */
+helm_status helm_set_model(helm_grid *g, const double *m, double omega, double alpha);
+
+/* Eq. 6: sets the shift (beta1, beta2) of M = -Lap - (beta1 - j beta2) w^2 m^2
+ * and builds the multigrid hierarchy and the coarse-grid inverse on the
+ * device. Default (1, 0.5). Errors: HELM_ERR_STATE (no model),
+ * HELM_ERR_UNSUPPORTED (grid cannot be coarsened to coarse_max, or an exact
+ * preconditioner on more than 4096 nodes), HELM_ERR_NOMEM, HELM_ERR_CUDA. */
+helm_status helm_set_shift(helm_grid *g, double beta1, double beta2);
+
+/* Eq. 7: solves H u = f by restarted flexible GMRES, right-preconditioned
+ * by M, from u0 = 0, until ||f - H u||_2 / ||f||_2 <= tol (recomputed in
+ * complex128 after each cycle). f, u: N complex values (host or device,
+ * not overlapping). iterations (nullable): inner iterations used.
+ * true_rel_residual (nullable): the final true relative residual.
+ * Errors: HELM_ERR_STATE, HELM_ERR_ARG, HELM_ERR_NONFINITE (f not finite),
+ * HELM_ERR_NOT_CONVERGED (u holds the last iterate), HELM_ERR_BREAKDOWN,
+ * HELM_ERR_NOMEM, HELM_ERR_CUDA. */
+helm_status helm_solve(helm_grid *g, const helm_c128 *f, double tol, helm_c128 *u,
+                       int *iterations, double *true_rel_residual);
+
+/* Solves nrhs independent systems with the same H and M in one pass: every
+ * kernel launch of the Krylov loop covers all right-hand sides, each with
+ * its own Krylov space, Hessenberg matrix and stopping test. f, u: nrhs x N
+ * complex values, right-hand side k at offset k*N. iterations and
+ * true_rel_residual (nullable): nrhs entries each. Returns HELM_OK when all
+ * converged, HELM_ERR_NOT_CONVERGED if any did not. Other errors as
+ * helm_solve. */
+helm_status helm_solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double tol,
+                             helm_c128 *u, int *iterations, double *true_rel_residual);
+
+/* Eq. 3: y = H x on the fine grid (x, y: N complex values, host or device,
+ * not overlapping). Errors: HELM_ERR_STATE, HELM_ERR_ARG, HELM_ERR_CUDA. */
+helm_status helm_apply_H(helm_grid *g, const helm_c128 *x, helm_c128 *y);
+
+/* Eq. 6: y = M x on multigrid level `level` (0 = fine grid), in the grid's
+ * preconditioner arithmetic. x, y: the level's node count of complex values.
+ * Errors: HELM_ERR_STATE, HELM_ERR_ARG, HELM_ERR_CUDA. */
+helm_status helm_apply_M(helm_grid *g, int level, const helm_c128 *x, helm_c128 *y);
+
+/* Eq. 7, inner step: z = M^-1 r as applied inside the Krylov loop (one
+ * V-cycle, the dense inverse, or a copy), in the preconditioner's
+ * arithmetic. r, z: N complex values. Errors as helm_apply_H. */
+helm_status helm_apply_precond(helm_grid *g, const helm_c128 *r, helm_c128 *z);
+
+/* The true relative residual ||f - H u||_2 / ||f||_2 in complex128.
+ * Errors: HELM_ERR_STATE, HELM_ERR_ARG, HELM_ERR_CUDA. */
+helm_status helm_true_residual(helm_grid *g, const helm_c128 *f, const helm_c128 *u,
+                               double *rel);
+
+/* Number of multigrid levels (1 = no coarsening; 0 before helm_set_shift)
+ * and the node counts and spacing of one level. */
+int         helm_num_levels(const helm_grid *g);
+helm_status helm_level_info(const helm_grid *g, int level, int64_t n_out[3], double *h_out);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *helm_last_error(void);
+
+/* Per-kernel timing. helm_profile_start() turns on CUDA-event timing of every
+ * launch the library makes (process-wide, all grids; it adds two event
+ * records per launch). helm_profile_stop() waits for those events, turns the
+ * timing off and writes a JSON object into json (cap bytes) that maps each
+ * kernel name to its launch count, summed device milliseconds, algorithmic
+ * bytes and FP64 flops. Errors: HELM_ERR_ARG (buffer too small),
+ * HELM_ERR_CUDA. The paper has no counterpart: this is instrumentation. */
+helm_status helm_profile_start(void);
+helm_status helm_profile_stop(char *json, size_t cap);
+
+/* Number of kernels this library has launched in this process (all grids).
+ * Used to report launch counts; not thread-safe across concurrent grids. */
+uint64_t    helm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

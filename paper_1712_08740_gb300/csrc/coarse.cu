@@ -1,0 +1,174 @@
+// Coarsest-level solve of the shifted Laplacian (Eq. 6): the level's matrix is
+// assembled densely on the device, inverted once per (model, omega, shift) by
+// Gauss-Jordan elimination, and applied in every V-cycle as a dense
+// matrix-vector product (one warp per row).
+//
+// Gauss-Jordan runs without pivoting. D M (D halves boundary rows per face)
+// is complex symmetric with a positive-definite imaginary part (beta2 > 0 and
+// the outgoing boundary term), so every leading block is non-singular and no
+// zero pivot can occur; row scaling by D does not change that.
+#include "helm_internal.cuh"
+
+namespace helm {
+
+namespace {
+
+template <typename T> __device__ __forceinline__ T dsqrt(T v);
+template <> __device__ __forceinline__ float dsqrt<float>(float v) { return sqrtf(v); }
+template <> __device__ __forceinline__ double dsqrt<double>(double v) { return sqrt(v); }
+
+template <typename T>
+__global__ void k_assemble_dense(LevelView<T> L, OpShift<T> s, cplx_t<T> *__restrict__ A) {
+    const int N = L.nx * L.ny * L.nz;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const int ix = p % L.nx;
+    const int iy = (p / L.nx) % L.ny;
+    const int iz = p / (L.nx * L.ny);
+    const int coord[3] = {ix, iy, iz};
+    const int n[3] = {L.nx, L.ny, L.nz};
+    const int stride[3] = {1, L.nx, L.nx * L.ny};
+    cplx_t<T> *row = A + (size_t)p * N;
+    int nf = 0;
+    for (int a = 0; a < L.dim; ++a) {
+        const int i = coord[a];
+        if (i > 0) {
+            T c = (i == n[a] - 1) ? T(2) : T(1);
+            row[p - stride[a]].x += -c * L.inv_h2;
+        } else {
+            ++nf;
+        }
+        if (i < n[a] - 1) {
+            T c = (i == 0) ? T(2) : T(1);
+            row[p + stride[a]].x += -c * L.inv_h2;
+        } else {
+            ++nf;
+        }
+    }
+    const T wp = L.w[p];
+    T dre = T(2 * L.dim) * L.inv_h2 - s.s_re * wp;
+    T dim_ = -s.s_im * wp;
+    if (nf) {
+        const T f = T(nf) * L.two_over_h * dsqrt<T>(wp);
+        dre -= f * s.q_im;
+        dim_ += f * s.q_re;
+    }
+    row[p].x = dre;
+    row[p].y = dim_;
+}
+
+// Step k, part 1: save column k, then scale row k by 1/a_kk (a_kk <- 1/a_kk).
+template <typename T>
+__global__ void k_gj_pivot(cplx_t<T> *__restrict__ A, cplx_t<T> *__restrict__ col, int n, int k) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = A[(size_t)i * n + k];
+    __syncthreads();
+    const cplx_t<T> p = col[k];
+    const T den = p.x * p.x + p.y * p.y;
+    const T ir = p.x / den, ii = -p.y / den;       // 1 / p
+    cplx_t<T> *rk = A + (size_t)k * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        cplx_t<T> v = (j == k) ? mk<cplx_t<T>>(1.0, 0.0) : rk[j];
+        cplx_t<T> o;
+        o.x = v.x * ir - v.y * ii;
+        o.y = v.x * ii + v.y * ir;
+        rk[j] = o;
+    }
+}
+
+// Step k, part 2: every other row i: a_ij -= a_ik_old * a_kj_new (a_ik_old from col).
+template <typename T>
+__global__ void k_gj_elim(cplx_t<T> *__restrict__ A, const cplx_t<T> *__restrict__ col, int n,
+                          int k) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n || i == k) return;
+    const cplx_t<T> f = col[i];
+    const cplx_t<T> rkj = A[(size_t)k * n + j];
+    cplx_t<T> a = (j == k) ? mk<cplx_t<T>>(0.0, 0.0) : A[(size_t)i * n + j];
+    a.x -= f.x * rkj.x - f.y * rkj.y;
+    a.y -= f.x * rkj.y + f.y * rkj.x;
+    A[(size_t)i * n + j] = a;
+}
+
+template <typename T>
+__global__ void k_dense_gemv(const cplx_t<T> *__restrict__ Ainv, int n,
+                             const cplx_t<T> *__restrict__ r, size_t sr, cplx_t<T> *__restrict__ z,
+                             size_t sz, const int *__restrict__ active) {
+    const int rhs = blockIdx.y;
+    if (active && !active[rhs]) return;
+    r += rhs * sr;
+    z += rhs * sz;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (i >= n) return;
+    const cplx_t<T> *row = Ainv + (size_t)i * n;
+    T are = 0, aim = 0;
+    for (int j = lane; j < n; j += 32) {
+        const cplx_t<T> a = row[j];
+        const cplx_t<T> v = r[j];
+        are += a.x * v.x - a.y * v.y;
+        aim += a.x * v.y + a.y * v.x;
+    }
+    for (int o = 16; o; o >>= 1) {
+        are += __shfl_xor_sync(0xffffffffu, are, o);
+        aim += __shfl_xor_sync(0xffffffffu, aim, o);
+    }
+    if (lane == 0) {
+        cplx_t<T> out;
+        out.x = are;
+        out.y = aim;
+        z[i] = out;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_assemble_dense(const LevelView<T> &L, OpShift<T> s, cplx_t<T> *A, cudaStream_t st) {
+    const int N = L.nx * L.ny * L.nz;
+    cudaMemsetAsync(A, 0, sizeof(cplx_t<T>) * (size_t)N * N, st);
+    k_assemble_dense<T><<<(N + 127) / 128, 128, 0, st>>>(L, s, A);
+    count_launch();
+}
+
+template <typename T>
+void launch_gauss_jordan(cplx_t<T> *A, cplx_t<T> *colbuf, int n, cudaStream_t st) {
+    const dim3 blk(32, 8);
+    const dim3 grd((n + 31) / 32, (n + 7) / 8);
+    prof_begin(st);
+    for (int k = 0; k < n; ++k) {
+        k_gj_pivot<T><<<1, 1024, 0, st>>>(A, colbuf, n, k);
+        k_gj_elim<T><<<grd, blk, 0, st>>>(A, colbuf, n, k);
+    }
+    count_launch(2ull * n);
+    if (prof_on())
+        prof_end(sizeof(T) == 8 ? "gauss_jordan_f64" : "gauss_jordan_f32", st,
+                 2.0 * n * (double)n * n * sizeof(cplx_t<T>), sizeof(T) == 8 ? 8.0 * n * n * (double)n : 0.0);
+}
+
+template <typename T>
+void launch_dense_gemv(const cplx_t<T> *Ainv, int n, const cplx_t<T> *r, size_t sr,
+                       cplx_t<T> *z, size_t sz, int nb, const int *active, cudaStream_t st) {
+    const int warps = 8;
+    dim3 g((n + warps - 1) / warps, nb);
+    prof_begin(st);
+    k_dense_gemv<T><<<g, warps * 32, 0, st>>>(Ainv, n, r, sr, z, sz, active);
+    count_launch();
+    if (prof_on())
+        prof_end(sizeof(T) == 8 ? "coarse_gemv_f64" : "coarse_gemv_f32", st,
+                 ((double)n * n + 2.0 * n * nb) * sizeof(cplx_t<T>),
+                 sizeof(T) == 8 ? 8.0 * n * n * nb : 0.0);
+}
+
+template void launch_assemble_dense<float>(const LevelView<float> &, OpShift<float>, float2 *,
+                                           cudaStream_t);
+template void launch_assemble_dense<double>(const LevelView<double> &, OpShift<double>, double2 *,
+                                            cudaStream_t);
+template void launch_gauss_jordan<float>(float2 *, float2 *, int, cudaStream_t);
+template void launch_gauss_jordan<double>(double2 *, double2 *, int, cudaStream_t);
+template void launch_dense_gemv<float>(const float2 *, int, const float2 *, size_t, float2 *,
+                                       size_t, int, const int *, cudaStream_t);
+template void launch_dense_gemv<double>(const double2 *, int, const double2 *, size_t, double2 *,
+                                        size_t, int, const int *, cudaStream_t);
+
+}  // namespace helm

@@ -1,0 +1,64 @@
+// Library-side state of one helm_grid: model, multigrid hierarchy, coarse
+// inverse and the Krylov workspace, all resident in device memory.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/helm.h"
+#include "helm_internal.cuh"
+
+namespace helm {
+
+helm_status fail(helm_status s, const char *fmt, ...);
+void clear_error();
+
+// A device allocation that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    helm_status ensure(size_t b);
+    void release();
+    template <typename P> P *as() const { return static_cast<P *>(p); }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+};
+
+struct MGLevel {
+    int n[3] = {1, 1, 1};
+    int dim = 1;
+    double h = 0.0;
+    size_t N = 0;
+    DevBuf m;                  // slowness on this level (injected)
+    DevBuf w64, w32;           // omega^2 m^2
+    DevBuf u, t, b, r;         // V-cycle work vectors, [cap_rhs][N] in the V-cycle type
+};
+
+}  // namespace helm
+
+struct helm_grid {
+    int dim = 0;
+    int n[3] = {1, 1, 1};
+    double h = 0.0;
+    size_t N = 0;
+    cudaStream_t st = 0;
+    helm_options opt{};
+    bool has_model = false;
+    bool ready = false;        // hierarchy + coarse inverse match model/shift/options
+    double omega = 0.0, alpha = 0.0, beta1 = 1.0, beta2 = 0.5;
+
+    std::vector<helm::MGLevel> lv;      // lv[0] is the fine grid
+    int vc_prec = -1;                   // precision the hierarchy was built for
+    int nc = 0;                         // coarse inverse order
+    helm::DevBuf Ainv, colbuf;
+
+    // Krylov workspace
+    int cap_rhs = 0, cap_m = 0, cap_prec = -1;
+    helm::DevBuf V, Z, Zin, hbuf, nrm, yv, partial, counter, act_it, act_cy, flag;
+    helm::DevBuf fst, ust, xst, yst;    // staging for host pointers / helper vectors
+    void *pin = nullptr;                // pinned host mirror of hbuf + nrm
+    size_t pin_bytes = 0;
+};

@@ -1,0 +1,152 @@
+// Internal declarations shared by the libhelm translation units.
+//
+// Operators. On a level with spacing h and node coefficient w = omega^2 m^2
+// (real, per node) the library applies
+//     (A u)_p = d_p u_p - (1/h^2) sum_axes (c_lo u_lo + c_hi u_hi)
+//     d_p     = 2 dim / h^2 - s w_p + nfaces_p (2/h) j kappa_p
+//     kappa_p = sqrt(w_p) * q,   q = sqrt(1 - j alpha) (principal root)
+// with neighbour weights c = 1 inside, c = 2 for the inward neighbour of a
+// boundary node (centred ghost node of the absorbing condition) and c = 0
+// for the missing outer neighbour. s = 1 - j alpha gives H (Eq. 2-3);
+// s = beta1 - j beta2 gives the shifted Laplacian M (Eq. 6).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace helm {
+
+// ------------------------------------------------------------ complex helpers
+template <typename T> struct cplx;
+template <> struct cplx<float>  { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using cplx_t = typename cplx<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(double re, double im);
+template <> __host__ __device__ __forceinline__ float2 mk<float2>(double re, double im) {
+    return make_float2((float)re, (float)im);
+}
+template <> __host__ __device__ __forceinline__ double2 mk<double2>(double re, double im) {
+    return make_double2(re, im);
+}
+
+// widen/narrow between complex types
+template <typename To, typename From> __device__ __forceinline__ To cvt(From a) {
+    return mk<To>((double)a.x, (double)a.y);
+}
+template <> __device__ __forceinline__ float2 cvt<float2, float2>(float2 a) { return a; }
+template <> __device__ __forceinline__ double2 cvt<double2, double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ double2 cvt<double2, float2>(float2 a) {
+    return make_double2((double)a.x, (double)a.y);
+}
+template <> __device__ __forceinline__ float2 cvt<float2, double2>(double2 a) {
+    return make_float2(__double2float_rn(a.x), __double2float_rn(a.y));
+}
+
+// ------------------------------------------------------------ level geometry
+// One multigrid level (or the fine grid) as the kernels see it.
+template <typename T> struct LevelView {
+    int nx, ny, nz;          // node counts (1 on unused axes)
+    int dim;
+    T inv_h2;                // 1 / h^2
+    T two_over_h;            // 2 / h
+    const T *w;              // omega^2 m^2 per node
+};
+
+// Shift of the zero-order term and the boundary factor q = sqrt(1 - j alpha).
+template <typename T> struct OpShift {
+    T s_re, s_im;            // s
+    T q_re, q_im;            // q
+};
+
+// ------------------------------------------------------------ launch counter + profiler
+void count_launch(uint64_t k = 1);
+uint64_t launch_count();
+
+// Optional per-launch timing (off by default). prof_begin records a start
+// event on the launch stream; prof_end records the stop event and the
+// launch's algorithmic bytes and FP64 flops under `name`.
+bool prof_on();
+void prof_begin(cudaStream_t st);
+void prof_end(const char *name, cudaStream_t st, double bytes, double flops64);
+
+// ------------------------------------------------------------ stencil family
+enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_JACOBI = 2, ST_JACOBI0 = 3 };
+
+// mode APPLY : y = A x
+// mode RESID : y = b - A x
+// mode JACOBI: y = x + wj (b - A x) / d
+// mode JACOBI0: y = wj b / d        (x ignored: first sweep from zero)
+// nb right-hand sides at strides sx, sb, sy (elements); blockIdx.z walks them.
+template <typename T, typename CIn, typename COut>
+void launch_stencil(int mode, const LevelView<T> &L, OpShift<T> s, const CIn *x, size_t sx,
+                    const COut *b, size_t sb, COut *y, size_t sy, int nb, T wj,
+                    const int *active, cudaStream_t st);
+
+template <typename T>
+void launch_restrict(const LevelView<T> &fine, const LevelView<T> &coarse, const cplx_t<T> *rf,
+                     size_t sf, cplx_t<T> *rc, size_t sc, int nb, const int *active,
+                     cudaStream_t st);
+
+template <typename T>
+void launch_prolong_add(const LevelView<T> &fine, const LevelView<T> &coarse,
+                        const cplx_t<T> *ec, size_t sc, const cplx_t<T> *uin, size_t sin,
+                        cplx_t<T> *uf, size_t sf, int nb, const int *active, cudaStream_t st);
+
+// ------------------------------------------------------------ set-up kernels
+// w64 = omega^2 m^2 (and w32 = float(w64) if non-null); flag |= 1 where m is
+// not finite or not > 0
+void launch_make_w(const double *m, size_t n, double omega, double *w64, float *w32, int *flag,
+                   cudaStream_t st);
+// coarse[I] = fine[2 I] (injection) on an nx x ny x nz coarse grid
+template <typename T>
+void launch_inject(const T *fine, int fnx, int fny, T *coarse, int cnx, int cny, int cnz,
+                   cudaStream_t st);
+
+// ------------------------------------------------------------ coarse solve
+template <typename T>
+void launch_assemble_dense(const LevelView<T> &L, OpShift<T> s, cplx_t<T> *A, cudaStream_t st);
+template <typename T>
+void launch_gauss_jordan(cplx_t<T> *A, cplx_t<T> *colbuf, int n, cudaStream_t st);
+// z = Ainv r for nb right-hand sides
+template <typename T>
+void launch_dense_gemv(const cplx_t<T> *Ainv, int n, const cplx_t<T> *r, size_t sr,
+                       cplx_t<T> *z, size_t sz, int nb, const int *active, cudaStream_t st);
+
+// ------------------------------------------------------------ Krylov (complex128 outer)
+// All vectors of right-hand side k sit at base + k * stride_rhs; basis vector i
+// of right-hand side k at V + k * stride_rhs + i * N.
+struct KrylovScratch {
+    double2 *partial;        // [nrhs][max_blocks][nvec_max] block partial sums
+    unsigned *counter;       // [nrhs] last-block counters (zero between launches)
+    int max_blocks;
+    int nvec_max;
+};
+
+// out[k * out_stride + i] = sum_p conj(V_i[p]) w[p], i < nvec
+void launch_multidot(const double2 *V, size_t sV, int nvec, const double2 *w, size_t sw,
+                     size_t N, double2 *out, size_t out_stride, int nrhs, const int *active,
+                     KrylovScratch &ks, cudaStream_t st);
+// w[p] -= sum_i V_i[p] c[k * c_stride + i]; if norm2 != null, norm2[k] = ||w_new||^2
+void launch_multiaxpy(const double2 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
+                      double2 *w, size_t sw, size_t N, double *norm2, int nrhs,
+                      const int *active, KrylovScratch &ks, cudaStream_t st);
+// norm2[k] = ||x||^2
+void launch_norm2(const double2 *x, size_t sx, size_t N, double *norm2, int nrhs,
+                  const int *active, KrylovScratch &ks, cudaStream_t st);
+// y = x * scale[k] (real per right-hand side); COut may be float2 for the mixed V-cycle input
+template <typename COut>
+void launch_scale(const double2 *x, size_t sx, const double *scale, COut *y, size_t sy, size_t N,
+                  int nrhs, const int *active, cudaStream_t st);
+// x += sum_i Z_i y[k * y_stride + i]   (Z complex128 or complex64)
+template <typename CZ>
+void launch_update(const CZ *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
+                   double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st);
+template <typename CIn, typename COut>
+void launch_convert(const CIn *x, size_t sx, COut *y, size_t sy, size_t N, int nrhs,
+                    cudaStream_t st);
+// finite check: flag[0] |= 1 if any entry is NaN/Inf
+void launch_finite_check(const double *x, size_t n, int *flag, cudaStream_t st);
+
+}  // namespace helm

@@ -1,0 +1,136 @@
+// The V-cycle that applies M^-1 (Eq. 6) inside the Krylov loop (Eq. 7), and
+// the operator views it and the solver share.
+//
+// One V(nu1, nu2) cycle from a zero initial guess on every level:
+//   nu1 damped-Jacobi sweeps (the first one is wj D^-1 b), residual,
+//   full-weighting restriction, recursion, multilinear prolongation added to
+//   the iterate, nu2 damped-Jacobi sweeps. The coarsest level is solved by
+//   its dense inverse. Sweeps ping-pong between the level's iterate and a
+//   scratch vector; the order is chosen so that the last sweep lands in the
+//   iterate without a copy.
+#pragma once
+
+#include <array>
+#include <complex>
+#include <vector>
+
+#include "grid.cuh"
+
+namespace helm {
+
+bool is_device_ptr(const void *p);
+helm_status check_cuda(const char *where);
+helm_status sync_stream(helm_grid *g, const char *where);
+helm_status ensure_ready(helm_grid *g);
+helm_status ensure_level_work(helm_grid *g, int nrhs);
+const char *last_error();
+
+template <typename T> inline LevelView<T> level_view(const helm_grid *g, int l) {
+    const MGLevel &L = g->lv[l];
+    LevelView<T> v;
+    v.nx = L.n[0];
+    v.ny = L.n[1];
+    v.nz = L.n[2];
+    v.dim = L.dim;
+    v.inv_h2 = (T)(1.0 / (L.h * L.h));
+    v.two_over_h = (T)(2.0 / L.h);
+    v.w = (sizeof(T) == sizeof(double)) ? (const T *)L.w64.p : (const T *)L.w32.p;
+    return v;
+}
+
+inline std::complex<double> q_of(double alpha) {
+    return std::sqrt(std::complex<double>(1.0, -alpha));
+}
+
+// M = -Lap_bc - (beta1 - j beta2) w
+template <typename T> inline OpShift<T> shift_M(const helm_grid *g) {
+    const std::complex<double> q = q_of(g->alpha);
+    return OpShift<T>{(T)g->beta1, (T)(-g->beta2), (T)q.real(), (T)q.imag()};
+}
+
+// H = -Lap_bc - (1 - j alpha) w
+inline OpShift<double> shift_H(const helm_grid *g) {
+    const std::complex<double> q = q_of(g->alpha);
+    return OpShift<double>{1.0, -g->alpha, q.real(), q.imag()};
+}
+
+// u0 = V-cycle(b0) for nb right-hand sides; b0/u0 with per-rhs strides sb0/su0.
+template <typename T>
+void vcycle(helm_grid *g, const cplx_t<T> *b0, size_t sb0, cplx_t<T> *u0, size_t su0, int nb,
+            const int *act) {
+    using C = cplx_t<T>;
+    const int L = (int)g->lv.size();
+    const OpShift<T> sM = shift_M<T>(g);
+    const T wj = (T)g->opt.omega_jacobi;
+    const int nu1 = g->opt.nu1, nu2 = g->opt.nu2;
+    cudaStream_t st = g->st;
+    if (L == 1) {
+        launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, b0, sb0, u0, su0, nb, act, st);
+        return;
+    }
+    std::vector<const C *> B(L);
+    std::vector<C *> U(L);
+    std::vector<size_t> SB(L), SU(L);
+    B[0] = b0;
+    SB[0] = sb0;
+    U[0] = u0;
+    SU[0] = su0;
+    for (int l = 1; l < L; ++l) {
+        B[l] = g->lv[l].b.as<C>();
+        U[l] = g->lv[l].u.as<C>();
+        SB[l] = SU[l] = g->lv[l].N;
+    }
+    for (int l = 0; l < L - 1; ++l) {
+        const LevelView<T> Lv = level_view<T>(g, l);
+        const size_t N = g->lv[l].N;
+        C *tmp = g->lv[l].t.as<C>();
+        if (nu1 == 0) {
+            cudaMemset2DAsync(U[l], SU[l] * sizeof(C), 0, N * sizeof(C), nb, st);
+            launch_restrict<T>(Lv, level_view<T>(g, l + 1), B[l], SB[l], g->lv[l + 1].b.as<C>(),
+                               g->lv[l + 1].N, nb, act, st);
+            continue;
+        }
+        // sweep k (1-based) writes U[l] when nu1 - k is even, tmp otherwise
+        const C *prev = nullptr;
+        size_t sprev = 0;
+        for (int k = 1; k <= nu1; ++k) {
+            C *dst = ((nu1 - k) % 2 == 0) ? U[l] : tmp;
+            const size_t sdst = ((nu1 - k) % 2 == 0) ? SU[l] : N;
+            if (k == 1)
+                launch_stencil<T, C, C>(ST_JACOBI0, Lv, sM, (const C *)nullptr, 0, B[l], SB[l], dst,
+                                        sdst, nb, wj, act, st);
+            else
+                launch_stencil<T, C, C>(ST_JACOBI, Lv, sM, prev, sprev, B[l], SB[l], dst, sdst, nb,
+                                        wj, act, st);
+            prev = dst;
+            sprev = sdst;
+        }
+        C *res = g->lv[l].r.as<C>();
+        launch_stencil<T, C, C>(ST_RESID, Lv, sM, U[l], SU[l], B[l], SB[l], res, N, nb, wj, act,
+                                st);
+        launch_restrict<T>(Lv, level_view<T>(g, l + 1), res, N, g->lv[l + 1].b.as<C>(),
+                           g->lv[l + 1].N, nb, act, st);
+    }
+    launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, B[L - 1], SB[L - 1], U[L - 1], SU[L - 1], nb,
+                         act, st);
+    for (int l = L - 2; l >= 0; --l) {
+        const LevelView<T> Lv = level_view<T>(g, l);
+        const LevelView<T> Cv = level_view<T>(g, l + 1);
+        const size_t N = g->lv[l].N;
+        C *tmp = g->lv[l].t.as<C>();
+        // corrected iterate goes to U when nu2 is even, to tmp when odd
+        C *cur = (nu2 % 2 == 0) ? U[l] : tmp;
+        size_t scur = (nu2 % 2 == 0) ? SU[l] : N;
+        launch_prolong_add<T>(Lv, Cv, U[l + 1], SU[l + 1], U[l], SU[l], cur, scur, nb, act, st);
+        for (int k = 1; k <= nu2; ++k) {
+            C *dst = (cur == U[l]) ? tmp : U[l];
+            const size_t sdst = (cur == U[l]) ? N : SU[l];
+            launch_stencil<T, C, C>(ST_JACOBI, Lv, sM, cur, scur, B[l], SB[l], dst, sdst, nb, wj,
+                                    act, st);
+            cur = dst;
+            scur = sdst;
+        }
+    }
+}
+
+}  // namespace helm

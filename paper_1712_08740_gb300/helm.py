@@ -1,0 +1,287 @@
+"""ctypes binding of libhelm (include/helm.h): argument marshalling only.
+
+Every function here takes the C function's name and arguments. Arrays may
+be torch tensors (CUDA or CPU) or numpy arrays, complex128 (or float64 for
+the slowness), C-contiguous; their raw pointers go straight to the library,
+which reads host or device memory as the pointer says. All arithmetic runs
+in the library's CUDA kernels. If the shared library is missing this module
+raises at import: there is no other code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libhelm.so")
+
+HELM_OK = 0
+STATUS_NAMES = {0: "HELM_OK", 1: "HELM_ERR_ARG", 2: "HELM_ERR_NOMEM", 3: "HELM_ERR_CUDA",
+                4: "HELM_ERR_NOT_CONVERGED", 5: "HELM_ERR_BREAKDOWN", 6: "HELM_ERR_NONFINITE",
+                7: "HELM_ERR_STATE", 8: "HELM_ERR_UNSUPPORTED"}
+PRECOND = {"mg": 0, "exact": 1, "none": 2}
+PRECISION = {"f64": 0, "mixed": 1}
+
+EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "helm_set_stream",
+            "helm_set_options", "helm_get_options", "helm_set_model", "helm_set_shift",
+            "helm_solve", "helm_solve_batch", "helm_apply_H", "helm_apply_M",
+            "helm_apply_precond", "helm_true_residual", "helm_num_levels", "helm_level_info",
+            "helm_last_error", "helm_kernel_launches", "helm_profile_start", "helm_profile_stop")
+
+
+class helm_options(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("precond", ctypes.c_int),
+                ("precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("omega_jacobi", ctypes.c_double), ("coarse_max", ctypes.c_int),
+                ("reorth", ctypes.c_int)]
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhelm.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "helm_default_options": (None, [ctypes.POINTER(helm_options)]),
+        "helm_create_grid": (I, [I, ctypes.POINTER(ctypes.c_int64), D, ctypes.POINTER(P)]),
+        "helm_destroy_grid": (None, [P]),
+        "helm_set_stream": (I, [P, P]),
+        "helm_set_options": (I, [P, ctypes.POINTER(helm_options)]),
+        "helm_get_options": (I, [P, ctypes.POINTER(helm_options)]),
+        "helm_set_model": (I, [P, P, D, D]),
+        "helm_set_shift": (I, [P, D, D]),
+        "helm_solve": (I, [P, P, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "helm_solve_batch": (I, [P, I, P, D, P, P, P]),
+        "helm_apply_H": (I, [P, P, P]),
+        "helm_apply_M": (I, [P, I, P, P]),
+        "helm_apply_precond": (I, [P, P, P]),
+        "helm_true_residual": (I, [P, P, P, ctypes.POINTER(D)]),
+        "helm_num_levels": (I, [P]),
+        "helm_level_info": (I, [P, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]),
+        "helm_last_error": (ctypes.c_char_p, []),
+        "helm_kernel_launches": (ctypes.c_uint64, []),
+        "helm_profile_start": (I, []),
+        "helm_profile_stop": (I, [ctypes.c_char_p, ctypes.c_size_t]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status):
+    if status != HELM_OK:
+        raise HelmError(status, _lib.helm_last_error().decode())
+
+
+def _ptr(a, dtype):
+    """Raw pointer of a contiguous torch tensor or numpy array of `dtype`."""
+    if hasattr(a, "data_ptr"):                  # torch.Tensor
+        import torch
+        want = {np.complex128: torch.complex128, np.float64: torch.float64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous numpy {np.dtype(dtype).name} array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ------------------------------------------------------------------ C functions, same names
+
+def helm_default_options():
+    o = helm_options()
+    _lib.helm_default_options(ctypes.byref(o))
+    return o
+
+
+def helm_create_grid(dim, n, h):
+    nn = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    g = ctypes.c_void_p()
+    _check(_lib.helm_create_grid(int(dim), nn, float(h), ctypes.byref(g)))
+    return g
+
+
+def helm_destroy_grid(g):
+    _lib.helm_destroy_grid(g)
+
+
+def helm_set_stream(g, stream):
+    _check(_lib.helm_set_stream(g, ctypes.c_void_p(int(stream))))
+
+
+def helm_set_options(g, opt):
+    _check(_lib.helm_set_options(g, ctypes.byref(opt)))
+
+
+def helm_get_options(g):
+    o = helm_options()
+    _check(_lib.helm_get_options(g, ctypes.byref(o)))
+    return o
+
+
+def helm_set_model(g, m, omega, alpha):
+    _check(_lib.helm_set_model(g, _ptr(m, np.float64), float(omega), float(alpha)))
+
+
+def helm_set_shift(g, beta1, beta2):
+    _check(_lib.helm_set_shift(g, float(beta1), float(beta2)))
+
+
+def helm_solve(g, f, tol, u, check=True):
+    """Returns (status, iterations, true relative residual); raises unless
+    check is False."""
+    its = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = _lib.helm_solve(g, _ptr(f, np.complex128), float(tol), _ptr(u, np.complex128),
+                         ctypes.byref(its), ctypes.byref(rel))
+    if check:
+        _check(st)
+    return st, its.value, rel.value
+
+
+def helm_solve_batch(g, nrhs, f, tol, u, check=True):
+    its = np.zeros(nrhs, dtype=np.int32)
+    rel = np.zeros(nrhs, dtype=np.float64)
+    st = _lib.helm_solve_batch(g, int(nrhs), _ptr(f, np.complex128), float(tol),
+                               _ptr(u, np.complex128), its.ctypes.data_as(ctypes.c_void_p),
+                               rel.ctypes.data_as(ctypes.c_void_p))
+    if check:
+        _check(st)
+    return st, its, rel
+
+
+def helm_apply_H(g, x, y):
+    _check(_lib.helm_apply_H(g, _ptr(x, np.complex128), _ptr(y, np.complex128)))
+
+
+def helm_apply_M(g, level, x, y):
+    _check(_lib.helm_apply_M(g, int(level), _ptr(x, np.complex128), _ptr(y, np.complex128)))
+
+
+def helm_apply_precond(g, r, z):
+    _check(_lib.helm_apply_precond(g, _ptr(r, np.complex128), _ptr(z, np.complex128)))
+
+
+def helm_true_residual(g, f, u):
+    rel = ctypes.c_double(0.0)
+    _check(_lib.helm_true_residual(g, _ptr(f, np.complex128), _ptr(u, np.complex128),
+                                   ctypes.byref(rel)))
+    return rel.value
+
+
+def helm_num_levels(g):
+    return int(_lib.helm_num_levels(g))
+
+
+def helm_level_info(g, level):
+    nn = (ctypes.c_int64 * 3)()
+    h = ctypes.c_double(0.0)
+    _check(_lib.helm_level_info(g, int(level), nn, ctypes.byref(h)))
+    return tuple(int(v) for v in nn), h.value
+
+
+def helm_last_error():
+    return _lib.helm_last_error().decode()
+
+
+def helm_kernel_launches():
+    return int(_lib.helm_kernel_launches())
+
+
+def helm_profile_start():
+    _check(_lib.helm_profile_start())
+
+
+def helm_profile_stop():
+    """Per-kernel {name: {launches, ms, bytes, flops64}} since helm_profile_start."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(_lib.helm_profile_stop(buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+class Grid:
+    """Owns one helm_grid. ``n`` is the node count per axis, x first."""
+
+    def __init__(self, n, h, *, restart=30, precond="mg", precision="f64", nu1=1, nu2=1,
+                 omega_jacobi=0.8, coarse_max=1500, reorth=True, max_iters=5000):
+        self.n = tuple(int(k) for k in n)
+        self.N = int(np.prod(self.n))
+        self.h = float(h)
+        self._g = helm_create_grid(len(self.n), self.n, h)
+        self.set_options(restart=restart, precond=precond, precision=precision, nu1=nu1,
+                         nu2=nu2, omega_jacobi=omega_jacobi, coarse_max=coarse_max,
+                         reorth=reorth, max_iters=max_iters)
+
+    def set_options(self, **kw):
+        o = helm_get_options(self._g)
+        for k, v in kw.items():
+            if k == "precond":
+                v = PRECOND[v]
+            elif k == "precision":
+                v = PRECISION[v]
+            elif k == "reorth":
+                v = int(bool(v))
+            setattr(o, k, v)
+        helm_set_options(self._g, o)
+
+    def set_model(self, m, omega, alpha):
+        helm_set_model(self._g, m, omega, alpha)
+
+    def set_shift(self, beta1, beta2):
+        helm_set_shift(self._g, beta1, beta2)
+
+    def set_stream(self, stream):
+        helm_set_stream(self._g, stream)
+
+    def solve(self, f, tol, u, check=True):
+        return helm_solve(self._g, f, tol, u, check)
+
+    def solve_batch(self, nrhs, f, tol, u, check=True):
+        return helm_solve_batch(self._g, nrhs, f, tol, u, check)
+
+    def apply_H(self, x, y):
+        helm_apply_H(self._g, x, y)
+
+    def apply_M(self, level, x, y):
+        helm_apply_M(self._g, level, x, y)
+
+    def apply_precond(self, r, z):
+        helm_apply_precond(self._g, r, z)
+
+    def true_residual(self, f, u):
+        return helm_true_residual(self._g, f, u)
+
+    @property
+    def num_levels(self):
+        return helm_num_levels(self._g)
+
+    def level_info(self, level):
+        return helm_level_info(self._g, level)
+
+    def close(self):
+        if self._g:
+            helm_destroy_grid(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,64 @@
+"""The C ABI: the library builds, loads and exports every function that
+include/helm.h declares. Runs without a GPU (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1712_08740_gb300 import helm
+    return helm
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "helm.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(helm_[A-Za-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("helm_create_grid", "helm_set_model", "helm_set_shift", "helm_solve",
+                     "helm_solve_batch", "helm_apply_H", "helm_apply_precond", "helm_destroy_grid",
+                     "helm_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(so, name), name
+    assert set(declared_functions()) == set(lib.EXPORTED)
+
+
+def test_defaults_and_argument_errors_without_gpu(lib):
+    o = lib.helm_default_options()
+    assert (o.restart, o.precond, o.precision, o.nu1, o.nu2) == (30, 0, 0, 1, 1)
+    assert o.omega_jacobi == 0.8 and o.coarse_max == 1500 and o.reorth == 1
+    with pytest.raises(lib.HelmError) as e:
+        lib.helm_create_grid(4, (3, 3, 3), 1.0)
+    assert e.value.status == 1 and "dim" in e.value.message
+    with pytest.raises(lib.HelmError) as e:
+        lib.helm_create_grid(2, (1, 5), 1.0)
+    assert e.value.status == 1
+    with pytest.raises(lib.HelmError):
+        lib.helm_create_grid(2, (5, 5), -1.0)
+
+
+def test_oracle_is_not_imported_by_the_product():
+    pkg = os.path.join(ROOT, "paper_1712_08740_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                with open(os.path.join(dirpath, fn)) as fh:
+                    src = fh.read()
+                assert "oracle" not in re.findall(r"^\s*(?:from|import)\s+(\w+)", src, re.M), fn

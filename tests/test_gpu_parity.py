@@ -1,0 +1,279 @@
+"""GPU parity: every step of the path, called through the C ABI, against the
+CPU oracle on the same seeded inputs.
+
+Tolerances. Stencil and V-cycle steps in complex128 repeat the oracle's
+arithmetic up to rounding order: 1e-13 (stencil) and 1e-10 (V-cycle, whose
+dense coarse inverse carries cond(M_c) * eps). In complex64 the V-cycle
+agrees to ~1e-6 relative. Full solves must match the sparse-LU solution
+to 1e-6 relative L2 with a true relative residual <= 1e-8 (complex128 outer
+loop in both precision forms).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import direct, gmres  # noqa: E402
+from oracle import multigrid as mg  # noqa: E402
+from oracle import operator as op  # noqa: E402
+from workloads import workload  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def helm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1712_08740_gb300 import helm as h
+    return h
+
+
+def rand_model(n, seed, lo=1500.0, hi=4500.0):
+    rng = np.random.default_rng(seed)
+    return 1.0 / rng.uniform(lo, hi, size=tuple(n)[::-1])
+
+
+def rand_c(N, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(N) + 1j * rng.standard_normal(N)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).ravel()).to(DEV)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+SHAPES = [(37,), (2,), (37, 21), (130, 67), (2, 3), (9, 7, 5), (131, 3, 4)]
+
+
+@pytest.mark.parametrize("n", SHAPES)
+def test_apply_H_matches_oracle(helm, n):
+    h, om, al = 10.0, 2 * np.pi * 10.0, 0.01
+    m = rand_model(n, 1)
+    g = helm.Grid(n, h)
+    g.set_model(dev(m), om, al)
+    x = rand_c(int(np.prod(n)), 2)
+    y = torch.empty(len(x), dtype=torch.complex128, device=DEV)
+    g.apply_H(dev(x), y)
+    ref = op.assemble_H(n, h, m, om, al) @ x
+    assert rel(y.cpu().numpy(), ref) < 1e-13
+
+
+def test_unit_vectors_give_dense_H_columns(helm):
+    n, h, om, al = (8, 8), 12.0, 2 * np.pi * 9.0, 0.02
+    m = rand_model(n, 3)
+    g = helm.Grid(n, h)
+    g.set_model(m.ravel().copy(), om, al)          # host pointer path
+    Hd = op.assemble_H(n, h, m, om, al).toarray()
+    N = 64
+    y = np.zeros(N, complex)
+    for k in range(N):
+        e = np.zeros(N, complex)
+        e[k] = 1.0
+        g.apply_H(e, y)                              # host arrays in and out
+        assert np.abs(y - Hd[:, k]).max() <= 1e-15 * np.abs(Hd).max()
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-13), ("mixed", 3e-6)])
+def test_apply_M_every_level(helm, precision, tol):
+    n, h, om, al, b = (129, 65), 10.0, 2 * np.pi * 10.0, 0.01, (1.0, 0.5)
+    m = rand_model(n, 4)
+    g = helm.Grid(n, h, precision=precision)
+    g.set_model(dev(m), om, al)
+    g.set_shift(*b)
+    levels = mg.build_levels(n, h, m, om, al, *b, coarse_max=1500)
+    assert g.num_levels == len(levels)
+    for l, L in enumerate(levels):
+        nl, hl = g.level_info(l)
+        assert nl[:2] == L.n and abs(hl - L.h) < 1e-12
+        x = rand_c(L.M.shape[0], 10 + l)
+        y = torch.empty(len(x), dtype=torch.complex128, device=DEV)
+        g.apply_M(l, dev(x), y)
+        assert rel(y.cpu().numpy(), L.M @ x) < tol
+
+
+@pytest.mark.parametrize("n,nu", [((129, 65), (1, 1)), ((65, 33), (2, 1)), ((33, 17, 9), (1, 2)),
+                                  ((101, 51), (0, 1))])
+def test_vcycle_matches_oracle_f64(helm, n, nu):
+    h, om, al, b, wj = 10.0, 2 * np.pi * 10.0, 0.01, (1.0, 0.5), 0.8
+    m = rand_model(n, 5)
+    g = helm.Grid(n, h, nu1=nu[0], nu2=nu[1], omega_jacobi=wj)
+    g.set_model(dev(m), om, al)
+    g.set_shift(*b)
+    levels = mg.build_levels(n, h, m, om, al, *b, coarse_max=1500)
+    r = rand_c(int(np.prod(n)), 6)
+    z = torch.empty(len(r), dtype=torch.complex128, device=DEV)
+    g.apply_precond(dev(r), z)
+    ref = mg.vcycle(levels, r, nu[0], nu[1], wj)
+    assert rel(z.cpu().numpy(), ref) < 1e-10
+
+
+def test_vcycle_mixed_close_to_oracle(helm):
+    n, h, om, al, b = (129, 65), 10.0, 2 * np.pi * 10.0, 0.01, (1.0, 0.5)
+    m = rand_model(n, 7)
+    g = helm.Grid(n, h, precision="mixed")
+    g.set_model(dev(m), om, al)
+    g.set_shift(*b)
+    levels = mg.build_levels(n, h, m, om, al, *b)
+    r = rand_c(int(np.prod(n)), 8)
+    z = torch.empty(len(r), dtype=torch.complex128, device=DEV)
+    g.apply_precond(dev(r), z)
+    assert rel(z.cpu().numpy(), mg.vcycle(levels, r, 1, 1, 0.8)) < 2e-4
+
+
+def test_exact_precond_is_M_inverse(helm):
+    n, h, om, al = (61,), 5.0, 2 * np.pi * 10.0, 0.01
+    m = rand_model(n, 9)
+    g = helm.Grid(n, h, precond="exact")
+    g.set_model(dev(m), om, al)
+    g.set_shift(1.0, 0.5)
+    r = rand_c(61, 10)
+    z = torch.empty(61, dtype=torch.complex128, device=DEV)
+    g.apply_precond(dev(r), z)
+    M = op.assemble_M(n, h, m, om, al, 1.0, 0.5)
+    assert rel(z.cpu().numpy(), direct.spla.splu(M.tocsc()).solve(r)) < 1e-11
+
+
+def test_true_residual_matches_oracle(helm):
+    n, h, om, al = (70, 33), 10.0, 2 * np.pi * 10.0, 0.01
+    m = rand_model(n, 11)
+    g = helm.Grid(n, h)
+    g.set_model(dev(m), om, al)
+    f, u = rand_c(70 * 33, 12), rand_c(70 * 33, 13)
+    H = op.assemble_H(n, h, m, om, al)
+    assert abs(g.true_residual(dev(f), dev(u)) - direct.true_relative_residual(H, f, u)) < 1e-13
+
+
+# ------------------------------------------------------------------ full solves
+
+def solve_workload(helm, w, precision, precond=None, tol=None, host=False):
+    m = w.slowness()
+    f = w.rhs()
+    g = helm.Grid(w.n, w.h, restart=w.restart, precond=precond or w.precond, precision=precision)
+    g.set_model(dev(m), w.omega(), w.alpha)
+    g.set_shift(*w.beta)
+    if host:
+        fu = np.ascontiguousarray(f.ravel())
+        u = np.zeros_like(fu)
+        _, its, rr = g.solve(fu, tol or w.tol, u)
+        return u, its, rr, m, f
+    fd = dev(f)
+    ud = torch.empty_like(fd)
+    _, its, rr = g.solve(fd, tol or w.tol, ud)
+    return ud.cpu().numpy(), its, rr, m, f
+
+
+def test_solve_1d_well_exact_shift(helm):
+    w = workload("1d_well")
+    u, its, rr, m, f = solve_workload(helm, w, "f64")
+    u_lu = direct.lu_solve(w.n, w.h, m, w.omega(), w.alpha, f).ravel()
+    assert rr <= 1e-8 and rel(u, u_lu) <= 1e-6
+    # the oracle's GMRES with M applied by sparse LU takes 71 iterations
+    H = op.assemble_H(w.n, w.h, m, w.omega(), w.alpha)
+    M = op.assemble_M(w.n, w.h, m, w.omega(), w.alpha, *w.beta)
+    luM = direct.spla.splu(M.tocsc())
+    ref = gmres.gmres_right(lambda x: H @ x, f.ravel(), w.tol, w.restart, 5000, Pinv=luM.solve)
+    assert abs(its - ref["iterations"]) <= 2
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_solve_2d_smooth_401x201(helm, precision):
+    w = workload("2d_smooth")
+    u, its, rr, m, f = solve_workload(helm, w, precision)
+    u_lu = direct.lu_solve(w.n, w.h, m, w.omega(), w.alpha, f).ravel()
+    assert rr <= 1e-8, rr
+    assert rel(u, u_lu) <= 1e-6
+    assert its < 200
+
+
+def test_solve_host_pointers_equal_device(helm):
+    w = workload("2d_smooth_small")
+    u1, its1, rr1, _, _ = solve_workload(helm, w, "f64")
+    u2, its2, rr2, _, _ = solve_workload(helm, w, "f64", host=True)
+    assert its1 == its2 and np.array_equal(u1, u2)
+
+
+def test_solve_3d_small_mixed(helm):
+    w = workload("3d_smooth_small")
+    u, its, rr, m, f = solve_workload(helm, w, "mixed")
+    u_lu = direct.lu_solve(w.n, w.h, m, w.omega(), w.alpha, f).ravel()
+    assert rr <= 1e-8 and rel(u, u_lu) <= 1e-6
+
+
+def test_unpreconditioned_matches_oracle_iterations(helm):
+    n, h, om, al = (17, 9), 10.0, 2 * np.pi * 6.0, 0.05
+    m = rand_model(n, 14)
+    f = rand_c(17 * 9, 15)
+    g = helm.Grid(n, h, restart=20, precond="none")
+    g.set_model(dev(m), om, al)
+    g.set_shift(1.0, 0.5)
+    u = torch.empty(len(f), dtype=torch.complex128, device=DEV)
+    _, its, rr = g.solve(dev(f), 1e-9, u)
+    H = op.assemble_H(n, h, m, om, al)
+    ref = gmres.gmres_right(lambda x: H @ x, f, 1e-9, 20, 5000)
+    assert rr <= 1e-9 and abs(its - ref["iterations"]) <= 3
+    assert rel(u.cpu().numpy(), spsolve(H, f)) < 1e-6
+
+
+def spsolve(H, f):
+    return direct.spla.spsolve(H.tocsc(), f)
+
+
+def test_batch_equals_single(helm):
+    w = workload("2d_smooth_small")
+    m = w.slowness()
+    srcs = [(10, 2), (50, 2), (90, 2), (30, 40)]
+    from workloads import point_sources
+    F = np.stack([point_sources(w.n, w.h, [s]).ravel() for s in srcs])
+    g = helm.Grid(w.n, w.h, restart=30)
+    g.set_model(dev(m), w.omega(), w.alpha)
+    g.set_shift(*w.beta)
+    Fd = dev(F)
+    Ud = torch.empty_like(Fd)
+    _, its_b, rr_b = g.solve_batch(len(srcs), Fd, 1e-8, Ud)
+    Ub = Ud.cpu().numpy().reshape(len(srcs), -1)
+    for k in range(len(srcs)):
+        fk = dev(F[k])
+        uk = torch.empty_like(fk)
+        _, its, rr = g.solve(fk, 1e-8, uk)
+        assert its == its_b[k]
+        assert rel(Ub[k], uk.cpu().numpy()) < 1e-12
+        assert rr_b[k] <= 1e-8
+
+
+# ------------------------------------------------------------------ failure paths (host side)
+
+def test_errors_are_reported(helm):
+    n = (33, 17)
+    g = helm.Grid(n, 10.0)
+    f = dev(rand_c(33 * 17, 1))
+    u = torch.empty_like(f)
+    with pytest.raises(helm.HelmError) as e:
+        g.solve(f, 1e-8, u)
+    assert e.value.status == 7                       # solve before model
+    g.set_model(dev(rand_model(n, 2)), 60.0, 0.01)
+    bad = f.clone()
+    bad[5] = complex(float("nan"), 0.0)
+    with pytest.raises(helm.HelmError) as e:
+        g.solve(bad, 1e-8, u)
+    assert e.value.status == 6                       # non-finite right-hand side
+    g.set_options(max_iters=3)
+    st, its, rr = g.solve(f, 1e-12, u, check=False)
+    assert st == 4 and its == 3 and rr > 1e-12       # iteration cap: last iterate returned
+    m_bad = rand_model(n, 3)
+    m_bad[2, 2] = -1.0
+    with pytest.raises(helm.HelmError) as e:
+        g.set_model(dev(m_bad), 60.0, 0.01)
+    assert e.value.status == 6
+    g2 = helm.Grid((80, 60), 10.0)                   # even axes cannot be coarsened
+    g2.set_model(dev(rand_model((80, 60), 4)), 60.0, 0.01)
+    with pytest.raises(helm.HelmError) as e:
+        g2.set_shift(1.0, 0.5)
+    assert e.value.status == 8
