@@ -82,6 +82,7 @@ static bool can_coarsen(const int n[3], int dim) {
 // shift, options and precision.
 helm_status build_hierarchy(helm_grid *g) {
     if (!g->has_model) return fail(HELM_ERR_STATE, "helm_set_model has not been called");
+    prepare_vfused();
     const int prec = g->opt.precision;
     const int pc = g->opt.precond;
     // level dimensions
@@ -187,6 +188,7 @@ void helm_default_options(helm_options *o) {
     o->omega_jacobi = 0.8;
     o->coarse_max = 1500;
     o->reorth = 1;
+    o->graphs = 1;
 }
 
 const char *helm_last_error(void) { return helm::last_error(); }
@@ -233,7 +235,11 @@ helm_status helm_create_grid(int dim, const int64_t n[3], double h, helm_grid **
 void helm_destroy_grid(helm_grid *g) {
     if (!g) return;
     cudaStreamSynchronize(g->st);
-    if (g->pin) cudaFreeHost(g->pin);
+    for (auto e : g->step_graphs)
+        if (e) cudaGraphExecDestroy(e);
+    for (auto e : g->ring) cudaEventDestroy(e);
+    if (g->cap_st) cudaStreamDestroy(g->cap_st);
+    if (g->hflag) cudaFreeHost(g->hflag);
     delete g;
 }
 
@@ -256,11 +262,13 @@ helm_status helm_set_options(helm_grid *g, const helm_options *o) {
     if (!(o->omega_jacobi > 0.0 && o->omega_jacobi <= 1.0))
         return fail(HELM_ERR_ARG, "omega_jacobi must be in (0, 1]");
     if (o->coarse_max < 1) return fail(HELM_ERR_ARG, "coarse_max must be >= 1");
+    if (o->reorth < 0 || o->reorth > 2) return fail(HELM_ERR_ARG, "reorth must be 0, 1 or 2");
     if (o->precond == HELM_PRECOND_EXACT && g->N > 4096)
         return fail(HELM_ERR_UNSUPPORTED, "exact preconditioner needs <= 4096 nodes");
     const bool rebuild = o->precond != g->opt.precond || o->precision != g->opt.precision ||
                          o->coarse_max != g->opt.coarse_max;
     g->opt = *o;
+    g->use_graphs = o->graphs != 0;
     if (rebuild) g->ready = false;
     return HELM_OK;
 }

@@ -90,34 +90,67 @@ __global__ void k_gj_elim(cplx_t<T> *__restrict__ A, const cplx_t<T> *__restrict
     A[(size_t)i * n + j] = a;
 }
 
+// z_k = Ainv r_k for a tile of up to kRT right-hand sides per block: each warp
+// owns one row and reads it once for all right-hand sides of the tile.
+constexpr int kRT = 4;
+
 template <typename T>
 __global__ void k_dense_gemv(const cplx_t<T> *__restrict__ Ainv, int n,
                              const cplx_t<T> *__restrict__ r, size_t sr, cplx_t<T> *__restrict__ z,
-                             size_t sz, const int *__restrict__ active) {
-    const int rhs = blockIdx.y;
-    if (active && !active[rhs]) return;
-    r += rhs * sr;
-    z += rhs * sz;
+                             size_t sz, int nb, const int *__restrict__ active) {
+    const int rhs0 = blockIdx.y * kRT;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + warp;
     if (i >= n) return;
+    bool on[kRT];
+    int any = 0;
+#pragma unroll
+    for (int q = 0; q < kRT; ++q) {
+        on[q] = rhs0 + q < nb && (!active || active[rhs0 + q]);
+        any |= on[q];
+    }
+    if (!any) return;
     const cplx_t<T> *row = Ainv + (size_t)i * n;
-    T are = 0, aim = 0;
-    for (int j = lane; j < n; j += 32) {
+    T are[kRT][2], aim[kRT][2];
+#pragma unroll
+    for (int q = 0; q < kRT; ++q) are[q][0] = are[q][1] = aim[q][0] = aim[q][1] = 0;
+    int j = lane;
+    for (; j + 32 < n; j += 64) {
+        const cplx_t<T> a0 = row[j], a1 = row[j + 32];
+#pragma unroll
+        for (int q = 0; q < kRT; ++q) {
+            if (!on[q]) continue;
+            const cplx_t<T> *rq = r + (size_t)(rhs0 + q) * sr;
+            const cplx_t<T> v0 = rq[j], v1 = rq[j + 32];
+            are[q][0] += a0.x * v0.x - a0.y * v0.y;
+            aim[q][0] += a0.x * v0.y + a0.y * v0.x;
+            are[q][1] += a1.x * v1.x - a1.y * v1.y;
+            aim[q][1] += a1.x * v1.y + a1.y * v1.x;
+        }
+    }
+    for (; j < n; j += 32) {
         const cplx_t<T> a = row[j];
-        const cplx_t<T> v = r[j];
-        are += a.x * v.x - a.y * v.y;
-        aim += a.x * v.y + a.y * v.x;
+#pragma unroll
+        for (int q = 0; q < kRT; ++q) {
+            if (!on[q]) continue;
+            const cplx_t<T> v = r[(size_t)(rhs0 + q) * sr + j];
+            are[q][0] += a.x * v.x - a.y * v.y;
+            aim[q][0] += a.x * v.y + a.y * v.x;
+        }
     }
-    for (int o = 16; o; o >>= 1) {
-        are += __shfl_xor_sync(0xffffffffu, are, o);
-        aim += __shfl_xor_sync(0xffffffffu, aim, o);
-    }
-    if (lane == 0) {
-        cplx_t<T> out;
-        out.x = are;
-        out.y = aim;
-        z[i] = out;
+#pragma unroll
+    for (int q = 0; q < kRT; ++q) {
+        T sre = are[q][0] + are[q][1], sim = aim[q][0] + aim[q][1];
+        for (int o = 16; o; o >>= 1) {
+            sre += __shfl_xor_sync(0xffffffffu, sre, o);
+            sim += __shfl_xor_sync(0xffffffffu, sim, o);
+        }
+        if (lane == 0 && on[q]) {
+            cplx_t<T> out;
+            out.x = sre;
+            out.y = sim;
+            z[(size_t)(rhs0 + q) * sz + i] = out;
+        }
     }
 }
 
@@ -150,13 +183,13 @@ template <typename T>
 void launch_dense_gemv(const cplx_t<T> *Ainv, int n, const cplx_t<T> *r, size_t sr,
                        cplx_t<T> *z, size_t sz, int nb, const int *active, cudaStream_t st) {
     const int warps = 8;
-    dim3 g((n + warps - 1) / warps, nb);
+    dim3 g((n + warps - 1) / warps, (nb + kRT - 1) / kRT);
     prof_begin(st);
-    k_dense_gemv<T><<<g, warps * 32, 0, st>>>(Ainv, n, r, sr, z, sz, active);
+    k_dense_gemv<T><<<g, warps * 32, 0, st>>>(Ainv, n, r, sr, z, sz, nb, active);
     count_launch();
     if (prof_on())
         prof_end(sizeof(T) == 8 ? "coarse_gemv_f64" : "coarse_gemv_f32", st,
-                 ((double)n * n + 2.0 * n * nb) * sizeof(cplx_t<T>),
+                 ((double)n * n * ((nb + kRT - 1) / kRT) + 2.0 * n * nb) * sizeof(cplx_t<T>),
                  sizeof(T) == 8 ? 8.0 * n * n * nb : 0.0);
 }
 

@@ -1,39 +1,33 @@
 // Restarted flexible GMRES for H M^-1 z = f, u = M^-1 z (Eq. 7), for one or
 // many right-hand sides that share H and M.
 //
-// Device side (complex128 unless noted): V-cycle z_j = M^-1 v_j (complex64 in
-// the mixed form), w = H z_j written straight into the basis slot v_{j+1},
-// classical Gram-Schmidt (twice by default) as fused multi-dot and
-// multi-axpy kernels, the norm fused into the last axpy, scaling, and at the
-// end of a cycle x += Z y and the true residual f - H x.
-// Host side: the (m+1) x m Hessenberg least-squares problem per right-hand
-// side with complex Givens rotations (real cosine), which costs O(m) flops
-// per step and needs one small device-to-host copy per Arnoldi step.
+// Everything runs on the device. One Arnoldi step j is: the V-cycle
+// z_j = M^-1 v_j (complex64 in the mixed form), w = H z_j written straight
+// into basis slot v_{j+1}, classical Gram-Schmidt (twice by default) as fused
+// multi-dot / multi-axpy kernels with the norm fused into the last axpy, the
+// Givens update of the least-squares problem (cycle.cu), and the scaling of
+// v_{j+1}. A cycle ends with y = R^-1 g, x += Z y and the true residual
+// f - H x in complex128.
+//
+// The host only launches. Each step j is captured once into a CUDA graph
+// (per grid, batch size and options) and replayed; converged right-hand sides
+// are switched off by device flags, so steps launched ahead of the stopping
+// decision are no-ops for them. The host runs at most kLookahead steps ahead
+// of the device, polling a host-mapped "any right-hand side still stepping"
+// flag written by the Givens kernel, and synchronises once per cycle.
 #include <cmath>
 #include <complex>
 #include <cstring>
 #include <vector>
 
+#include "cycle.cuh"
 #include "vcycle.cuh"
 
 namespace helm {
 
-using cd = std::complex<double>;
-
 namespace {
 
-struct RhsState {
-    double fnorm = 0.0;
-    std::vector<cd> R, g, sn;
-    std::vector<double> cs;
-    int k = 0;             // steps in the current cycle
-    int its = 0;
-    bool done = false;      // converged or given up
-    bool iter = false;      // still stepping in this cycle
-    bool converged = false;
-    bool broke = false;
-    double relres = 0.0;
-};
+constexpr int kLookahead = 2;
 
 helm_status ensure_workspace(helm_grid *g, int nrhs) {
     const int m = g->opt.restart;
@@ -50,38 +44,73 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
             return s;
     }
     const int nv = m + 1;
-    if ((s = g->hbuf.ensure((size_t)nrhs * 2 * nv * sizeof(double2)))) return s;
-    if ((s = g->nrm.ensure((size_t)nrhs * sizeof(double)))) return s;
-    if ((s = g->yv.ensure((size_t)nrhs * m * sizeof(double2)))) return s;
-    const int max_blocks = 4 * 152;
-    if ((s = g->partial.ensure((size_t)nrhs * max_blocks * nv * sizeof(double2)))) return s;
-    if ((s = g->counter.ensure((size_t)nrhs * sizeof(unsigned)))) return s;
-    cudaMemsetAsync(g->counter.p, 0, (size_t)nrhs * sizeof(unsigned), g->st);
-    if ((s = g->act_it.ensure((size_t)nrhs * sizeof(int)))) return s;
-    if ((s = g->act_cy.ensure((size_t)nrhs * sizeof(int)))) return s;
-    const size_t pin_need = (size_t)nrhs * 2 * nv * sizeof(double2) + (size_t)nrhs * sizeof(double);
-    if (g->pin_bytes < pin_need) {
-        if (g->pin) cudaFreeHost(g->pin);
-        g->pin = nullptr;
-        g->pin_bytes = 0;
-        if (cudaMallocHost(&g->pin, pin_need) != cudaSuccess) {
+    const size_t R = (size_t)nrhs;
+    if ((s = g->hbuf.ensure(R * 2 * nv * sizeof(double2)))) return s;
+    if ((s = g->nrm.ensure(R * sizeof(double)))) return s;
+    if ((s = g->yv.ensure(R * m * sizeof(double2)))) return s;
+    const int max_blocks = kMaxBlocks;
+    if ((s = g->partial.ensure(R * max_blocks * nv * sizeof(double2)))) return s;
+    if ((s = g->counter.ensure(R * sizeof(unsigned)))) return s;
+    cudaMemsetAsync(g->counter.p, 0, R * sizeof(unsigned), g->st);
+    if ((s = g->act_it.ensure(R * sizeof(int))) || (s = g->act_cy.ensure(R * sizeof(int))) ||
+        (s = g->act2.ensure(R * sizeof(int))))
+        return s;
+    if ((s = g->cR.ensure(R * nv * m * sizeof(double2))) || (s = g->cg.ensure(R * nv * sizeof(double2))) ||
+        (s = g->ccs.ensure(R * m * sizeof(double))) || (s = g->csn.ensure(R * m * sizeof(double2))) ||
+        (s = g->cfn.ensure(R * sizeof(double))) || (s = g->cbeta.ensure(R * sizeof(double))) ||
+        (s = g->crel.ensure(R * sizeof(double))) || (s = g->ck.ensure(R * sizeof(int))) ||
+        (s = g->cits.ensure(R * sizeof(int))) || (s = g->cstat.ensure(R * sizeof(int))) ||
+        (s = g->cany.ensure(64)))
+        return s;
+    cudaMemsetAsync(g->cany.p, 0, 64, g->st);
+    prepare_cycle_kernels();
+    if (!g->hflag) {
+        if (cudaHostAlloc((void **)&g->hflag, 64, cudaHostAllocMapped) != cudaSuccess) {
             cudaGetLastError();
-            return fail(HELM_ERR_NOMEM, "pinned host buffer of %zu bytes", pin_need);
+            g->hflag = nullptr;
+            return fail(HELM_ERR_NOMEM, "host-mapped flag");
         }
-        g->pin_bytes = pin_need;
+        *(volatile int *)g->hflag = 0;
+    }
+    while ((int)g->ring.size() < kLookahead + 1) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return fail(HELM_ERR_CUDA, "event creation");
+        g->ring.push_back(e);
     }
     if ((s = ensure_level_work(g, nrhs))) return s;
     g->cap_rhs = nrhs;
     g->cap_m = m;
     g->cap_prec = prec;
+    g->graph_key = -1;
     return HELM_OK;
+}
+
+CycleState cycle_state(helm_grid *g) {
+    CycleState S;
+    S.m = g->opt.restart;
+    S.R = g->cR.as<double2>();
+    S.g = g->cg.as<double2>();
+    S.cs = g->ccs.as<double>();
+    S.sn = g->csn.as<double2>();
+    S.fnorm = g->cfn.as<double>();
+    S.beta = g->cbeta.as<double>();
+    S.relres = g->crel.as<double>();
+    S.k = g->ck.as<int>();
+    S.its = g->cits.as<int>();
+    S.status = g->cstat.as<int>();
+    S.act_it = g->act_it.as<int>();
+    S.act_cy = g->act_cy.as<int>();
+    S.any_dev = g->cany.as<int>();
+    S.ticket = reinterpret_cast<unsigned *>(g->cany.as<int>() + 8);
+    return S;
 }
 
 KrylovScratch scratch(helm_grid *g) {
     KrylovScratch ks;
     ks.partial = g->partial.as<double2>();
     ks.counter = g->counter.as<unsigned>();
-    ks.max_blocks = 4 * 152;
+    ks.max_blocks = kMaxBlocks;
     ks.nvec_max = g->opt.restart + 1;
     return ks;
 }
@@ -92,12 +121,10 @@ void apply_precond_j(helm_grid *g, int j, int nrhs, const int *act) {
     const int m = g->opt.restart;
     const size_t sV = (size_t)(m + 1) * N, sZ = (size_t)m * N;
     const double2 *vj = g->V.as<double2>() + (size_t)j * N;
-    if (g->opt.precision == HELM_PREC_F64) {
-        vcycle<double>(g, vj, sV, g->Z.as<double2>() + (size_t)j * N, sZ, nrhs, act);
-    } else {
-        launch_convert<double2, float2>(vj, sV, g->Zin.as<float2>(), N, N, nrhs, g->st);
-        vcycle<float>(g, g->Zin.as<float2>(), N, g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act);
-    }
+    if (g->opt.precision == HELM_PREC_F64)
+        vcycle<double, double2>(g, vj, sV, g->Z.as<double2>() + (size_t)j * N, sZ, nrhs, act);
+    else
+        vcycle<float, double2>(g, vj, sV, g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act);
 }
 
 // w = H z_j into basis slot j+1
@@ -125,19 +152,106 @@ void apply_H_j(helm_grid *g, int j, int nrhs, const int *act) {
     }
 }
 
-// Givens rotation with real cosine that maps (a, b) to (r, 0)
-inline void givens(cd a, cd b, double &c, cd &s, cd &r) {
-    const double aa = std::abs(a), bb = std::abs(b);
-    if (aa == 0.0) {
-        c = 0.0;
-        s = cd(1.0, 0.0);
-        r = b;
-        return;
+// One Arnoldi step j for all right-hand sides still stepping.
+void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
+    const size_t N = g->N;
+    const int m = g->opt.restart;
+    const int nv = m + 1;
+    const size_t sV = (size_t)nv * N;
+    cudaStream_t st = g->st;
+    KrylovScratch ks = scratch(g);
+    double2 *V = g->V.as<double2>();
+    double2 *hb = g->hbuf.as<double2>();
+    double *nrm = g->nrm.as<double>();
+    const int *act = g->act_it.as<int>();
+    if (g->opt.precond != HELM_PRECOND_NONE) apply_precond_j(g, j, nrhs, act);
+    apply_H_j(g, j, nrhs, act);
+    double2 *w = V + (size_t)(j + 1) * N;
+    const int nvec = j + 1;
+    const int mode = g->opt.reorth;      // 0: CGS once, 1: CGS twice, 2: twice only when needed
+    if (mode == 2) {
+        // first pass also returns ||w||^2 (w = slot j+1 taken as one more vector)
+        int *act2 = g->act2.as<int>();
+        launch_multidot(V, sV, nvec + 1, w, sV, N, hb, 2 * nv, nrhs, act, ks, st);
+        launch_multiaxpy(V, sV, nvec, hb, 2 * nv, w, sV, N, nrm, nrhs, act, ks, st);
+        launch_reorth_flags(act, hb, hb + nv, 2 * nv, nvec, nrm, 0.5, act2, nvec, nrhs, st);
+        launch_multidot(V, sV, nvec, w, sV, N, hb + nv, 2 * nv, nrhs, act2, ks, st);
+        launch_multiaxpy(V, sV, nvec, hb + nv, 2 * nv, w, sV, N, nrm, nrhs, act2, ks, st);
+    } else {
+        launch_multidot(V, sV, nvec, w, sV, N, hb, 2 * nv, nrhs, act, ks, st);
+        launch_multiaxpy(V, sV, nvec, hb, 2 * nv, w, sV, N, mode ? nullptr : nrm, nrhs, act, ks, st);
+        if (mode) {
+            launch_multidot(V, sV, nvec, w, sV, N, hb + nv, 2 * nv, nrhs, act, ks, st);
+            launch_multiaxpy(V, sV, nvec, hb + nv, 2 * nv, w, sV, N, nrm, nrhs, act, ks, st);
+        }
     }
-    const double rho = std::hypot(aa, bb);
-    c = aa / rho;
-    s = (a / aa) * std::conj(b) / rho;
-    r = (a / aa) * rho;
+    launch_givens(cycle_state(g), j, hb, 2 * nv, mode ? 1 : 0, nrm, nrhs, tol, g->opt.max_iters,
+                  g->hflag, st);
+    launch_scale<double2>(w, sV, nrm, w, sV, N, nrhs, act, st);
+}
+
+long long graph_key_of(const helm_grid *g, int nrhs, double tol) {
+    // everything baked into the captured kernels' arguments
+    long long k = nrhs;
+    k = k * 257 + g->opt.restart;
+    k = k * 3 + g->opt.precond;
+    k = k * 2 + g->opt.precision;
+    k = k * 17 + g->opt.nu1;
+    k = k * 17 + g->opt.nu2;
+    k = k * 3 + g->opt.reorth;
+    k ^= (long long)std::llround(g->opt.omega_jacobi * 1e6) << 20;
+    k ^= (long long)std::llround(-std::log10(tol) * 1e3) << 40;
+    k ^= (long long)g->opt.max_iters << 8;
+    k = k * 2 + (prof_on() ? 1 : 0);
+    return k;
+}
+
+void drop_graphs(helm_grid *g) {
+    for (auto e : g->step_graphs)
+        if (e) cudaGraphExecDestroy(e);
+    g->step_graphs.clear();
+    g->step_launches.clear();
+    g->step_prof.clear();
+    g->graph_key = -1;
+}
+
+helm_status capture_steps(helm_grid *g, int nrhs, double tol) {
+    const long long key = graph_key_of(g, nrhs, tol);
+    if (g->graph_key == key && (int)g->step_graphs.size() == g->opt.restart) return HELM_OK;
+    drop_graphs(g);
+    if (!g->cap_st) {
+        if (cudaStreamCreateWithFlags(&g->cap_st, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(HELM_ERR_CUDA, "capture stream");
+    }
+    cudaStream_t keep = g->st;
+    g->st = g->cap_st;
+    for (int j = 0; j < g->opt.restart; ++j) {
+        cudaGraph_t graph = nullptr;
+        const uint64_t l0 = launch_count();
+        if (prof_on()) prof_capture_begin();
+        cudaError_t e = cudaStreamBeginCapture(g->cap_st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            arnoldi_step(g, j, nrhs, tol);
+            e = cudaStreamEndCapture(g->cap_st, &graph);
+        }
+        g->step_prof.push_back(prof_on() ? prof_capture_end() : std::vector<ProfRecPublic>{});
+        g->step_launches.push_back(launch_count() - l0);
+        uncount_launch(g->step_launches.back());
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g->st = keep;
+            cudaGetLastError();
+            drop_graphs(g);
+            return fail(HELM_ERR_CUDA, "graph capture of Arnoldi step %d: %s", j,
+                        cudaGetErrorString(e));
+        }
+        g->step_graphs.push_back(exec);
+    }
+    g->st = keep;
+    g->graph_key = key;
+    return HELM_OK;
 }
 
 }  // namespace
@@ -150,202 +264,77 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
     if ((s = ensure_workspace(g, nrhs))) return s;
     const size_t N = g->N;
     const int m = g->opt.restart;
-    const int nv = m + 1;
     const size_t sV = (size_t)(m + 1) * N;
     cudaStream_t st = g->st;
     KrylovScratch ks = scratch(g);
     double2 *V = g->V.as<double2>();
-    double2 *hb = g->hbuf.as<double2>();
     double *nrm = g->nrm.as<double>();
-    int *act_it = g->act_it.as<int>(), *act_cy = g->act_cy.as<int>();
-    double2 *hpin = (double2 *)g->pin;
-    double *npin = (double *)((char *)g->pin + (size_t)nrhs * 2 * nv * sizeof(double2));
+    const CycleState S = cycle_state(g);
     const LevelView<double> L0 = level_view<double>(g, 0);
+    const bool graphs = g->use_graphs;
+    if (graphs && (s = capture_steps(g, nrhs, tol))) return s;
 
-    // non-finite input check
-    cudaMemsetAsync(g->flag.p, 0, sizeof(int), st);
-    launch_finite_check((const double *)f, 2 * N * (size_t)nrhs, g->flag.as<int>(), st);
-    int bad = 0;
-    cudaMemcpyAsync(&bad, g->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st);
-    // x = 0, v_0 = f, ||f||
+    // non-finite input check, x = 0, v_0 = f, ||f||, flags
+    int *flag = g->flag.as<int>();
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    launch_finite_check((const double *)f, 2 * N * (size_t)nrhs, flag, st);
     cudaMemsetAsync(u, 0, (size_t)nrhs * N * sizeof(double2), st);
     launch_convert<double2, double2>(f, N, V, sV, N, nrhs, st);
     launch_norm2(f, N, N, nrm, nrhs, nullptr, ks, st);
-    cudaMemcpyAsync(npin, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st);
+    launch_cycle_init(S, nrm, nrhs, g->hflag, st);
+    int bad = 0;
+    cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if ((s = sync_stream(g, "solve start"))) return s;
     if (bad) return fail(HELM_ERR_NONFINITE, "right-hand side contains NaN or Inf");
 
-    std::vector<RhsState> S(nrhs);
-    std::vector<int> h_act(nrhs);
-    for (int k = 0; k < nrhs; ++k) {
-        RhsState &R = S[k];
-        R.R.assign((size_t)(m + 1) * m, 0.0);
-        R.g.assign(m + 1, 0.0);
-        R.sn.assign(m, 0.0);
-        R.cs.assign(m, 0.0);
-        R.fnorm = std::sqrt(npin[k]);
-        if (R.fnorm == 0.0) {
-            R.done = R.converged = true;
-            R.relres = 0.0;
-        }
-    }
-    std::vector<double> beta(nrhs);
-    for (int k = 0; k < nrhs; ++k) beta[k] = S[k].fnorm;
-    std::vector<double2> ypin((size_t)nrhs * m);
-
-    while (true) {
-        // ---- start a cycle: v_0 = r / ||r|| (r already in slot 0, ||r||^2 in nrm)
-        int ncy = 0;
-        for (int k = 0; k < nrhs; ++k) {
-            RhsState &R = S[k];
-            R.iter = !R.done;
-            R.k = 0;
-            h_act[k] = R.iter ? 1 : 0;
-            ncy += h_act[k];
-            if (R.iter) {
-                std::fill(R.g.begin(), R.g.end(), cd(0.0));
-                R.g[0] = beta[k];
-            }
-        }
-        if (ncy == 0) break;
-        cudaMemcpyAsync(act_cy, h_act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(act_it, h_act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st);
-        launch_scale<double2>(V, sV, nrm, V, sV, N, nrhs, act_cy, st);
-
+    while (*(volatile int *)g->hflag) {
+        // v_0 = r / ||r|| (r in slot 0, ||r||^2 in nrm)
+        launch_scale<double2>(V, sV, nrm, V, sV, N, nrhs, S.act_cy, st);
         for (int j = 0; j < m; ++j) {
-            if (g->opt.precond != HELM_PRECOND_NONE) apply_precond_j(g, j, nrhs, act_it);
-            apply_H_j(g, j, nrhs, act_it);
-            double2 *w = V + (size_t)(j + 1) * N;
-            const int nvec = j + 1;
-            const bool two = g->opt.reorth != 0;
-            launch_multidot(V, sV, nvec, w, sV, N, hb, 2 * nv, nrhs, act_it, ks, st);
-            launch_multiaxpy(V, sV, nvec, hb, 2 * nv, w, sV, N, two ? nullptr : nrm, nrhs, act_it,
-                             ks, st);
-            if (two) {
-                launch_multidot(V, sV, nvec, w, sV, N, hb + nv, 2 * nv, nrhs, act_it, ks, st);
-                launch_multiaxpy(V, sV, nvec, hb + nv, 2 * nv, w, sV, N, nrm, nrhs, act_it, ks, st);
+            if (j >= kLookahead) {
+                cudaEvent_t e = g->ring[(j - kLookahead) % g->ring.size()];
+                if (cudaEventSynchronize(e) != cudaSuccess)
+                    return fail(HELM_ERR_CUDA, "Arnoldi step: %s", cudaGetErrorString(cudaGetLastError()));
+                if (!*(volatile int *)g->hflag) break;
             }
-            cudaMemcpyAsync(hpin, hb, (size_t)nrhs * 2 * nv * sizeof(double2),
-                            cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(npin, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st);
-            if ((s = sync_stream(g, "arnoldi step"))) return s;
-            bool changed = false;
-            int still = 0;
-            for (int k = 0; k < nrhs; ++k) {
-                RhsState &R = S[k];
-                if (!R.iter) continue;
-                cd *col = &R.R[(size_t)j];   // column j, row stride m
-                auto Rij = [&](int i) -> cd & { return R.R[(size_t)i * m + j]; };
-                for (int i = 0; i <= j; ++i) {
-                    const double2 a = hpin[(size_t)k * 2 * nv + i];
-                    cd v(a.x, a.y);
-                    if (two) {
-                        const double2 b2 = hpin[(size_t)k * 2 * nv + nv + i];
-                        v += cd(b2.x, b2.y);
-                    }
-                    Rij(i) = v;
-                }
-                (void)col;
-                const double hn = std::sqrt(npin[k]);
-                Rij(j + 1) = hn;
-                bool finite = std::isfinite(hn);
-                for (int i = 0; i <= j; ++i) finite = finite && std::isfinite(Rij(i).real()) &&
-                                                      std::isfinite(Rij(i).imag());
-                if (!finite) {
-                    R.iter = false;
-                    R.done = true;
-                    R.broke = true;
-                    changed = true;
-                    continue;
-                }
-                for (int i = 0; i < j; ++i) {
-                    const cd a = Rij(i), b = Rij(i + 1);
-                    Rij(i) = R.cs[i] * a + R.sn[i] * b;
-                    Rij(i + 1) = -std::conj(R.sn[i]) * a + R.cs[i] * b;
-                }
-                cd rr;
-                givens(Rij(j), Rij(j + 1), R.cs[j], R.sn[j], rr);
-                Rij(j) = rr;
-                Rij(j + 1) = 0.0;
-                R.g[j + 1] = -std::conj(R.sn[j]) * R.g[j];
-                R.g[j] = R.cs[j] * R.g[j];
-                R.k = j + 1;
-                R.its += 1;
-                const double est = std::abs(R.g[j + 1]);
-                if (est <= tol * R.fnorm || hn <= 1e-300 || R.its >= g->opt.max_iters) {
-                    R.iter = false;
-                    changed = true;
-                } else {
-                    ++still;
-                }
+            if (graphs) {
+                cudaError_t e = cudaGraphLaunch(g->step_graphs[j], st);
+                if (e != cudaSuccess) return fail(HELM_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+                count_launch(g->step_launches[j]);
+                if (prof_on()) prof_graph_replayed(g->step_prof[j]);
+            } else {
+                arnoldi_step(g, j, nrhs, tol);
             }
-            if (still == 0 || j == m - 1) break;
-            if (changed) {
-                for (int k = 0; k < nrhs; ++k) h_act[k] = S[k].iter ? 1 : 0;
-                cudaMemcpyAsync(act_it, h_act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice,
-                                st);
-            }
-            launch_scale<double2>(w, sV, nrm, w, sV, N, nrhs, act_it, st);
+            cudaEventRecord(g->ring[j % g->ring.size()], st);
         }
-
-        // ---- end of cycle: y = R^-1 g, x += Z y, r = f - H x
-        int kmax = 0;
-        for (int k = 0; k < nrhs; ++k) {
-            RhsState &R = S[k];
-            double2 *y = &ypin[(size_t)k * m];
-            for (int i = 0; i < m; ++i) y[i] = make_double2(0.0, 0.0);
-            if (R.done && !R.broke) continue;
-            if (R.broke || R.k == 0) continue;
-            std::vector<cd> yy(R.k);
-            for (int i = R.k - 1; i >= 0; --i) {
-                cd acc = R.g[i];
-                for (int q = i + 1; q < R.k; ++q) acc -= R.R[(size_t)i * m + q] * yy[q];
-                yy[i] = acc / R.R[(size_t)i * m + i];
-            }
-            for (int i = 0; i < R.k; ++i) y[i] = make_double2(yy[i].real(), yy[i].imag());
-            if (R.k > kmax) kmax = R.k;
-        }
-        for (int k = 0; k < nrhs; ++k) h_act[k] = (!S[k].done || S[k].broke) && S[k].k > 0 ? 1 : 0;
-        for (int k = 0; k < nrhs; ++k)
-            if (S[k].broke) h_act[k] = 0;
-        cudaMemcpyAsync(act_cy, h_act.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(g->yv.p, ypin.data(), (size_t)nrhs * m * sizeof(double2),
-                        cudaMemcpyHostToDevice, st);
-        if (kmax > 0) {
-            if (g->opt.precond == HELM_PRECOND_NONE)
-                launch_update<double2>(V, sV, kmax, g->yv.as<double2>(), m, u, N, N, nrhs, act_cy,
-                                       st);
-            else if (g->opt.precision == HELM_PREC_F64)
-                launch_update<double2>(g->Z.as<double2>(), (size_t)m * N, kmax,
-                                       g->yv.as<double2>(), m, u, N, N, nrhs, act_cy, st);
-            else
-                launch_update<float2>(g->Z.as<float2>(), (size_t)m * N, kmax, g->yv.as<double2>(),
-                                      m, u, N, N, nrhs, act_cy, st);
-        }
-        // true residual into slot 0
+        // end of cycle: y = R^-1 g, x += Z y, r = f - H x into slot 0, ||r||^2
+        launch_backsolve(S, g->yv.as<double2>(), nrhs, st);
+        if (g->opt.precond == HELM_PRECOND_NONE)
+            launch_update<double2>(V, sV, m, g->yv.as<double2>(), m, u, N, N, nrhs, S.act_cy, st);
+        else if (g->opt.precision == HELM_PREC_F64)
+            launch_update<double2>(g->Z.as<double2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u,
+                                   N, N, nrhs, S.act_cy, st);
+        else
+            launch_update<float2>(g->Z.as<float2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u, N,
+                                  N, nrhs, S.act_cy, st);
         launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, V, sV, nrhs,
-                                                 0.0, act_cy, st);
-        launch_norm2(V, sV, N, nrm, nrhs, act_cy, ks, st);
-        cudaMemcpyAsync(npin, nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st);
+                                                 0.0, S.act_cy, st);
+        launch_norm2(V, sV, N, nrm, nrhs, S.act_cy, ks, st);
+        launch_cycle_check(S, nrm, nrhs, tol, g->opt.max_iters, g->hflag, st);
         if ((s = sync_stream(g, "cycle end"))) return s;
-        for (int k = 0; k < nrhs; ++k) {
-            RhsState &R = S[k];
-            if (!h_act[k]) continue;
-            beta[k] = std::sqrt(npin[k]);
-            R.relres = beta[k] / R.fnorm;
-            if (R.relres <= tol) {
-                R.done = R.converged = true;
-            } else if (R.its >= g->opt.max_iters) {
-                R.done = true;
-            }
-        }
     }
+    std::vector<int> its(nrhs), stat(nrhs);
+    std::vector<double> rel(nrhs);
+    cudaMemcpyAsync(its.data(), S.its, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(stat.data(), S.status, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(rel.data(), S.relres, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if ((s = sync_stream(g, "solve end"))) return s;
     bool all_conv = true, any_broke = false;
     for (int k = 0; k < nrhs; ++k) {
-        if (iterations) iterations[k] = S[k].its;
-        if (relres_out) relres_out[k] = S[k].relres;
-        all_conv = all_conv && S[k].converged;
-        any_broke = any_broke || S[k].broke;
+        if (iterations) iterations[k] = its[k];
+        if (relres_out) relres_out[k] = rel[k];
+        all_conv = all_conv && stat[k] == ST_CONVERGED;
+        any_broke = any_broke || stat[k] == ST_BROKE;
     }
     if (any_broke) return fail(HELM_ERR_BREAKDOWN, "Arnoldi produced a non-finite value");
     if (!all_conv)
@@ -483,11 +472,10 @@ helm_status helm_apply_precond(helm_grid *g, const helm_c128 *r, helm_c128 *z) {
     if (g->opt.precond == HELM_PRECOND_NONE) {
         cudaMemcpyAsync(zd, rd, bytes, cudaMemcpyDeviceToDevice, g->st);
     } else if (g->vc_prec == HELM_PREC_F64) {
-        vcycle<double>(g, (const double2 *)rd, N, (double2 *)zd, N, 1, nullptr);
+        vcycle<double, double2>(g, (const double2 *)rd, N, (double2 *)zd, N, 1, nullptr);
     } else {
-        float2 *bf = g->lv[0].b.as<float2>(), *uf = g->lv[0].u.as<float2>();
-        launch_convert<double2, float2>((const double2 *)rd, 0, bf, 0, N, 1, g->st);
-        vcycle<float>(g, bf, N, uf, N, 1, nullptr);
+        float2 *uf = g->lv[0].u.as<float2>();
+        vcycle<float, double2>(g, (const double2 *)rd, N, uf, N, 1, nullptr);
         launch_convert<float2, double2>(uf, 0, (double2 *)zd, 0, N, 1, g->st);
     }
     if ((s = check_cuda("helm_apply_precond"))) return s;
@@ -505,14 +493,14 @@ helm_status helm_true_residual(helm_grid *g, const helm_c128 *f, const helm_c128
     const void *fd, *ud;
     if ((s = stage_in(g, f, bytes, g->fst, &fd)) || (s = stage_in(g, u, bytes, g->xst, &ud))) return s;
     if ((s = g->yst.ensure(bytes)) || (s = g->nrm.ensure(2 * sizeof(double))) ||
-        (s = g->partial.ensure((size_t)4 * 152 * sizeof(double2))) ||
+        (s = g->partial.ensure((size_t)kMaxBlocks * sizeof(double2))) ||
         (s = g->counter.ensure(sizeof(unsigned))))
         return s;
     if (g->cap_rhs == 0) cudaMemsetAsync(g->counter.p, 0, sizeof(unsigned), g->st);
     KrylovScratch ks;
     ks.partial = g->partial.as<double2>();
     ks.counter = g->counter.as<unsigned>();
-    ks.max_blocks = 4 * 152;
+    ks.max_blocks = kMaxBlocks;
     ks.nvec_max = 1;
     double2 *r = g->yst.as<double2>();
     launch_stencil<double, double2, double2>(ST_RESID, level_view<double>(g, 0), shift_H(g),

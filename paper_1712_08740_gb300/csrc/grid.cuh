@@ -57,8 +57,17 @@ struct helm_grid {
 
     // Krylov workspace
     int cap_rhs = 0, cap_m = 0, cap_prec = -1;
-    helm::DevBuf V, Z, Zin, hbuf, nrm, yv, partial, counter, act_it, act_cy, flag;
+    helm::DevBuf V, Z, Zin, hbuf, nrm, yv, partial, counter, act_it, act_cy, act2, flag;
+    helm::DevBuf cR, cg, ccs, csn, cfn, cbeta, crel, ck, cits, cstat, cany;   // FGMRES state
     helm::DevBuf fst, ust, xst, yst;    // staging for host pointers / helper vectors
-    void *pin = nullptr;                // pinned host mirror of hbuf + nrm
-    size_t pin_bytes = 0;
+    int *hflag = nullptr;               // host-mapped "any right-hand side active" flag
+    std::vector<cudaEvent_t> ring;      // look-ahead events of the Arnoldi loop
+
+    // CUDA graphs of one Arnoldi step per j, valid for graph_key
+    std::vector<cudaGraphExec_t> step_graphs;
+    std::vector<uint64_t> step_launches;                           // kernels per step graph
+    std::vector<std::vector<helm::ProfRecPublic>> step_prof;       // timing nodes per graph
+    long long graph_key = -1;
+    cudaStream_t cap_st = nullptr;      // private stream used only for capture
+    bool use_graphs = true;
 };

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <vector>
 
 namespace helm {
 
@@ -37,11 +38,32 @@ template <typename To, typename From> __device__ __forceinline__ To cvt(From a) 
 }
 template <> __device__ __forceinline__ float2 cvt<float2, float2>(float2 a) { return a; }
 template <> __device__ __forceinline__ double2 cvt<double2, double2>(double2 a) { return a; }
+// Precision changes go through the integer pipe: GB300 runs F2F conversions
+// at its (low) FP64 rate, while these bit manipulations use INT32 lanes.
+// f2d_exact widens exactly (zero, normal, inf/NaN; denormals fall back to the
+// hardware conversion). d2f_trunc narrows by truncating the mantissa (error
+// below one float ulp), flushing |x| < 2^-126 to zero: it feeds the complex64
+// preconditioner only, where rounding mode does not matter.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u) return (u & 0x7fffffu) ? (double)f : __hiloint2double((int)(u & 0x80000000u), 0);
+    const unsigned hi = (u & 0x80000000u) | ((e == 255u ? 2047u : e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)((u & 0x7u) << 29));
+}
+__device__ __forceinline__ float d2f_trunc(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    const unsigned sign = hi & 0x80000000u;
+    if (e < 897u) return __uint_as_float(sign);
+    if (e > 1150u) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
 template <> __device__ __forceinline__ double2 cvt<double2, float2>(float2 a) {
-    return make_double2((double)a.x, (double)a.y);
+    return make_double2(f2d_exact(a.x), f2d_exact(a.y));
 }
 template <> __device__ __forceinline__ float2 cvt<float2, double2>(double2 a) {
-    return make_float2(__double2float_rn(a.x), __double2float_rn(a.y));
+    return make_float2(d2f_trunc(a.x), d2f_trunc(a.y));
 }
 
 // ------------------------------------------------------------ level geometry
@@ -62,6 +84,7 @@ template <typename T> struct OpShift {
 
 // ------------------------------------------------------------ launch counter + profiler
 void count_launch(uint64_t k = 1);
+void uncount_launch(uint64_t k);     // kernels that were captured into a graph, not run
 uint64_t launch_count();
 
 // Optional per-launch timing (off by default). prof_begin records a start
@@ -70,6 +93,16 @@ uint64_t launch_count();
 bool prof_on();
 void prof_begin(cudaStream_t st);
 void prof_end(const char *name, cudaStream_t st, double bytes, double flops64);
+// During graph capture the timing events become event-record nodes of the
+// graph; prof_graph_replayed() reads them after each replay of that graph.
+struct ProfRecPublic {
+    const char *name;
+    cudaEvent_t e0, e1;
+    double bytes, flops;
+};
+void prof_capture_begin();
+std::vector<ProfRecPublic> prof_capture_end();
+void prof_graph_replayed(const std::vector<ProfRecPublic> &recs);
 
 // ------------------------------------------------------------ stencil family
 enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_JACOBI = 2, ST_JACOBI0 = 3 };
@@ -94,6 +127,19 @@ void launch_prolong_add(const LevelView<T> &fine, const LevelView<T> &coarse,
                         const cplx_t<T> *ec, size_t sc, const cplx_t<T> *uin, size_t sin,
                         cplx_t<T> *uf, size_t sf, int nb, const int *active, cudaStream_t st);
 
+// Fused V(1,1) level kernels for 2D/3D (vfused.cu). CB: type of the level's
+// right-hand side (complex128 basis vector at level 0 of the mixed form).
+template <typename T, typename CB>
+void launch_vdown(const LevelView<T> &F, const LevelView<T> &Cv, OpShift<T> s, T wj, const CB *b,
+                  size_t sb, cplx_t<T> *u, size_t su, cplx_t<T> *bc, size_t sbc, int nb,
+                  const int *active, cudaStream_t st);
+template <typename T, typename CB>
+void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, OpShift<T> s, T wj,
+                const cplx_t<T> *uin, size_t sin, const cplx_t<T> *ec, size_t sec, const CB *b,
+                size_t sb, cplx_t<T> *uout, size_t sout, int nb, const int *active,
+                cudaStream_t st);
+void prepare_vfused();   // sets shared-memory attributes; call outside graph capture
+
 // ------------------------------------------------------------ set-up kernels
 // w64 = omega^2 m^2 (and w32 = float(w64) if non-null); flag |= 1 where m is
 // not finite or not > 0
@@ -117,6 +163,8 @@ void launch_dense_gemv(const cplx_t<T> *Ainv, int n, const cplx_t<T> *r, size_t 
 // ------------------------------------------------------------ Krylov (complex128 outer)
 // All vectors of right-hand side k sit at base + k * stride_rhs; basis vector i
 // of right-hand side k at V + k * stride_rhs + i * N.
+constexpr int kMaxBlocks = 8 * 152;   // reduction grids: up to 8 blocks per SM
+
 struct KrylovScratch {
     double2 *partial;        // [nrhs][max_blocks][nvec_max] block partial sums
     unsigned *counter;       // [nrhs] last-block counters (zero between launches)
@@ -146,6 +194,10 @@ void launch_update(const CZ *Z, size_t sZ, int nvec, const double2 *y, size_t y_
 template <typename CIn, typename COut>
 void launch_convert(const CIn *x, size_t sx, COut *y, size_t sy, size_t N, int nrhs,
                     cudaStream_t st);
+// act2[r] = act[r] && n1[r] < eta2 * Re h1[r][wslot]; zero h2[r][0..nvec) where no second pass
+void launch_reorth_flags(const int *act, const double2 *h1, double2 *h2, int hstride, int wslot,
+                         const double *n1, double eta2, int *act2, int nvec, int nrhs,
+                         cudaStream_t st);
 // finite check: flag[0] |= 1 if any entry is NaN/Inf
 void launch_finite_check(const double *x, size_t n, int *flag, cudaStream_t st);
 

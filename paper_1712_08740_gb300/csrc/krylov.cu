@@ -25,6 +25,23 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Reduce-scatter of 16 doubles across a warp: afterwards lanes 2i and 2i+1 both
+// hold the warp sum of v[i]. Costs 16 additions instead of 5 per value.
+__device__ __forceinline__ double warp_reduce16(double v[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+        const bool up = (lane & bit) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const double send = up ? v[k] : v[k + half];
+            const double keep = up ? v[k + half] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // Last-block reduction of partial[b * nv + i] over b < nblk into out[i * ostride] / norm.
 // Returns true in the block that did it.
 __device__ bool last_block(unsigned *counter) {
@@ -40,6 +57,14 @@ __device__ bool last_block(unsigned *counter) {
     return is_last;
 }
 
+// Multi-dot: out[i] = sum_p conj(V_i[p]) w[p], i < nvec.
+// Basis vectors are taken in groups of kGroup: for each group a thread walks
+// its points once (w in a register, kGroup complex accumulators), so V is read
+// once and w nvec/kGroup times (from L1/L2). Every block then writes one
+// partial per vector; the last block adds the partials in block order, one
+// warp per vector (lane-strided over blocks, fixed shuffle tree).
+constexpr int kGroup = 8;
+
 __global__ void __launch_bounds__(kThreads)
 k_multidot(const double2 *__restrict__ V, size_t sV, int nvec, const double2 *__restrict__ w,
            size_t sw, size_t N, double2 *__restrict__ out, size_t ostride,
@@ -52,28 +77,37 @@ k_multidot(const double2 *__restrict__ V, size_t sV, int nvec, const double2 *__
     double2 *part = partial + ((size_t)r * gridDim.x + blockIdx.x) * nvec_max;
     __shared__ double2 red[kWarps][kMaxVec];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t chunk = (size_t)kThreads * kItems;
-    const size_t step = chunk * gridDim.x;
-    for (int i = 0; i < nvec; ++i) {
-        const double2 *Vi = V + (size_t)i * N;
-        double are = 0.0, aim = 0.0;
-        for (size_t base = blockIdx.x * chunk; base < N; base += step) {
+    const size_t step = (size_t)gridDim.x * kThreads;
+    for (int i0 = 0; i0 < nvec; i0 += kGroup) {
+        double are[kGroup], aim[kGroup];
 #pragma unroll
-            for (int t = 0; t < kItems; ++t) {
-                const size_t p = base + (size_t)t * kThreads + threadIdx.x;
-                if (p < N) {
-                    const double2 v = Vi[p];
-                    const double2 x = w[p];
-                    are = fma(v.x, x.x, are);
-                    are = fma(v.y, x.y, are);
-                    aim = fma(v.x, x.y, aim);
-                    aim = fma(-v.y, x.x, aim);
+        for (int q = 0; q < kGroup; ++q) are[q] = aim[q] = 0.0;
+        for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N; p += step) {
+            const double2 x = w[p];
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) {
+                if (i0 + q < nvec) {
+                    const double2 v = V[(size_t)(i0 + q) * N + p];
+                    are[q] = fma(v.x, x.x, are[q]);
+                    are[q] = fma(v.y, x.y, are[q]);
+                    aim[q] = fma(v.x, x.y, aim[q]);
+                    aim[q] = fma(-v.y, x.x, aim[q]);
                 }
             }
         }
-        are = warp_sum(are);
-        aim = warp_sum(aim);
-        if (lane == 0) red[warp][i] = make_double2(are, aim);
+        double v[16];
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) {
+            v[2 * q] = are[q];
+            v[2 * q + 1] = aim[q];
+        }
+        const double tot = warp_reduce16(v);
+        // lane 2i holds component i = 2q + (0 re | 1 im)
+        const int comp = (lane >> 1) & 15;
+        if ((lane & 1) == 0 && i0 + (comp >> 1) < nvec) {
+            double *dst = reinterpret_cast<double *>(&red[warp][i0 + (comp >> 1)]);
+            dst[comp & 1] = tot;
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nvec; i += kThreads) {
@@ -86,13 +120,16 @@ k_multidot(const double2 *__restrict__ V, size_t sV, int nvec, const double2 *__
     }
     if (last_block(counter + r)) {
         const double2 *pr = partial + (size_t)r * gridDim.x * nvec_max;
-        for (int i = threadIdx.x; i < nvec; i += kThreads) {
-            double2 s = make_double2(0.0, 0.0);
-            for (unsigned b = 0; b < gridDim.x; ++b) {
-                s.x += pr[(size_t)b * nvec_max + i].x;
-                s.y += pr[(size_t)b * nvec_max + i].y;
+        for (int i = warp; i < nvec; i += kWarps) {
+            double sx = 0.0, sy = 0.0;
+            for (unsigned b = lane; b < gridDim.x; b += 32) {
+                const double2 v = pr[(size_t)b * nvec_max + i];
+                sx += v.x;
+                sy += v.y;
             }
-            out[r * ostride + i] = s;
+            sx = warp_sum(sx);
+            sy = warp_sum(sy);
+            if (lane == 0) out[r * ostride + i] = make_double2(sx, sy);
         }
         if (threadIdx.x == 0) counter[r] = 0;
     }
@@ -111,11 +148,14 @@ __device__ void reduce_norm(double v, double *partial_d, unsigned *counter, doub
         partial_d[(size_t)r * gridDim.x + blockIdx.x] = s;
     }
     if (last_block(counter + r)) {
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
             double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += partial_d[(size_t)r * gridDim.x + b];
-            norm2[r] = s;
-            counter[r] = 0;
+            for (unsigned b = lane; b < gridDim.x; b += 32) s += partial_d[(size_t)r * gridDim.x + b];
+            s = warp_sum(s);
+            if (lane == 0) {
+                norm2[r] = s;
+                counter[r] = 0;
+            }
         }
     }
 }
@@ -136,7 +176,21 @@ k_multiaxpy(const double2 *__restrict__ V, size_t sV, int nvec, const double2 *_
     for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N;
          p += (size_t)gridDim.x * kThreads) {
         double2 acc = w[p];
-        for (int i = 0; i < nvec; ++i) {
+        int i = 0;
+        for (; i + 4 <= nvec; i += 4) {
+            double2 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = V[(size_t)(i + q) * N + p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double2 h = cs[i + q];
+                acc.x = fma(-v[q].x, h.x, acc.x);
+                acc.x = fma(v[q].y, h.y, acc.x);
+                acc.y = fma(-v[q].x, h.y, acc.y);
+                acc.y = fma(-v[q].y, h.x, acc.y);
+            }
+        }
+        for (; i < nvec; ++i) {
             const double2 v = V[(size_t)i * N + p];
             const double2 h = cs[i];
             acc.x = fma(-v.x, h.x, acc.x);
@@ -177,7 +231,10 @@ k_scale(const double2 *x, size_t sx, const double *__restrict__ norm2, COut *y, 
     if (active && !active[r]) return;
     x += r * sx;
     y += r * sy;
-    const double s = 1.0 / sqrt(norm2[r]);
+    __shared__ double s_sh;
+    if (threadIdx.x == 0) s_sh = 1.0 / sqrt(norm2[r]);
+    __syncthreads();
+    const double s = s_sh;
     for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N;
          p += (size_t)gridDim.x * kThreads) {
         const double2 v = x[p];
@@ -200,6 +257,7 @@ k_update(const CZ *__restrict__ Z, size_t sZ, int nvec, const double2 *__restric
     for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N;
          p += (size_t)gridDim.x * kThreads) {
         double2 acc = x[p];
+#pragma unroll 4
         for (int i = 0; i < nvec; ++i) {
             const double2 z = cvt<double2>(Z[(size_t)i * N + p]);
             const double2 h = ys[i];
@@ -223,6 +281,24 @@ k_convert(const CIn *__restrict__ x, size_t sx, COut *__restrict__ y, size_t sy,
         y[p] = cvt<COut>(x[p]);
 }
 
+// Selective reorthogonalisation test (Daniel-Gragg-Kaufman-Stewart): a second
+// Gram-Schmidt pass is needed when the first pass cancelled most of w,
+// ||w'||^2 < eta2 ||w||^2. ||w||^2 is the last entry of the first multi-dot
+// (w itself taken as an extra vector). Right-hand sides that skip the second
+// pass get zero second-pass coefficients.
+__global__ void k_reorth_flags(const int *__restrict__ act, const double2 *__restrict__ h1,
+                               double2 *__restrict__ h2, int hstride, int wslot,
+                               const double *__restrict__ n1, double eta2, int *__restrict__ act2,
+                               int nvec, int nrhs) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrhs; r += gridDim.x * blockDim.x) {
+        const int a = act ? act[r] : 1;
+        const int need = a && (n1[r] < eta2 * h1[(size_t)r * hstride + wslot].x);
+        act2[r] = need;
+        if (a && !need)
+            for (int i = 0; i < nvec; ++i) h2[(size_t)r * hstride + i] = make_double2(0.0, 0.0);
+    }
+}
+
 __global__ void k_finite(const double *__restrict__ x, size_t n, int *__restrict__ flag) {
     int bad = 0;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
@@ -242,7 +318,7 @@ inline int blocks_for(size_t N, int per_block, int cap) {
 void launch_multidot(const double2 *V, size_t sV, int nvec, const double2 *w, size_t sw,
                      size_t N, double2 *out, size_t out_stride, int nrhs, const int *active,
                      KrylovScratch &ks, cudaStream_t st) {
-    const int nb = blocks_for(N, kThreads * kItems, ks.max_blocks);
+    const int nb = blocks_for(N, kThreads * 2, ks.max_blocks);
     prof_begin(st);
     k_multidot<<<dim3(nb, nrhs), kThreads, 0, st>>>(V, sV, nvec, w, sw, N, out, out_stride,
                                                     ks.partial, ks.counter, ks.nvec_max, active);
@@ -254,7 +330,7 @@ void launch_multidot(const double2 *V, size_t sV, int nvec, const double2 *w, si
 void launch_multiaxpy(const double2 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
                       double2 *w, size_t sw, size_t N, double *norm2, int nrhs,
                       const int *active, KrylovScratch &ks, cudaStream_t st) {
-    const int nb = blocks_for(N, kThreads * kItems, ks.max_blocks);
+    const int nb = blocks_for(N, kThreads, ks.max_blocks);
     prof_begin(st);
     k_multiaxpy<<<dim3(nb, nrhs), kThreads, 0, st>>>(V, sV, nvec, c, c_stride, w, sw, N, norm2,
                                                      (double *)ks.partial, ks.counter, active);
@@ -266,7 +342,7 @@ void launch_multiaxpy(const double2 *V, size_t sV, int nvec, const double2 *c, s
 
 void launch_norm2(const double2 *x, size_t sx, size_t N, double *norm2, int nrhs,
                   const int *active, KrylovScratch &ks, cudaStream_t st) {
-    const int nb = blocks_for(N, kThreads * kItems, ks.max_blocks);
+    const int nb = blocks_for(N, kThreads * 2, ks.max_blocks);
     prof_begin(st);
     k_norm2<<<dim3(nb, nrhs), kThreads, 0, st>>>(x, sx, N, norm2, (double *)ks.partial,
                                                  ks.counter, active);
@@ -277,7 +353,7 @@ void launch_norm2(const double2 *x, size_t sx, size_t N, double *norm2, int nrhs
 template <typename COut>
 void launch_scale(const double2 *x, size_t sx, const double *norm2, COut *y, size_t sy, size_t N,
                   int nrhs, const int *active, cudaStream_t st) {
-    const int nb = blocks_for(N, kThreads * kItems, 1 << 16);
+    const int nb = blocks_for(N, kThreads, 1 << 16);
     prof_begin(st);
     k_scale<COut><<<dim3(nb, nrhs), kThreads, 0, st>>>(x, sx, norm2, y, sy, N, active);
     count_launch();
@@ -287,7 +363,7 @@ void launch_scale(const double2 *x, size_t sx, const double *norm2, COut *y, siz
 template <typename CZ>
 void launch_update(const CZ *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
                    double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st) {
-    const int nb = blocks_for(N, kThreads * kItems, 1 << 16);
+    const int nb = blocks_for(N, kThreads, 1 << 16);
     prof_begin(st);
     k_update<CZ><<<dim3(nb, nrhs), kThreads, 0, st>>>(Z, sZ, nvec, y, y_stride, x, sx, N, active);
     count_launch();
@@ -299,11 +375,19 @@ void launch_update(const CZ *Z, size_t sZ, int nvec, const double2 *y, size_t y_
 template <typename CIn, typename COut>
 void launch_convert(const CIn *x, size_t sx, COut *y, size_t sy, size_t N, int nrhs,
                     cudaStream_t st) {
-    const int nb = blocks_for(N, kThreads * kItems, 1 << 16);
+    const int nb = blocks_for(N, kThreads, 1 << 16);
     prof_begin(st);
     k_convert<CIn, COut><<<dim3(nb, nrhs), kThreads, 0, st>>>(x, sx, y, sy, N);
     count_launch();
     if (prof_on()) prof_end("convert", st, (double)(sizeof(CIn) + sizeof(COut)) * N * nrhs, 0.0);
+}
+
+void launch_reorth_flags(const int *act, const double2 *h1, double2 *h2, int hstride, int wslot,
+                         const double *n1, double eta2, int *act2, int nvec, int nrhs,
+                         cudaStream_t st) {
+    k_reorth_flags<<<(nrhs + 127) / 128, 128, 0, st>>>(act, h1, h2, hstride, wslot, n1, eta2, act2,
+                                                       nvec, nrhs);
+    count_launch();
 }
 
 void launch_finite_check(const double *x, size_t n, int *flag, cudaStream_t st) {

@@ -24,7 +24,11 @@ struct ProfRec {
 struct Prof {
     std::mutex mu;
     bool on = false;
+    bool capturing = false;             // records go to `captured` (event nodes in a graph)
     std::vector<ProfRec> recs;
+    std::vector<ProfRec> captured;
+    std::map<std::string, double[3]> graph_agg;   // name -> ms, bytes, flops of replays
+    std::map<std::string, uint64_t> graph_cnt;
     std::vector<cudaEvent_t> pool;
     cudaEvent_t pending = nullptr;
     cudaEvent_t get() {
@@ -68,6 +72,7 @@ __global__ void k_inject(const T *__restrict__ fine, int fnx, int fny, T *__rest
 }  // namespace
 
 void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void uncount_launch(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 bool prof_on() { return g_prof.on; }
@@ -76,16 +81,54 @@ void prof_begin(cudaStream_t st) {
     if (!g_prof.on) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     g_prof.pending = g_prof.get();
-    cudaEventRecord(g_prof.pending, st);
+    if (g_prof.capturing)
+        cudaEventRecordWithFlags(g_prof.pending, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(g_prof.pending, st);
 }
 
 void prof_end(const char *name, cudaStream_t st, double bytes, double flops64) {
     if (!g_prof.on || !g_prof.pending) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     cudaEvent_t e1 = g_prof.get();
-    cudaEventRecord(e1, st);
-    g_prof.recs.push_back({name, g_prof.pending, e1, bytes, flops64});
+    if (g_prof.capturing) {
+        cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
+        g_prof.captured.push_back({name, g_prof.pending, e1, bytes, flops64});
+    } else {
+        cudaEventRecord(e1, st);
+        g_prof.recs.push_back({name, g_prof.pending, e1, bytes, flops64});
+    }
     g_prof.pending = nullptr;
+}
+
+void prof_capture_begin() {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.capturing = true;
+    g_prof.captured.clear();
+}
+
+std::vector<ProfRecPublic> prof_capture_end() {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.capturing = false;
+    std::vector<ProfRecPublic> out;
+    for (auto &r : g_prof.captured) out.push_back({r.name, r.e0, r.e1, r.bytes, r.flops});
+    g_prof.captured.clear();
+    return out;
+}
+
+void prof_graph_replayed(const std::vector<ProfRecPublic> &recs) {
+    if (!g_prof.on) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (auto &r : recs) {
+        if (cudaEventSynchronize(r.e1) != cudaSuccess) return;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.e0, r.e1);
+        auto &a = g_prof.graph_agg[r.name];
+        a[0] += ms;
+        a[1] += r.bytes;
+        a[2] += r.flops;
+        g_prof.graph_cnt[r.name] += 1;
+    }
 }
 
 void launch_make_w(const double *m, size_t n, double omega, double *w64, float *w32, int *flag,
@@ -121,6 +164,8 @@ helm_status helm_profile_start(void) {
         helm::g_prof.pool.push_back(r.e1);
     }
     helm::g_prof.recs.clear();
+    helm::g_prof.graph_agg.clear();
+    helm::g_prof.graph_cnt.clear();
     helm::g_prof.on = true;
     return HELM_OK;
 }
@@ -139,6 +184,13 @@ helm_status helm_profile_stop(char *json, size_t cap) {
         a.ms += ms;
         a.bytes += r.bytes;
         a.flops += r.flops;
+    }
+    for (auto &kv : helm::g_prof.graph_agg) {
+        Agg &a = agg[kv.first];
+        a.n += helm::g_prof.graph_cnt[kv.first];
+        a.ms += kv.second[0];
+        a.bytes += kv.second[1];
+        a.flops += kv.second[2];
     }
     std::string out = "{";
     bool first = true;

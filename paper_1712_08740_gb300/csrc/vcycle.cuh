@@ -11,6 +11,7 @@
 #pragma once
 
 #include <array>
+#include <type_traits>
 #include <complex>
 #include <vector>
 
@@ -55,8 +56,10 @@ inline OpShift<double> shift_H(const helm_grid *g) {
 }
 
 // u0 = V-cycle(b0) for nb right-hand sides; b0/u0 with per-rhs strides sb0/su0.
-template <typename T>
-void vcycle(helm_grid *g, const cplx_t<T> *b0, size_t sb0, cplx_t<T> *u0, size_t su0, int nb,
+// CB0 is the type of b0: complex128 basis vectors feed a complex64 V-cycle
+// directly in the mixed form (the fused kernels convert on load).
+template <typename T, typename CB0>
+void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, int nb,
             const int *act) {
     using C = cplx_t<T>;
     const int L = (int)g->lv.size();
@@ -64,29 +67,71 @@ void vcycle(helm_grid *g, const cplx_t<T> *b0, size_t sb0, cplx_t<T> *u0, size_t
     const T wj = (T)g->opt.omega_jacobi;
     const int nu1 = g->opt.nu1, nu2 = g->opt.nu2;
     cudaStream_t st = g->st;
+    const bool fused = L > 1 && g->dim >= 2 && nu1 == 1 && nu2 == 1;
+    if (fused) {
+        // down: u_l (pre-smoothed, into the level's scratch) and b_{l+1}
+        for (int l = 0; l < L - 1; ++l) {
+            const LevelView<T> F = level_view<T>(g, l), Cv = level_view<T>(g, l + 1);
+            C *bc = g->lv[l + 1].b.template as<C>();
+            if (l == 0)
+                launch_vdown<T, CB0>(F, Cv, sM, wj, b0, sb0, g->lv[0].t.template as<C>(), g->lv[0].N,
+                                     bc, g->lv[1].N, nb, act, st);
+            else
+                launch_vdown<T, C>(F, Cv, sM, wj, g->lv[l].b.template as<C>(), g->lv[l].N,
+                                   g->lv[l].t.template as<C>(), g->lv[l].N, bc, g->lv[l + 1].N, nb,
+                                   act, st);
+        }
+        C *uc = (L - 1 == 0) ? u0 : g->lv[L - 1].u.template as<C>();
+        launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, g->lv[L - 1].b.template as<C>(),
+                             g->lv[L - 1].N, uc, g->lv[L - 1].N, nb, act, st);
+        // up: u_l = Jacobi(u_pre + P e_{l+1})
+        for (int l = L - 2; l >= 0; --l) {
+            const LevelView<T> F = level_view<T>(g, l), Cv = level_view<T>(g, l + 1);
+            const C *ec = g->lv[l + 1].u.template as<C>();
+            if (l == 0)
+                launch_vup<T, CB0>(F, Cv, sM, wj, g->lv[0].t.template as<C>(), g->lv[0].N, ec,
+                                   g->lv[1].N, b0, sb0, u0, su0, nb, act, st);
+            else
+                launch_vup<T, C>(F, Cv, sM, wj, g->lv[l].t.template as<C>(), g->lv[l].N, ec,
+                                 g->lv[l + 1].N, g->lv[l].b.template as<C>(), g->lv[l].N,
+                                 g->lv[l].u.template as<C>(), g->lv[l].N, nb, act, st);
+        }
+        return;
+    }
+    // general path: level-0 right-hand side in the V-cycle's own type
+    const C *b0c;
+    size_t sb0c;
+    if constexpr (std::is_same<CB0, C>::value) {
+        b0c = b0;
+        sb0c = sb0;
+    } else {
+        launch_convert<CB0, C>(b0, sb0, g->lv[0].b.template as<C>(), g->lv[0].N, g->lv[0].N, nb, st);
+        b0c = g->lv[0].b.template as<C>();
+        sb0c = g->lv[0].N;
+    }
     if (L == 1) {
-        launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, b0, sb0, u0, su0, nb, act, st);
+        launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, b0c, sb0c, u0, su0, nb, act, st);
         return;
     }
     std::vector<const C *> B(L);
     std::vector<C *> U(L);
     std::vector<size_t> SB(L), SU(L);
-    B[0] = b0;
-    SB[0] = sb0;
+    B[0] = b0c;
+    SB[0] = sb0c;
     U[0] = u0;
     SU[0] = su0;
     for (int l = 1; l < L; ++l) {
-        B[l] = g->lv[l].b.as<C>();
-        U[l] = g->lv[l].u.as<C>();
+        B[l] = g->lv[l].b.template as<C>();
+        U[l] = g->lv[l].u.template as<C>();
         SB[l] = SU[l] = g->lv[l].N;
     }
     for (int l = 0; l < L - 1; ++l) {
         const LevelView<T> Lv = level_view<T>(g, l);
         const size_t N = g->lv[l].N;
-        C *tmp = g->lv[l].t.as<C>();
+        C *tmp = g->lv[l].t.template as<C>();
         if (nu1 == 0) {
             cudaMemset2DAsync(U[l], SU[l] * sizeof(C), 0, N * sizeof(C), nb, st);
-            launch_restrict<T>(Lv, level_view<T>(g, l + 1), B[l], SB[l], g->lv[l + 1].b.as<C>(),
+            launch_restrict<T>(Lv, level_view<T>(g, l + 1), B[l], SB[l], g->lv[l + 1].b.template as<C>(),
                                g->lv[l + 1].N, nb, act, st);
             continue;
         }
@@ -105,10 +150,10 @@ void vcycle(helm_grid *g, const cplx_t<T> *b0, size_t sb0, cplx_t<T> *u0, size_t
             prev = dst;
             sprev = sdst;
         }
-        C *res = g->lv[l].r.as<C>();
+        C *res = g->lv[l].r.template as<C>();
         launch_stencil<T, C, C>(ST_RESID, Lv, sM, U[l], SU[l], B[l], SB[l], res, N, nb, wj, act,
                                 st);
-        launch_restrict<T>(Lv, level_view<T>(g, l + 1), res, N, g->lv[l + 1].b.as<C>(),
+        launch_restrict<T>(Lv, level_view<T>(g, l + 1), res, N, g->lv[l + 1].b.template as<C>(),
                            g->lv[l + 1].N, nb, act, st);
     }
     launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, B[L - 1], SB[L - 1], U[L - 1], SU[L - 1], nb,
@@ -117,7 +162,7 @@ void vcycle(helm_grid *g, const cplx_t<T> *b0, size_t sb0, cplx_t<T> *u0, size_t
         const LevelView<T> Lv = level_view<T>(g, l);
         const LevelView<T> Cv = level_view<T>(g, l + 1);
         const size_t N = g->lv[l].N;
-        C *tmp = g->lv[l].t.as<C>();
+        C *tmp = g->lv[l].t.template as<C>();
         // corrected iterate goes to U when nu2 is even, to tmp when odd
         C *cur = (nu2 % 2 == 0) ? U[l] : tmp;
         size_t scur = (nu2 % 2 == 0) ? SU[l] : N;

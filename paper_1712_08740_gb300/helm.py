@@ -35,7 +35,7 @@ class helm_options(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("precond", ctypes.c_int),
                 ("precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega_jacobi", ctypes.c_double), ("coarse_max", ctypes.c_int),
-                ("reorth", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class HelmError(RuntimeError):
@@ -220,14 +220,14 @@ class Grid:
     """Owns one helm_grid. ``n`` is the node count per axis, x first."""
 
     def __init__(self, n, h, *, restart=30, precond="mg", precision="f64", nu1=1, nu2=1,
-                 omega_jacobi=0.8, coarse_max=1500, reorth=True, max_iters=5000):
+                 omega_jacobi=0.8, coarse_max=1500, reorth=True, max_iters=5000, graphs=True):
         self.n = tuple(int(k) for k in n)
         self.N = int(np.prod(self.n))
         self.h = float(h)
         self._g = helm_create_grid(len(self.n), self.n, h)
         self.set_options(restart=restart, precond=precond, precision=precision, nu1=nu1,
                          nu2=nu2, omega_jacobi=omega_jacobi, coarse_max=coarse_max,
-                         reorth=reorth, max_iters=max_iters)
+                         reorth=reorth, max_iters=max_iters, graphs=graphs)
 
     def set_options(self, **kw):
         o = helm_get_options(self._g)
@@ -236,8 +236,10 @@ class Grid:
                 v = PRECOND[v]
             elif k == "precision":
                 v = PRECISION[v]
-            elif k == "reorth":
+            elif k == "graphs":
                 v = int(bool(v))
+            elif k == "reorth":
+                v = int(v)
             setattr(o, k, v)
         helm_set_options(self._g, o)
 

@@ -277,3 +277,40 @@ def test_errors_are_reported(helm):
     with pytest.raises(helm.HelmError) as e:
         g2.set_shift(1.0, 0.5)
     assert e.value.status == 8
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_graph_replay_equals_direct_launches(helm, precision):
+    w = workload("2d_smooth_small")
+    m = w.slowness()
+    from workloads import point_sources
+    F = np.stack([point_sources(w.n, w.h, [s]).ravel() for s in [(10, 2), (70, 30), (99, 50)]])
+    out = []
+    for graphs in (True, False):
+        g = helm.Grid(w.n, w.h, restart=12, precision=precision, graphs=graphs)
+        g.set_model(dev(m), w.omega(), w.alpha)
+        g.set_shift(*w.beta)
+        Fd = dev(F)
+        Ud = torch.empty_like(Fd)
+        _, its, rr = g.solve_batch(3, Fd, 1e-9, Ud)
+        out.append((Ud.cpu().numpy(), its, rr))
+        assert np.all(rr <= 1e-9)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("reorth", [0, 2])
+def test_gram_schmidt_variants_reach_tolerance(helm, reorth):
+    w = workload("2d_smooth_small")
+    ref = None
+    for mode in (1, reorth):
+        g = helm.Grid(w.n, w.h, restart=20, reorth=mode)
+        g.set_model(dev(w.slowness()), w.omega(), w.alpha)
+        g.set_shift(*w.beta)
+        fd = dev(w.rhs())
+        ud = torch.empty_like(fd)
+        _, its, rr = g.solve(fd, 1e-10, ud)
+        assert rr <= 1e-10
+        if ref is None:
+            ref = (ud.cpu().numpy(), its)
+        else:
+            assert abs(its - ref[1]) <= 2 and rel(ud.cpu().numpy(), ref[0]) < 1e-8
