@@ -180,6 +180,18 @@ const char *helm_last_error(void);
 helm_status helm_profile_start(void);
 helm_status helm_profile_stop(char *json, size_t cap);
 
+/* Times one kernel of the Arnoldi step j with the data of the grid's last
+ * solve: `reps` back-to-back launches are captured in a CUDA graph, replayed
+ * once to warm up and once between two CUDA events on the grid's stream.
+ * kernel: "multidot", "multiaxpy", "stencil_apply" (H z_j) or "vcycle"
+ * (M^-1 v_j, all its kernels). Outputs: average microseconds per launch, and
+ * the launch's algorithmic bytes and FP64 flops (0 for "vcycle"); bytes and
+ * flops64 are nullable. The basis and Hessenberg scratch of the last solve
+ * are overwritten. Errors: HELM_ERR_STATE (no solve yet), HELM_ERR_ARG,
+ * HELM_ERR_CUDA. The paper has no counterpart: this is instrumentation. */
+helm_status helm_time_kernel(helm_grid *g, const char *kernel, int j, int reps,
+                             double *us_per_launch, double *bytes, double *flops64);
+
 /* Number of kernels this library has launched in this process (all grids).
  * Used to report launch counts; not thread-safe across concurrent grids. */
 uint64_t    helm_kernel_launches(void);

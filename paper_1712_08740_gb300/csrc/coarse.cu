@@ -90,6 +90,55 @@ __global__ void k_gj_elim(cplx_t<T> *__restrict__ A, const cplx_t<T> *__restrict
     A[(size_t)i * n + j] = a;
 }
 
+// z = Ainv r for one right-hand side: one warp per row, eight independent
+// accumulators so that each lane keeps eight row loads in flight.
+template <typename T>
+__global__ void k_dense_gemv1(const cplx_t<T> *__restrict__ Ainv, int n,
+                              const cplx_t<T> *__restrict__ r, cplx_t<T> *__restrict__ z,
+                              const int *__restrict__ active) {
+    if (active && !active[0]) return;
+    // rows are split evenly over the grid (one block per SM), then over warps
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = (int)((long long)n * blockIdx.x / gridDim.x);
+    const int r1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
+    for (int i = r0 + warp; i < r1; i += (blockDim.x >> 5)) {
+    const cplx_t<T> *row = Ainv + (size_t)i * n;
+    T are[8] = {0, 0, 0, 0, 0, 0, 0, 0}, aim[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int j = lane;
+    for (; j + 224 < n; j += 256) {
+        cplx_t<T> a[8], v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            a[q] = row[j + 32 * q];
+            v[q] = r[j + 32 * q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            are[q] += a[q].x * v[q].x - a[q].y * v[q].y;
+            aim[q] += a[q].x * v[q].y + a[q].y * v[q].x;
+        }
+    }
+    for (; j < n; j += 32) {
+        const cplx_t<T> a = row[j];
+        const cplx_t<T> v = r[j];
+        are[0] += a.x * v.x - a.y * v.y;
+        aim[0] += a.x * v.y + a.y * v.x;
+    }
+    T sre = ((are[0] + are[1]) + (are[2] + are[3])) + ((are[4] + are[5]) + (are[6] + are[7]));
+    T sim = ((aim[0] + aim[1]) + (aim[2] + aim[3])) + ((aim[4] + aim[5]) + (aim[6] + aim[7]));
+    for (int o = 16; o; o >>= 1) {
+        sre += __shfl_xor_sync(0xffffffffu, sre, o);
+        sim += __shfl_xor_sync(0xffffffffu, sim, o);
+    }
+    if (lane == 0) {
+        cplx_t<T> out;
+        out.x = sre;
+        out.y = sim;
+        z[i] = out;
+    }
+    }
+}
+
 // z_k = Ainv r_k for a tile of up to kRT right-hand sides per block: each warp
 // owns one row and reads it once for all right-hand sides of the tile.
 constexpr int kRT = 4;
@@ -185,7 +234,10 @@ void launch_dense_gemv(const cplx_t<T> *Ainv, int n, const cplx_t<T> *r, size_t 
     const int warps = 8;
     dim3 g((n + warps - 1) / warps, (nb + kRT - 1) / kRT);
     prof_begin(st);
-    k_dense_gemv<T><<<g, warps * 32, 0, st>>>(Ainv, n, r, sr, z, sz, nb, active);
+    if (nb == 1)
+        k_dense_gemv1<T><<<n < 152 * 4 ? (n + 3) / 4 : 152, warps * 32, 0, st>>>(Ainv, n, r, z, active);
+    else
+        k_dense_gemv<T><<<g, warps * 32, 0, st>>>(Ainv, n, r, sr, z, sz, nb, active);
     count_launch();
     if (prof_on())
         prof_end(sizeof(T) == 8 ? "coarse_gemv_f64" : "coarse_gemv_f32", st,

@@ -40,89 +40,103 @@ __global__ void k_cycle_init(CycleState S, const double *__restrict__ nrm2, int 
         S.act_cy[r] = live;
         S.act_it[r] = live;
         S.g[(size_t)r * (S.m + 1)] = make_double2(fn, 0.0);
+        S.Q[(size_t)r * (S.m + 1) * (S.m + 1)] = make_double2(1.0, 0.0);
         any |= live;
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0 && host_flag) *(volatile int *)host_flag = any;
 }
 
-// One warp per right-hand side. The warp stages the new Hessenberg column
-// (sum of the two Gram-Schmidt passes), the rotations so far and g in shared
-// memory; lane 0 applies the j earlier rotations and builds the new one there
-// (a serial chain of O(j) shared-memory operations instead of global round
-// trips); the warp writes the rotated column back. Block-level "any right-hand
-// side still stepping" is combined across blocks with an atomic and a
-// last-block ticket, whose block publishes it to the host-mapped flag.
+// One warp per right-hand side. The product of the rotations so far is kept
+// explicitly, Q_j = G_{j-1} ... G_0 (lower Hessenberg, column-major per
+// right-hand side), so rotating the new Hessenberg column is a lane-parallel
+// product Q_j h instead of a serial chain of j rotations: on GB300 every FP64
+// warp instruction holds the SM's FP64 pipe for ~16 cycles whatever the lane
+// mask, so short dependent chains matter. Lane 0 builds the new complex
+// rotation (real cosine) from the last two entries; the warp then writes the
+// rotated column into R and the two new rows of Q. Entries of Q outside the
+// Hessenberg profile are never read, so Q needs no clearing between cycles:
+// only Q[0][0] = 1 is set when a cycle starts. "Any right-hand side still
+// stepping" is combined across blocks with an atomic and a last-block ticket,
+// whose block publishes it to the host-mapped flag.
 __global__ void k_givens(CycleState S, int j, const double2 *__restrict__ hb, int hstride, int two,
                          const double *__restrict__ nrm2, int nrhs, double tol, int max_iters,
-                         int *host_flag, int *any_dev, unsigned *ticket) {
+                         int *host_flag, int *any_dev, unsigned *ticket, int q_in_smem) {
     extern __shared__ unsigned char smem_raw[];
     const int m = S.m;
+    const int ld = m + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + warp;
-    double2 *col = reinterpret_cast<double2 *>(smem_raw) + (size_t)warp * (2 * m + 2);
-    double2 *snl = col + (m + 1);                       // m sines
-    double *csl = reinterpret_cast<double *>(reinterpret_cast<double2 *>(smem_raw) +
-                                             (size_t)(blockDim.x >> 5) * (2 * m + 2)) + (size_t)warp * m;
+    double2 *h = reinterpret_cast<double2 *>(smem_raw) + (size_t)warp * (2 * ld);
+    double2 *rot = h + ld;
+    // with one warp per block, Q_j (its Hessenberg profile) is staged in shared memory
+    double2 *Qs = (blockDim.x == 32 && q_in_smem) ? rot + ld : nullptr;
     int live = 0;
     if (r < nrhs && S.act_it[r]) {
-        double2 *R = S.R + (size_t)r * (m + 1) * m + (size_t)j * (m + 1);
-        double2 *g = S.g + (size_t)r * (m + 1);
-        double *cs = S.cs + (size_t)r * m;
-        double2 *sn = S.sn + (size_t)r * m;
+        double2 *R = S.R + (size_t)r * ld * m + (size_t)j * ld;
+        double2 *Q = S.Q + (size_t)r * ld * ld;
+        double2 *g = S.g + (size_t)r * ld;
         bool finite = true;
         for (int i = lane; i <= j; i += 32) {
             double2 v = hb[(size_t)r * hstride + i];
-            if (two) v = cadd(v, hb[(size_t)r * hstride + (m + 1) + i]);
+            if (two) v = cadd(v, hb[(size_t)r * hstride + ld + i]);
             finite = finite && isfinite(v.x) && isfinite(v.y);
-            col[i] = v;
+            h[i] = v;
         }
-        for (int i = lane; i < j; i += 32) {
-            snl[i] = sn[i];
-            csl[i] = cs[i];
-        }
-        finite = __all_sync(0xffffffffu, finite);
         const double hn = sqrt(nrm2[r]);
+        finite = __all_sync(0xffffffffu, finite) && isfinite(hn);
+        if (Qs) {
+            // columns c <= j of Q_j, rows i <= j (coalesced down each column)
+            for (int c = 0; c <= j; ++c)
+                for (int i = max(c - 1, 0) + lane; i <= j; i += 32) Qs[i + c * ld] = Q[i + (size_t)c * ld];
+        }
         __syncwarp();
-        if (!(finite && isfinite(hn))) {
+        const double2 *Qr = Qs ? Qs : Q;
+        if (!finite) {
             if (lane == 0) {
                 S.status[r] = ST_BROKE;
                 S.act_it[r] = 0;
                 S.act_cy[r] = 0;
             }
         } else {
-            int stop = 0;
-            if (lane == 0) {
-                col[j + 1] = make_double2(hn, 0.0);
-                for (int i = 0; i < j; ++i) {
-                    const double2 a = col[i], b = col[i + 1];
-                    const double c = csl[i];
-                    const double2 sv = snl[i];
-                    col[i] = cadd(cscale(c, a), cmul(sv, b));
-                    col[i + 1] = cadd(cscale(-1.0, cconjmul(sv, a)), cscale(c, b));
+            // rotated h: rot[i] = sum_{c <= min(i+1, j)} Q[i][c] h[c]
+            for (int i = lane; i <= j; i += 32) {
+                const int cmax = min(i + 1, j);
+                double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+                int c = 0;
+                for (; c + 1 <= cmax; c += 2) {
+                    a0 = cadd(a0, cmul(Qr[i + (size_t)c * ld], h[c]));
+                    a1 = cadd(a1, cmul(Qr[i + (size_t)(c + 1) * ld], h[c + 1]));
                 }
-                const double2 a = col[j], b = col[j + 1];
-                const double aa = cabs2(a), bb = cabs2(b);
-                double c;
-                double2 sv, rr;
+                if (c <= cmax) a0 = cadd(a0, cmul(Qr[i + (size_t)c * ld], h[c]));
+                rot[i] = cadd(a0, a1);
+            }
+            __syncwarp();
+            int stop = 0;
+            double cs = 0.0;
+            double2 sv = make_double2(0.0, 0.0);
+            if (lane == 0) {
+                const double2 a = rot[j];
+                const double2 b = make_double2(hn, 0.0);
+                const double aa = cabs2(a), bb = hn;
+                double2 rr;
                 if (aa == 0.0) {
-                    c = 0.0;
+                    cs = 0.0;
                     sv = make_double2(1.0, 0.0);
                     rr = b;
                 } else {
                     const double rho = hypot(aa, bb);
                     const double2 ph = cscale(1.0 / aa, a);
-                    c = aa / rho;
-                    sv = cscale(1.0 / rho, cmul(ph, make_double2(b.x, -b.y)));
+                    cs = aa / rho;
+                    sv = cscale(bb / rho, ph);                     // (a/|a|) conj(b) / rho, b real
                     rr = cscale(rho, ph);
                 }
-                cs[j] = c;
-                sn[j] = sv;
-                col[j] = rr;
-                col[j + 1] = make_double2(0.0, 0.0);
+                rot[j] = rr;
+                S.cs[(size_t)r * m + j] = cs;
+                S.sn[(size_t)r * m + j] = sv;
                 const double2 gj = g[j];
                 g[j + 1] = cscale(-1.0, cconjmul(sv, gj));
-                g[j] = cscale(c, gj);
+                g[j] = cscale(cs, gj);
                 S.k[r] = j + 1;
                 const int its = S.its[r] + 1;
                 S.its[r] = its;
@@ -130,8 +144,19 @@ __global__ void k_givens(CycleState S, int j, const double2 *__restrict__ hb, in
                 stop = (est <= tol * S.fnorm[r] || hn <= 1e-300 || its >= max_iters || j + 1 >= m);
                 if (stop) S.act_it[r] = 0;
             }
+            cs = __shfl_sync(0xffffffffu, cs, 0);
+            sv.x = __shfl_sync(0xffffffffu, sv.x, 0);
+            sv.y = __shfl_sync(0xffffffffu, sv.y, 0);
             __syncwarp();
-            for (int i = lane; i <= j + 1; i += 32) R[i] = col[i];
+            // rotated column into R (R[j+1][j] = 0)
+            for (int i = lane; i <= j + 1; i += 32) R[i] = (i <= j) ? rot[i] : make_double2(0.0, 0.0);
+            // rows j and j+1 of Q_{j+1} = G_j diag(Q_j, 1)
+            for (int c = lane; c <= j + 1; c += 32) {
+                const double2 qj = (c <= j) ? Qr[j + (size_t)c * ld] : make_double2(0.0, 0.0);
+                const double2 e = (c == j + 1) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+                Q[j + (size_t)c * ld] = cadd(cscale(cs, qj), cmul(sv, e));
+                Q[j + 1 + (size_t)c * ld] = cadd(cscale(-1.0, cconjmul(sv, qj)), cscale(cs, e));
+            }
             live = __shfl_sync(0xffffffffu, stop, 0) ? 0 : 1;
         }
     }
@@ -208,6 +233,7 @@ __global__ void k_cycle_check(CycleState S, const double *__restrict__ nrm2, int
         S.k[r] = 0;
         double2 *g = S.g + (size_t)r * (m + 1);
         g[0] = make_double2(live ? S.beta[r] : 0.0, 0.0);
+        S.Q[(size_t)r * (m + 1) * (m + 1)] = make_double2(1.0, 0.0);
         any |= live;
     }
     any = __syncthreads_or(any);
@@ -227,11 +253,15 @@ void launch_cycle_init(const CycleState &S, const double *nrm2, int nrhs, int *h
 void launch_givens(const CycleState &S, int j, const double2 *hb, int hstride, int two,
                    const double *nrm2, int nrhs, double tol, int max_iters, int *host_flag,
                    cudaStream_t st) {
-    const int warps = 4;
-    const size_t sm = (size_t)warps * ((2 * S.m + 2) * sizeof(double2) + S.m * sizeof(double));
+    // small batches: one warp per block with Q_j staged in shared memory
+    const size_t ld = S.m + 1;
+    const size_t qsm = (2 * ld + ld * ld) * sizeof(double2);
+    const bool qs = nrhs <= 2 * 152 && qsm <= 96 * 1024;
+    const int warps = qs ? 1 : 4;
+    const size_t sm = qs ? qsm : (size_t)warps * 2 * ld * sizeof(double2);
     prof_begin(st);
     k_givens<<<(nrhs + warps - 1) / warps, warps * 32, sm, st>>>(
-        S, j, hb, hstride, two, nrm2, nrhs, tol, max_iters, host_flag, S.any_dev, S.ticket);
+        S, j, hb, hstride, two, nrm2, nrhs, tol, max_iters, host_flag, S.any_dev, S.ticket, qs ? 1 : 0);
     count_launch();
     if (prof_on()) prof_end("givens", st, 0.0, 0.0);
 }
@@ -248,7 +278,7 @@ void launch_backsolve(const CycleState &S, double2 *y, int nrhs, cudaStream_t st
 
 void prepare_cycle_kernels() {
     cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 8192);
-    cudaFuncSetAttribute(k_givens, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_givens, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 8192);
 }
 
 void launch_cycle_check(const CycleState &S, const double *nrm2, int nrhs, double tol,

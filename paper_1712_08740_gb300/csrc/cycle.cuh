@@ -14,6 +14,7 @@ struct CycleState {
     double2 *g;            // [nrhs][m+1] rotated right-hand side of the least-squares problem
     double *cs;            // [nrhs][m] Givens cosines
     double2 *sn;           // [nrhs][m] Givens sines
+    double2 *Q;            // [nrhs][(m+1) x (m+1)] product of the rotations, column-major
     double *fnorm;         // [nrhs] ||f||
     double *beta;          // [nrhs] ||r|| at the start of the cycle
     double *relres;        // [nrhs] last true relative residual

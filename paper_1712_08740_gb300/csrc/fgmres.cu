@@ -18,6 +18,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "cycle.cuh"
@@ -60,7 +61,7 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
         (s = g->cfn.ensure(R * sizeof(double))) || (s = g->cbeta.ensure(R * sizeof(double))) ||
         (s = g->crel.ensure(R * sizeof(double))) || (s = g->ck.ensure(R * sizeof(int))) ||
         (s = g->cits.ensure(R * sizeof(int))) || (s = g->cstat.ensure(R * sizeof(int))) ||
-        (s = g->cany.ensure(64)))
+        (s = g->cany.ensure(64)) || (s = g->cQ.ensure(R * nv * nv * sizeof(double2))))
         return s;
     cudaMemsetAsync(g->cany.p, 0, 64, g->st);
     prepare_cycle_kernels();
@@ -93,6 +94,7 @@ CycleState cycle_state(helm_grid *g) {
     S.g = g->cg.as<double2>();
     S.cs = g->ccs.as<double>();
     S.sn = g->csn.as<double2>();
+    S.Q = g->cQ.as<double2>();
     S.fnorm = g->cfn.as<double>();
     S.beta = g->cbeta.as<double>();
     S.relres = g->crel.as<double>();
@@ -273,6 +275,7 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
     const LevelView<double> L0 = level_view<double>(g, 0);
     const bool graphs = g->use_graphs;
     if (graphs && (s = capture_steps(g, nrhs, tol))) return s;
+    g->last_nrhs = nrhs;
 
     // non-finite input check, x = 0, v_0 = f, ||f||, flags
     int *flag = g->flag.as<int>();
@@ -517,3 +520,90 @@ helm_status helm_true_residual(helm_grid *g, const helm_c128 *f, const helm_c128
 }
 
 }  // extern "C"
+
+extern "C" helm_status helm_time_kernel(helm_grid *g, const char *kernel, int j, int reps,
+                                        double *us_per_launch, double *bytes, double *flops64) {
+    clear_error();
+    if (!g || !kernel || !us_per_launch || reps < 1) return fail(HELM_ERR_ARG, "bad argument");
+    if (!g->ready || g->last_nrhs < 1 || g->cap_rhs < g->last_nrhs)
+        return fail(HELM_ERR_STATE, "run a solve on this grid first");
+    const int m = g->opt.restart;
+    if (j < 0 || j >= m) return fail(HELM_ERR_ARG, "step j must be in [0, restart)");
+    const int nrhs = g->last_nrhs;
+    const size_t N = g->N;
+    const int nv = m + 1;
+    const size_t sV = (size_t)nv * N;
+    KrylovScratch ks = scratch(g);
+    double2 *V = g->V.as<double2>();
+    double2 *hb = g->hbuf.as<double2>();
+    double *nrm = g->nrm.as<double>();
+    const int nvec = j + 1;
+    const std::string name(kernel);
+    double b = 0.0, fl = 0.0;
+    auto one = [&]() -> bool {
+        if (name == "multidot") {
+            launch_multidot(V, sV, nvec, V + (size_t)(j + 1) * N, sV, N, hb, 2 * nv, nrhs, nullptr, ks, g->st);
+            b = (nvec + 1.0) * N * 16.0 * nrhs;
+            fl = 8.0 * nvec * N * nrhs;
+        } else if (name == "multiaxpy") {
+            launch_multiaxpy(V, sV, nvec, hb, 2 * nv, V + (size_t)(j + 1) * N, sV, N, nrm, nrhs, nullptr,
+                             ks, g->st);
+            b = (nvec + 2.0) * N * 16.0 * nrhs;
+            fl = (8.0 * nvec + 4.0) * N * nrhs;
+        } else if (name == "stencil_apply") {
+            apply_H_j(g, j, nrhs, nullptr);
+            const double zb = (g->opt.precond == HELM_PRECOND_NONE || g->opt.precision == HELM_PREC_F64) ? 16.0 : 8.0;
+            b = (zb + 16.0 + 8.0) * N * nrhs;
+            fl = (4.0 * g->dim + 12.0) * N * nrhs;
+        } else if (name == "vcycle") {
+            if (g->opt.precond == HELM_PRECOND_NONE) return false;
+            apply_precond_j(g, j, nrhs, nullptr);
+            b = 0.0;
+            fl = 0.0;
+        } else {
+            return false;
+        }
+        return true;
+    };
+    // one untimed launch (checks the name), then a graph of `reps` launches
+    if (!one()) return fail(HELM_ERR_ARG, "unknown kernel '%s'", kernel);
+    helm_status s;
+    if ((s = sync_stream(g, "helm_time_kernel"))) return s;
+    if (!g->cap_st && cudaStreamCreateWithFlags(&g->cap_st, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(HELM_ERR_CUDA, "capture stream");
+    cudaStream_t keep = g->st;
+    g->st = g->cap_st;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const uint64_t l0 = launch_count();
+    cudaError_t e = cudaStreamBeginCapture(g->cap_st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < reps; ++k) one();
+        e = cudaStreamEndCapture(g->cap_st, &graph);
+    }
+    const uint64_t per = (launch_count() - l0) / (uint64_t)reps;
+    uncount_launch(launch_count() - l0);
+    g->st = keep;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(HELM_ERR_CUDA, "kernel timing graph: %s", cudaGetErrorString(e));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaGraphLaunch(exec, g->st);            // warm
+    cudaEventRecord(e0, g->st);
+    cudaGraphLaunch(exec, g->st);
+    cudaEventRecord(e1, g->st);
+    count_launch(2 * per * (uint64_t)reps);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) return fail(HELM_ERR_CUDA, "kernel timing: %s", cudaGetErrorString(e));
+    *us_per_launch = ms * 1e3 / reps;
+    if (bytes) *bytes = b;
+    if (flops64) *flops64 = fl;
+    return HELM_OK;
+}

@@ -58,7 +58,7 @@ struct helm_grid {
     // Krylov workspace
     int cap_rhs = 0, cap_m = 0, cap_prec = -1;
     helm::DevBuf V, Z, Zin, hbuf, nrm, yv, partial, counter, act_it, act_cy, act2, flag;
-    helm::DevBuf cR, cg, ccs, csn, cfn, cbeta, crel, ck, cits, cstat, cany;   // FGMRES state
+    helm::DevBuf cR, cg, ccs, csn, cfn, cbeta, crel, ck, cits, cstat, cany, cQ;   // FGMRES state
     helm::DevBuf fst, ust, xst, yst;    // staging for host pointers / helper vectors
     int *hflag = nullptr;               // host-mapped "any right-hand side active" flag
     std::vector<cudaEvent_t> ring;      // look-ahead events of the Arnoldi loop
@@ -70,4 +70,5 @@ struct helm_grid {
     long long graph_key = -1;
     cudaStream_t cap_st = nullptr;      // private stream used only for capture
     bool use_graphs = true;
+    int last_nrhs = 0;                  // batch size of the last solve (kernel timing)
 };

@@ -74,7 +74,8 @@ k_multidot(const double2 *__restrict__ V, size_t sV, int nvec, const double2 *__
     if (active && !active[r]) return;
     V += r * sV;
     w += r * sw;
-    double2 *part = partial + ((size_t)r * gridDim.x + blockIdx.x) * nvec_max;
+    // partials transposed, [rhs][vector][block], so the last block reads them coalesced
+    double2 *part = partial + (size_t)r * nvec_max * gridDim.x + blockIdx.x;
     __shared__ double2 red[kWarps][kMaxVec];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t step = (size_t)gridDim.x * kThreads;
@@ -116,14 +117,14 @@ k_multidot(const double2 *__restrict__ V, size_t sV, int nvec, const double2 *__
             s.x += red[q][i].x;
             s.y += red[q][i].y;
         }
-        part[i] = s;
+        part[(size_t)i * gridDim.x] = s;
     }
     if (last_block(counter + r)) {
-        const double2 *pr = partial + (size_t)r * gridDim.x * nvec_max;
+        const double2 *pr = partial + (size_t)r * nvec_max * gridDim.x;
         for (int i = warp; i < nvec; i += kWarps) {
             double sx = 0.0, sy = 0.0;
             for (unsigned b = lane; b < gridDim.x; b += 32) {
-                const double2 v = pr[(size_t)b * nvec_max + i];
+                const double2 v = pr[(size_t)i * gridDim.x + b];
                 sx += v.x;
                 sy += v.y;
             }
@@ -307,6 +308,16 @@ __global__ void k_finite(const double *__restrict__ x, size_t n, int *__restrict
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// Reduction grids are whole multiples of the SM count (152 on GB300): one,
+// two, four or eight blocks per SM, so that no SM runs an extra block while
+// the others idle, with roughly `per_thread` points per thread.
+inline int sm_blocks_for(size_t N, int per_thread, int cap) {
+    const size_t per_wave = (size_t)152 * kThreads * per_thread;
+    int k = 1;
+    while (k < 8 && (size_t)k * per_wave < N && 152 * 2 * k <= cap) k *= 2;
+    return 152 * k <= cap ? 152 * k : cap;
+}
+
 inline int blocks_for(size_t N, int per_block, int cap) {
     size_t b = (N + per_block - 1) / per_block;
     if (b < 1) b = 1;
@@ -318,7 +329,7 @@ inline int blocks_for(size_t N, int per_block, int cap) {
 void launch_multidot(const double2 *V, size_t sV, int nvec, const double2 *w, size_t sw,
                      size_t N, double2 *out, size_t out_stride, int nrhs, const int *active,
                      KrylovScratch &ks, cudaStream_t st) {
-    const int nb = blocks_for(N, kThreads * 2, ks.max_blocks);
+    const int nb = sm_blocks_for(N, 2, ks.max_blocks);
     prof_begin(st);
     k_multidot<<<dim3(nb, nrhs), kThreads, 0, st>>>(V, sV, nvec, w, sw, N, out, out_stride,
                                                     ks.partial, ks.counter, ks.nvec_max, active);
@@ -330,7 +341,7 @@ void launch_multidot(const double2 *V, size_t sV, int nvec, const double2 *w, si
 void launch_multiaxpy(const double2 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
                       double2 *w, size_t sw, size_t N, double *norm2, int nrhs,
                       const int *active, KrylovScratch &ks, cudaStream_t st) {
-    const int nb = blocks_for(N, kThreads, ks.max_blocks);
+    const int nb = sm_blocks_for(N, 2, ks.max_blocks);
     prof_begin(st);
     k_multiaxpy<<<dim3(nb, nrhs), kThreads, 0, st>>>(V, sV, nvec, c, c_stride, w, sw, N, norm2,
                                                      (double *)ks.partial, ks.counter, active);
@@ -342,7 +353,7 @@ void launch_multiaxpy(const double2 *V, size_t sV, int nvec, const double2 *c, s
 
 void launch_norm2(const double2 *x, size_t sx, size_t N, double *norm2, int nrhs,
                   const int *active, KrylovScratch &ks, cudaStream_t st) {
-    const int nb = blocks_for(N, kThreads * 2, ks.max_blocks);
+    const int nb = sm_blocks_for(N, 4, ks.max_blocks);
     prof_begin(st);
     k_norm2<<<dim3(nb, nrhs), kThreads, 0, st>>>(x, sx, N, norm2, (double *)ks.partial,
                                                  ks.counter, active);

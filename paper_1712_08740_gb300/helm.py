@@ -28,7 +28,8 @@ EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "he
             "helm_set_options", "helm_get_options", "helm_set_model", "helm_set_shift",
             "helm_solve", "helm_solve_batch", "helm_apply_H", "helm_apply_M",
             "helm_apply_precond", "helm_true_residual", "helm_num_levels", "helm_level_info",
-            "helm_last_error", "helm_kernel_launches", "helm_profile_start", "helm_profile_stop")
+            "helm_last_error", "helm_kernel_launches", "helm_profile_start", "helm_profile_stop",
+            "helm_time_kernel")
 
 
 class helm_options(ctypes.Structure):
@@ -71,6 +72,8 @@ def _load():
         "helm_kernel_launches": (ctypes.c_uint64, []),
         "helm_profile_start": (I, []),
         "helm_profile_stop": (I, [ctypes.c_char_p, ctypes.c_size_t]),
+        "helm_time_kernel": (I, [P, ctypes.c_char_p, I, I, ctypes.POINTER(D), ctypes.POINTER(D),
+                                 ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -214,6 +217,14 @@ def helm_profile_stop():
     return json.loads(buf.value.decode())
 
 
+def helm_time_kernel(g, kernel, j, reps):
+    """(microseconds per launch, algorithmic bytes, FP64 flops) of one kernel."""
+    us, b, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.helm_time_kernel(g, kernel.encode(), int(j), int(reps), ctypes.byref(us),
+                                 ctypes.byref(b), ctypes.byref(fl)))
+    return us.value, b.value, fl.value
+
+
 # ------------------------------------------------------------------ convenience wrapper
 
 class Grid:
@@ -269,6 +280,9 @@ class Grid:
 
     def true_residual(self, f, u):
         return helm_true_residual(self._g, f, u)
+
+    def time_kernel(self, kernel, j, reps=50):
+        return helm_time_kernel(self._g, kernel, j, reps)
 
     @property
     def num_levels(self):
