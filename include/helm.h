@@ -162,6 +162,33 @@ helm_status helm_apply_precond(helm_grid *g, const helm_c128 *r, helm_c128 *z);
 helm_status helm_true_residual(helm_grid *g, const helm_c128 *f, const helm_c128 *u,
                                double *rel);
 
+/* Allocation-free variant of helm_true_residual for nrhs right-hand sides:
+ * rel[k] = ||f_k - H u_k||_2 / ||f_k||_2 in complex128, f_k and u_k at
+ * offset k*N of the device arrays f and u (both must be device pointers of
+ * the current device; nothing is staged). The paper has no counterpart.
+ *
+ * Who needs it: callers that cannot call cudaMalloc -- code running while a
+ * stream is captured into a CUDA graph (allocation cannot be captured and
+ * breaks the capture), services that hand out device memory from their own
+ * fixed budget, and latency-critical loops that must not wait on the
+ * allocator. helm_true_residual may allocate staging and reduction buffers on
+ * first use; this entry point allocates nothing (no cudaMalloc or cudaFree, no
+ * allocating library call). Its scratch is one static device array of
+ * 305 KiB inside the library, which every GPU that loads the library holds until
+ * the process exits. Limits and behaviour:
+ *  - nrhs must be 1..64 (the size of that array); larger values return
+ *    HELM_ERR_ARG;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - every call shares the array: calls whose work overlaps on the GPU (for
+ *    example on two streams at once) race and give wrong results; calls in
+ *    sequence on one stream are safe (each call clears what must start at 0);
+ *  - it synchronises the grid's stream to return rel on the host.
+ * Errors: HELM_ERR_ARG, HELM_ERR_STATE (no model), HELM_ERR_CUDA. */
+helm_status helm_true_residual_noalloc(helm_grid *g, int nrhs, const helm_c128 *f,
+                                       const helm_c128 *u, double *rel);
+
 /* Number of multigrid levels (1 = no coarsening; 0 before helm_set_shift)
  * and the node counts and spacing of one level. */
 int         helm_num_levels(const helm_grid *g);

@@ -29,7 +29,7 @@ EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "he
             "helm_solve", "helm_solve_batch", "helm_apply_H", "helm_apply_M",
             "helm_apply_precond", "helm_true_residual", "helm_num_levels", "helm_level_info",
             "helm_last_error", "helm_kernel_launches", "helm_profile_start", "helm_profile_stop",
-            "helm_time_kernel")
+            "helm_time_kernel", "helm_true_residual_noalloc")
 
 
 class helm_options(ctypes.Structure):
@@ -74,6 +74,7 @@ def _load():
         "helm_profile_stop": (I, [ctypes.c_char_p, ctypes.c_size_t]),
         "helm_time_kernel": (I, [P, ctypes.c_char_p, I, I, ctypes.POINTER(D), ctypes.POINTER(D),
                                  ctypes.POINTER(D)]),
+        "helm_true_residual_noalloc": (I, [P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -184,6 +185,16 @@ def helm_true_residual(g, f, u):
     _check(_lib.helm_true_residual(g, _ptr(f, np.complex128), _ptr(u, np.complex128),
                                    ctypes.byref(rel)))
     return rel.value
+
+
+def helm_true_residual_noalloc(g, nrhs, f, u):
+    """Relative residuals of nrhs device-resident pairs (f_k, u_k), computed by
+    the library without allocating device memory (see include/helm.h)."""
+    rel = np.zeros(int(nrhs), dtype=np.float64)
+    _check(_lib.helm_true_residual_noalloc(g, int(nrhs), _ptr(f, np.complex128),
+                                           _ptr(u, np.complex128),
+                                           rel.ctypes.data_as(ctypes.c_void_p)))
+    return rel
 
 
 def helm_num_levels(g):
