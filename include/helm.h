@@ -197,6 +197,75 @@ helm_status helm_level_info(const helm_grid *g, int level, int64_t n_out[3], dou
 /* Message for the last failed call on this thread ("" if none). */
 const char *helm_last_error(void);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop for streams of independent solves (different grids,
+ * frequencies, media and source counts). A dispatcher admits queued requests
+ * in arrival order (FIFO) to `workers` worker threads, each with its own CUDA
+ * stream, when the device memory all admitted requests hold fits
+ * `memory_budget` (footprints from helm_solve_footprint; idle workers drop
+ * their cached grids to make room). Workers keep one grid resident between
+ * requests of the same size. Requests on different workers run concurrently
+ * and their kernels overlap on the device; each request's right-hand sides
+ * are solved together by helm_solve_batch. The paper has no counterpart: it
+ * solves one problem at a time. */
+typedef struct helm_server helm_server;
+
+typedef struct {
+    int workers;             /* requests in flight at once (1..64)                     */
+    size_t memory_budget;    /* device bytes all admitted requests may hold together  */
+    helm_options options;    /* solver options for every request                      */
+    double beta1, beta2;     /* shift of M (Eq. 6), as in helm_set_shift              */
+} helm_server_config;
+
+typedef struct {
+    int dim;                 /* 1, 2 or 3                                              */
+    int64_t n[3];            /* nodes per axis (unused axes 1)                         */
+    double h;                /* spacing, m                                             */
+    const double *m;         /* slowness, host, N values; copied by helm_server_submit */
+    double omega, alpha;     /* angular frequency, damping (Eq. 2)                     */
+    int nrhs;                /* right-hand sides                                       */
+    const helm_c128 *f;      /* host, nrhs x N; copied by helm_server_submit           */
+    double tol;              /* true relative residual to reach                        */
+} helm_request;
+
+typedef struct {
+    uint64_t id;
+    helm_status status;
+    int nrhs;
+    int iterations_max;            /* over the request's right-hand sides          */
+    double true_rel_residual_max;
+    double t_submit, t_admit, t_done;   /* seconds on the server clock             */
+    size_t footprint_bytes;        /* device bytes it was admitted with            */
+} helm_result;
+
+/* Device bytes a solve of nrhs right-hand sides on an n grid holds under `opt`
+ * (an upper estimate: basis x restart, multigrid work vectors, coefficients,
+ * coarse inverse, staging). 0 on bad arguments. */
+size_t helm_solve_footprint(int dim, const int64_t n[3], int nrhs, const helm_options *opt);
+
+/* Creates the server on the current device and starts its threads.
+ * Errors: HELM_ERR_ARG, HELM_ERR_CUDA. */
+helm_status helm_server_create(const helm_server_config *cfg, helm_server **out);
+
+/* Queues a request and returns its id at once. u: host buffer of nrhs x N
+ * complex values that receives the solutions; it must stay valid until the
+ * request is done. Errors: HELM_ERR_ARG. */
+helm_status helm_server_submit(helm_server *s, const helm_request *req, helm_c128 *u, uint64_t *id);
+
+/* Waits for request `id`, fills *res and forgets the request. Returns the
+ * request's own status (HELM_ERR_NOMEM if its footprint can never fit the
+ * budget). Errors: HELM_ERR_ARG (unknown id). */
+helm_status helm_server_wait(helm_server *s, uint64_t id, helm_result *res);
+
+/* *done = 1 once request `id` has finished (its u is then written). */
+helm_status helm_server_poll(helm_server *s, uint64_t id, int *done);
+
+/* Seconds since the server was created (the clock of helm_result times). */
+double helm_server_clock(const helm_server *s);
+
+/* Finishes the running requests, stops the threads and frees every grid. */
+void helm_server_destroy(helm_server *s);
+
 /* Per-kernel timing. helm_profile_start() turns on CUDA-event timing of every
  * launch the library makes (process-wide, all grids; it adds two event
  * records per launch). helm_profile_stop() waits for those events, turns the

@@ -103,9 +103,11 @@ helm_status build_hierarchy(helm_grid *g) {
                     "coarsest level has %zu nodes (> 4096): grid axes must be odd so that "
                     "(n+1)/2 coarsening reaches coarse_max",
                     Nc);
-    // keep level 0 (its m/w were set by helm_set_model), rebuild the rest
-    g->lv.resize(1);
-    for (size_t l = 1; l < dims.size(); ++l) g->lv.emplace_back();
+    // keep level 0 (its m/w were set by helm_set_model); coarser levels keep their
+    // buffers when the level count is unchanged (no cudaFree, which would
+    // synchronise the whole device and stall other grids' streams)
+    if (g->lv.size() > dims.size()) g->lv.resize(dims.size());
+    while (g->lv.size() < dims.size()) g->lv.emplace_back();
     for (size_t l = 0; l < dims.size(); ++l) {
         MGLevel &L = g->lv[l];
         for (int a = 0; a < 3; ++a) L.n[a] = dims[l][a];

@@ -17,6 +17,7 @@
 // flag written by the Givens kernel, and synchronises once per cycle.
 #include <cmath>
 #include <complex>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -83,7 +84,6 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
     g->cap_rhs = nrhs;
     g->cap_m = m;
     g->cap_prec = prec;
-    g->graph_key = -1;
     return HELM_OK;
 }
 
@@ -193,19 +193,26 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
 }
 
 long long graph_key_of(const helm_grid *g, int nrhs, double tol) {
-    // everything baked into the captured kernels' arguments
-    long long k = nrhs;
-    k = k * 257 + g->opt.restart;
-    k = k * 3 + g->opt.precond;
-    k = k * 2 + g->opt.precision;
-    k = k * 17 + g->opt.nu1;
-    k = k * 17 + g->opt.nu2;
-    k = k * 3 + g->opt.reorth;
-    k ^= (long long)std::llround(g->opt.omega_jacobi * 1e6) << 20;
-    k ^= (long long)std::llround(-std::log10(tol) * 1e3) << 40;
-    k ^= (long long)g->opt.max_iters << 8;
-    k = k * 2 + (prof_on() ? 1 : 0);
-    return k;
+    // everything baked into the captured kernels' arguments: sizes, options,
+    // the shift and damping, and every device buffer address (FNV-1a mix)
+    unsigned long long ph = 1469598103934665603ull;
+    auto mixu = [&](unsigned long long v) { ph = (ph ^ v) * 1099511628211ull; };
+    auto mixp = [&](const void *p) { mixu((unsigned long long)(uintptr_t)p); };
+    auto mixd = [&](double d) { unsigned long long b; memcpy(&b, &d, 8); mixu(b); };
+    mixp(g->V.p); mixp(g->Z.p); mixp(g->hbuf.p); mixp(g->nrm.p); mixp(g->partial.p); mixp(g->counter.p);
+    mixp(g->act_it.p); mixp(g->act_cy.p); mixp(g->act2.p); mixp(g->Ainv.p); mixp(g->hflag);
+    mixp(g->cR.p); mixp(g->cg.p); mixp(g->ccs.p); mixp(g->csn.p); mixp(g->cQ.p); mixp(g->cfn.p);
+    mixp(g->ck.p); mixp(g->cits.p); mixp(g->cstat.p); mixp(g->cany.p);
+    for (const auto &L : g->lv) {
+        mixp(L.w64.p); mixp(L.w32.p); mixp(L.u.p); mixp(L.t.p); mixp(L.b.p); mixp(L.r.p);
+        mixu((unsigned long long)L.N);
+    }
+    mixu(g->lv.size()); mixu((unsigned long long)g->nc);
+    mixd(g->alpha); mixd(g->beta1); mixd(g->beta2); mixd(g->opt.omega_jacobi); mixd(tol);
+    mixu((unsigned long long)nrhs); mixu(g->opt.restart); mixu(g->opt.precond); mixu(g->opt.precision);
+    mixu(g->opt.nu1); mixu(g->opt.nu2); mixu(g->opt.reorth); mixu(g->opt.max_iters);
+    mixu(prof_on() ? 1u : 0u);
+    return (long long)(ph & 0x7fffffffffffffffull);
 }
 
 void drop_graphs(helm_grid *g) {

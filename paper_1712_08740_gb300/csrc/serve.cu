@@ -1,0 +1,377 @@
+// Serving front end: a request loop that solves Helmholtz problems of
+// different grid sizes, frequencies, media and source counts as they arrive.
+//
+// Design. A dispatcher thread takes requests from a FIFO queue and hands each
+// to an idle worker. Every worker owns a CUDA stream and keeps one grid (model
+// buffers, multigrid hierarchy, Krylov basis, captured step graphs) resident
+// between requests of the same size, so a request only pays for its own model
+// upload and coarse-grid factorisation. Admission is by device memory: a
+// request's footprint (Krylov basis x restart length, multigrid work vectors,
+// coefficients, coarse inverse, staging) is computed up front, and the head of
+// the queue is admitted only when the footprints held by all workers plus its
+// own fit the budget; idle workers drop their cached grids when that makes
+// room. Requests that arrive while others are on the GPU start as soon as a
+// worker and memory free up, and their kernels overlap on the device with the
+// others' (independent streams). All right-hand sides of a request are solved
+// together by the batched solver.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "vcycle.cuh"
+
+namespace helm {
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Req {
+    uint64_t id = 0;
+    int dim = 2;
+    int n[3] = {1, 1, 1};
+    double h = 0.0;
+    std::vector<double> m;
+    double omega = 0.0, alpha = 0.0;
+    int nrhs = 0;
+    std::vector<double2> f;
+    double tol = 0.0;
+    helm_c128 *u_out = nullptr;
+    size_t footprint = 0;
+    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    helm_status status = HELM_OK;
+    int its_max = 0;
+    double rel_max = 0.0;
+    bool done = false;
+    std::string err;
+};
+
+struct Worker {
+    std::thread th;
+    cudaStream_t st = nullptr;
+    helm_grid *grid = nullptr;
+    int gdim = 0, gn[3] = {0, 0, 0};
+    double gh = 0.0;
+    size_t held = 0;            // bytes held by the cached grid (or the running job)
+    std::shared_ptr<Req> job;
+    bool busy = false;
+};
+
+bool same_grid(const Worker &w, const Req &r) {
+    return w.grid && w.gdim == r.dim && w.gn[0] == r.n[0] && w.gn[1] == r.n[1] && w.gn[2] == r.n[2] &&
+           w.gh == r.h;
+}
+
+}  // namespace
+
+// Device bytes a solve of nrhs right-hand sides on this grid holds (upper estimate).
+size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o) {
+    const double N = (double)n[0] * n[1] * n[2];
+    const int m = o.restart;
+    const double zsz = (o.precond == HELM_PRECOND_NONE) ? 0.0 : (o.precision == HELM_PREC_F64 ? 16.0 : 8.0);
+    const double csz = (o.precision == HELM_PREC_F64) ? 16.0 : 8.0;
+    // coarsest level size by the same rule as the hierarchy
+    int c[3] = {n[0], n[1], n[2]};
+    double levels_sum = 0.0;
+    while (true) {
+        const double Nl = (double)c[0] * c[1] * c[2];
+        levels_sum += Nl;
+        bool odd = true;
+        for (int a = 0; a < dim; ++a) odd = odd && c[a] >= 3 && (c[a] % 2) == 1;
+        if (o.precond != HELM_PRECOND_MG || Nl <= o.coarse_max || !odd) break;
+        for (int a = 0; a < dim; ++a) c[a] = (c[a] + 1) / 2;
+    }
+    const double nc = (double)c[0] * c[1] * c[2];
+    double b = 0.0;
+    b += nrhs * (m + 1.0) * N * 16.0;                    // basis V
+    b += nrhs * (double)m * N * zsz;                     // preconditioned vectors Z
+    b += 4.0 * nrhs * levels_sum * csz;                  // V-cycle work vectors
+    b += levels_sum * (8.0 + 8.0 + 4.0);                 // slowness, coefficients
+    if (o.precond != HELM_PRECOND_NONE) b += nc * nc * csz + nc * csz;   // coarse inverse
+    b += 2.0 * nrhs * N * 16.0;                          // staging of host f and u
+    b += (double)nrhs * (m + 1.0) * (m + 1.0) * 16.0 * 3.0;   // Hessenberg, rotations
+    b += (double)nrhs * (m + 1.0) * kMaxBlocks * 16.0;   // reduction partials
+    b += 1 << 20;                                        // small buffers
+    return (size_t)b;
+}
+
+}  // namespace helm
+
+struct helm_server {
+    std::mutex mu;
+    std::condition_variable cv_disp, cv_done, cv_work;
+    std::deque<std::shared_ptr<helm::Req>> queue;
+    std::map<uint64_t, std::shared_ptr<helm::Req>> reqs;
+    std::vector<std::unique_ptr<helm::Worker>> workers;
+    size_t budget = 0;
+    helm_options opt{};
+    double beta1 = 1.0, beta2 = 0.5;
+    bool stop = false;
+    uint64_t next_id = 1;
+    int device = 0;
+    std::thread dispatcher;
+    helm::clk::time_point t0;
+    double now() const { return std::chrono::duration<double>(helm::clk::now() - t0).count(); }
+};
+
+namespace helm {
+namespace {
+
+void run_job(helm_server *S, Worker &w, Req &r) {
+    helm_status s = HELM_OK;
+    if (!same_grid(w, r)) {
+        if (w.grid) helm_destroy_grid(w.grid);
+        w.grid = nullptr;
+        int64_t n64[3] = {r.n[0], r.n[1], r.n[2]};
+        s = helm_create_grid(r.dim, n64, r.h, &w.grid);
+        if (s == HELM_OK) {
+            w.gdim = r.dim;
+            for (int a = 0; a < 3; ++a) w.gn[a] = r.n[a];
+            w.gh = r.h;
+            s = helm_set_stream(w.grid, w.st);
+        }
+    }
+    if (s == HELM_OK) s = helm_set_options(w.grid, &S->opt);
+    if (s == HELM_OK) s = helm_set_model(w.grid, r.m.data(), r.omega, r.alpha);
+    if (s == HELM_OK) s = helm_set_shift(w.grid, S->beta1, S->beta2);
+    std::vector<int> its(r.nrhs, 0);
+    std::vector<double> rel(r.nrhs, 0.0);
+    if (s == HELM_OK)
+        s = helm_solve_batch(w.grid, r.nrhs, reinterpret_cast<const helm_c128 *>(r.f.data()), r.tol,
+                             r.u_out, its.data(), rel.data());
+    r.status = s;
+    if (s != HELM_OK) r.err = helm_last_error();
+    for (int k = 0; k < r.nrhs; ++k) {
+        r.its_max = std::max(r.its_max, its[k]);
+        r.rel_max = std::max(r.rel_max, rel[k]);
+    }
+    if (s != HELM_OK && s != HELM_ERR_NOT_CONVERGED && w.grid) {   // do not keep a grid in a bad state
+        helm_destroy_grid(w.grid);
+        w.grid = nullptr;
+    }
+    r.f.clear();
+    r.f.shrink_to_fit();
+}
+
+void worker_loop(helm_server *S, Worker *w) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        S->cv_work.wait(lk, [&] { return S->stop || w->job != nullptr; });
+        if (!w->job) break;
+        std::shared_ptr<Req> r = w->job;
+        lk.unlock();
+        run_job(S, *w, *r);
+        lk.lock();
+        r->t_done = S->now();
+        r->done = true;
+        w->job = nullptr;
+        w->busy = false;
+        w->held = w->grid ? std::max(w->held, r->footprint) : 0;
+        S->cv_done.notify_all();
+        S->cv_disp.notify_all();
+    }
+    if (w->grid) helm_destroy_grid(w->grid);
+    w->grid = nullptr;
+}
+
+void dispatch_loop(helm_server *S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        if (S->queue.empty()) {
+            S->cv_disp.wait(lk);
+            continue;
+        }
+        std::shared_ptr<Req> r = S->queue.front();
+        // idle worker, preferring one whose resident grid has this size
+        Worker *pick = nullptr;
+        for (auto &w : S->workers)
+            if (!w->busy && same_grid(*w, *r)) { pick = w.get(); break; }
+        if (!pick)
+            for (auto &w : S->workers)
+                if (!w->busy && (!pick || w->held < pick->held)) pick = w.get();
+        if (!pick) {
+            S->cv_disp.wait(lk);
+            continue;
+        }
+        const bool reuse = same_grid(*pick, *r);
+        const size_t need = reuse ? std::max(pick->held, r->footprint) : r->footprint;
+        size_t others = 0;
+        for (auto &w : S->workers)
+            if (w.get() != pick) others += w->held;
+        if (others + need > S->budget) {
+            // make room by dropping grids cached by idle workers
+            for (auto &w : S->workers) {
+                if (w.get() == pick || w->busy || !w->grid) continue;
+                helm_destroy_grid(w->grid);
+                w->grid = nullptr;
+                others -= w->held;
+                w->held = 0;
+                if (others + need <= S->budget) break;
+            }
+        }
+        if (others + need > S->budget) {
+            if (others == 0) {   // can never fit: reject instead of waiting forever
+                S->queue.pop_front();
+                r->status = HELM_ERR_NOMEM;
+                r->err = "request footprint exceeds the server's memory budget";
+                r->t_admit = r->t_done = S->now();
+                r->done = true;
+                S->cv_done.notify_all();
+                continue;
+            }
+            S->cv_disp.wait(lk);   // wait for a running request to release memory
+            continue;
+        }
+        if (!reuse && pick->grid) {
+            helm_destroy_grid(pick->grid);
+            pick->grid = nullptr;
+        }
+        S->queue.pop_front();
+        r->t_admit = S->now();
+        pick->held = need;
+        pick->busy = true;
+        pick->job = r;
+        S->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+}  // namespace helm
+
+using namespace helm;
+
+extern "C" {
+
+helm_status helm_server_create(const helm_server_config *cfg, helm_server **out) {
+    clear_error();
+    if (!cfg || !out) return fail(HELM_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (cfg->workers < 1 || cfg->workers > 64) return fail(HELM_ERR_ARG, "workers must be 1..64");
+    if (cfg->memory_budget == 0) return fail(HELM_ERR_ARG, "memory_budget must be > 0");
+    auto *S = new helm_server();
+    S->budget = cfg->memory_budget;
+    S->opt = cfg->options;
+    S->beta1 = cfg->beta1;
+    S->beta2 = cfg->beta2;
+    S->t0 = clk::now();
+    cudaGetDevice(&S->device);
+    for (int i = 0; i < cfg->workers; ++i) {
+        auto w = std::make_unique<Worker>();
+        if (cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto &x : S->workers) cudaStreamDestroy(x->st);
+            delete S;
+            return fail(HELM_ERR_CUDA, "stream creation");
+        }
+        S->workers.push_back(std::move(w));
+    }
+    for (auto &w : S->workers) w->th = std::thread(worker_loop, S, w.get());
+    S->dispatcher = std::thread(dispatch_loop, S);
+    *out = S;
+    return HELM_OK;
+}
+
+void helm_server_destroy(helm_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_disp.notify_all();
+    S->cv_work.notify_all();
+    S->dispatcher.join();
+    for (auto &w : S->workers) w->th.join();
+    for (auto &w : S->workers) cudaStreamDestroy(w->st);
+    delete S;
+}
+
+double helm_server_clock(const helm_server *S) { return S ? S->now() : 0.0; }
+
+size_t helm_solve_footprint(int dim, const int64_t n[3], int nrhs, const helm_options *opt) {
+    if (!n || !opt || dim < 1 || dim > 3 || nrhs < 1) return 0;
+    int nn[3] = {1, 1, 1};
+    for (int a = 0; a < dim; ++a) nn[a] = (int)n[a];
+    return solve_footprint(dim, nn, nrhs, *opt);
+}
+
+helm_status helm_server_submit(helm_server *S, const helm_request *q, helm_c128 *u, uint64_t *id) {
+    clear_error();
+    if (!S || !q || !u || !id || !q->m || !q->f) return fail(HELM_ERR_ARG, "null argument");
+    if (q->dim < 1 || q->dim > 3 || q->nrhs < 1 || !(q->h > 0.0) || !(q->tol > 0.0 && q->tol < 1.0))
+        return fail(HELM_ERR_ARG, "bad request");
+    auto r = std::make_shared<Req>();
+    r->dim = q->dim;
+    size_t N = 1;
+    for (int a = 0; a < 3; ++a) {
+        r->n[a] = a < q->dim ? (int)q->n[a] : 1;
+        if (r->n[a] < (a < q->dim ? 2 : 1)) return fail(HELM_ERR_ARG, "bad grid");
+        N *= (size_t)r->n[a];
+    }
+    r->h = q->h;
+    r->m.assign(q->m, q->m + N);
+    r->omega = q->omega;
+    r->alpha = q->alpha;
+    r->nrhs = q->nrhs;
+    r->f.resize((size_t)q->nrhs * N);
+    memcpy(r->f.data(), q->f, (size_t)q->nrhs * N * sizeof(double2));
+    r->tol = q->tol;
+    r->u_out = u;
+    r->footprint = solve_footprint(r->dim, r->n, r->nrhs, S->opt);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->id = S->next_id++;
+        r->t_submit = S->now();
+        S->reqs[r->id] = r;
+        S->queue.push_back(r);
+        *id = r->id;
+    }
+    S->cv_disp.notify_all();
+    return HELM_OK;
+}
+
+static void fill_result(const Req &r, helm_result *res) {
+    res->id = r.id;
+    res->status = r.status;
+    res->nrhs = r.nrhs;
+    res->iterations_max = r.its_max;
+    res->true_rel_residual_max = r.rel_max;
+    res->t_submit = r.t_submit;
+    res->t_admit = r.t_admit;
+    res->t_done = r.t_done;
+    res->footprint_bytes = r.footprint;
+}
+
+helm_status helm_server_wait(helm_server *S, uint64_t id, helm_result *res) {
+    clear_error();
+    if (!S || !res) return fail(HELM_ERR_ARG, "null argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return fail(HELM_ERR_ARG, "unknown request %llu", (unsigned long long)id);
+    std::shared_ptr<Req> r = it->second;
+    S->cv_done.wait(lk, [&] { return r->done; });
+    fill_result(*r, res);
+    S->reqs.erase(id);
+    if (r->status != HELM_OK) return fail(r->status, "request %llu: %s", (unsigned long long)id, r->err.c_str());
+    return HELM_OK;
+}
+
+helm_status helm_server_poll(helm_server *S, uint64_t id, int *done) {
+    clear_error();
+    if (!S || !done) return fail(HELM_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return fail(HELM_ERR_ARG, "unknown request %llu", (unsigned long long)id);
+    *done = it->second->done ? 1 : 0;
+    return HELM_OK;
+}
+
+}  // extern "C"

@@ -29,7 +29,9 @@ EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "he
             "helm_solve", "helm_solve_batch", "helm_apply_H", "helm_apply_M",
             "helm_apply_precond", "helm_true_residual", "helm_num_levels", "helm_level_info",
             "helm_last_error", "helm_kernel_launches", "helm_profile_start", "helm_profile_stop",
-            "helm_time_kernel", "helm_true_residual_noalloc")
+            "helm_time_kernel", "helm_true_residual_noalloc", "helm_solve_footprint",
+            "helm_server_create", "helm_server_submit", "helm_server_wait", "helm_server_poll",
+            "helm_server_clock", "helm_server_destroy")
 
 
 class helm_options(ctypes.Structure):
@@ -37,6 +39,24 @@ class helm_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega_jacobi", ctypes.c_double), ("coarse_max", ctypes.c_int),
                 ("reorth", ctypes.c_int), ("graphs", ctypes.c_int)]
+
+
+class helm_server_config(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int), ("memory_budget", ctypes.c_size_t),
+                ("options", helm_options), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double)]
+
+
+class helm_request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("h", ctypes.c_double),
+                ("m", ctypes.c_void_p), ("omega", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("nrhs", ctypes.c_int), ("f", ctypes.c_void_p), ("tol", ctypes.c_double)]
+
+
+class helm_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("iterations_max", ctypes.c_int), ("true_rel_residual_max", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t)]
 
 
 class HelmError(RuntimeError):
@@ -75,6 +95,15 @@ def _load():
         "helm_time_kernel": (I, [P, ctypes.c_char_p, I, I, ctypes.POINTER(D), ctypes.POINTER(D),
                                  ctypes.POINTER(D)]),
         "helm_true_residual_noalloc": (I, [P, I, P, P, P]),
+        "helm_solve_footprint": (ctypes.c_size_t, [I, ctypes.POINTER(ctypes.c_int64), I,
+                                                   ctypes.POINTER(helm_options)]),
+        "helm_server_create": (I, [ctypes.POINTER(helm_server_config), ctypes.POINTER(P)]),
+        "helm_server_submit": (I, [P, ctypes.POINTER(helm_request), P,
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+        "helm_server_wait": (I, [P, ctypes.c_uint64, ctypes.POINTER(helm_result)]),
+        "helm_server_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(I)]),
+        "helm_server_clock": (D, [P]),
+        "helm_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -306,6 +335,100 @@ class Grid:
         if self._g:
             helm_destroy_grid(self._g)
             self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+
+def helm_solve_footprint(dim, n, nrhs, opt):
+    nn = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    return int(_lib.helm_solve_footprint(int(dim), nn, int(nrhs), ctypes.byref(opt)))
+
+
+def helm_server_create(cfg):
+    s = ctypes.c_void_p()
+    _check(_lib.helm_server_create(ctypes.byref(cfg), ctypes.byref(s)))
+    return s
+
+
+def helm_server_submit(s, req, u):
+    rid = ctypes.c_uint64(0)
+    _check(_lib.helm_server_submit(s, ctypes.byref(req), _ptr(u, np.complex128), ctypes.byref(rid)))
+    return rid.value
+
+
+def helm_server_wait(s, rid, check=True):
+    res = helm_result()
+    st = _lib.helm_server_wait(s, ctypes.c_uint64(rid), ctypes.byref(res))
+    if check:
+        _check(st)
+    return st, res
+
+
+def helm_server_poll(s, rid):
+    d = ctypes.c_int(0)
+    _check(_lib.helm_server_poll(s, ctypes.c_uint64(rid), ctypes.byref(d)))
+    return bool(d.value)
+
+
+def helm_server_clock(s):
+    return float(_lib.helm_server_clock(s))
+
+
+def helm_server_destroy(s):
+    _lib.helm_server_destroy(s)
+
+
+class Server:
+    """Request loop on the current CUDA device (see include/helm.h, serving)."""
+
+    def __init__(self, workers=4, memory_budget=64 << 30, beta=(1.0, 0.5), **opts):
+        o = helm_default_options()
+        for k, v in opts.items():
+            if k == "precond":
+                v = PRECOND[v]
+            elif k == "precision":
+                v = PRECISION[v]
+            setattr(o, k, int(v) if k != "omega_jacobi" else float(v))
+        self.options = o
+        cfg = helm_server_config(int(workers), int(memory_budget), o, float(beta[0]), float(beta[1]))
+        self._s = helm_server_create(cfg)
+        self._keep = {}
+
+    def submit(self, n, h, m, omega, alpha, f, tol):
+        """Queues one request; f is (nrhs, N) complex128, m (N,) float64 (host)."""
+        n = tuple(int(k) for k in n)
+        N = int(np.prod(n))
+        m = np.ascontiguousarray(np.asarray(m, dtype=np.float64).ravel())
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.complex128).reshape(-1, N))
+        u = np.zeros_like(f)
+        req = helm_request(len(n), (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n)))),
+                           float(h), ctypes.c_void_p(m.ctypes.data), float(omega), float(alpha),
+                           int(f.shape[0]), ctypes.c_void_p(f.ctypes.data), float(tol))
+        rid = helm_server_submit(self._s, req, u)
+        self._keep[rid] = (m, f, u)
+        return rid
+
+    def wait(self, rid, check=True):
+        st, res = helm_server_wait(self._s, rid, check=check)
+        _, _, u = self._keep.pop(rid)
+        return st, res, u
+
+    def done(self, rid):
+        return helm_server_poll(self._s, rid)
+
+    def clock(self):
+        return helm_server_clock(self._s)
+
+    def close(self):
+        if self._s:
+            helm_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:

@@ -62,3 +62,13 @@ def test_oracle_is_not_imported_by_the_product():
                 with open(os.path.join(dirpath, fn)) as fh:
                     src = fh.read()
                 assert "oracle" not in re.findall(r"^\s*(?:from|import)\s+(\w+)", src, re.M), fn
+
+
+def test_solve_footprint_scales(lib):
+    o = lib.helm_default_options()
+    a = lib.helm_solve_footprint(2, (401, 201), 1, o)
+    b = lib.helm_solve_footprint(2, (401, 201), 8, o)
+    assert 0 < a < b and b > 8 * 31 * 401 * 201 * 16
+    o.precision = 1
+    assert lib.helm_solve_footprint(2, (401, 201), 8, o) < b
+    assert lib.helm_solve_footprint(0, (401, 201), 8, o) == 0

@@ -1,0 +1,99 @@
+"""Serving loop (helm_server_*): continuous admission, overlap, memory budget.
+
+The key property: a request's result is the same whether it runs alone or in
+a mix with other requests that overlap it on the device (the kernels are
+deterministic and each request has its own grid, stream and workspace), so
+the comparison is bit-for-bit; and it matches the sparse-LU oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import direct  # noqa: E402
+from workloads import point_sources, smooth_random  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def helm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1712_08740_gb300 import helm as h
+    return h
+
+
+def make_requests(k, seed=0):
+    rng = np.random.default_rng(seed)
+    sizes = [(65, 33), (129, 65), (97, 49), (33, 17, 9)]
+    out = []
+    for i in range(k):
+        n = sizes[i % len(sizes)]
+        h = 10.0
+        c = smooth_random(n, h, seed=100 + i)
+        freq = float(rng.uniform(6.0, 12.0))
+        ns = int(rng.integers(1, 4))
+        srcs = [tuple([int(rng.integers(1, n[0] - 1))] + [2] * (len(n) - 1)) for _ in range(ns)]
+        F = np.stack([point_sources(n, h, [s]).ravel() for s in srcs])
+        out.append(dict(n=n, h=h, m=(1.0 / c).ravel(), omega=2 * np.pi * freq, alpha=0.01, F=F))
+    return out
+
+
+def solve_alone(helm, r, precision, tol):
+    g = helm.Grid(r["n"], r["h"], precision=precision)
+    g.set_model(r["m"].copy(), r["omega"], r["alpha"])
+    g.set_shift(1.0, 0.5)
+    U = np.zeros_like(r["F"])
+    g.solve_batch(r["F"].shape[0], r["F"], tol, U)
+    return U
+
+
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_results_same_alone_and_in_the_mix(helm, precision):
+    reqs = make_requests(8)
+    tol = 1e-9
+    alone = [solve_alone(helm, r, precision, tol) for r in reqs]
+    srv = helm.Server(workers=3, memory_budget=16 << 30, precision=precision)
+    ids = [srv.submit(r["n"], r["h"], r["m"], r["omega"], r["alpha"], r["F"], tol) for r in reqs]
+    for i, rid in zip(range(len(reqs)), ids):
+        st, res, U = srv.wait(rid)
+        assert st == 0 and res.true_rel_residual_max <= tol
+        assert np.array_equal(U, alone[i]), f"request {i} differs in the mix"
+    srv.close()
+    # and one of them against the sparse-LU oracle
+    r = reqs[1]
+    u_lu = direct.lu_solve(r["n"], r["h"], r["m"], r["omega"], r["alpha"],
+                           r["F"][0].reshape(r["n"][::-1]))
+    assert np.linalg.norm(alone[1][0] - u_lu.ravel()) <= 1e-6 * np.linalg.norm(u_lu)
+
+
+def test_admission_by_memory_budget(helm):
+    reqs = make_requests(4, seed=3)[:3]
+    o = helm.helm_default_options()
+    o.precision = 1
+    fp = [helm.helm_solve_footprint(len(r["n"]), r["n"], r["F"].shape[0], o) for r in reqs]
+    # a budget that admits only one request at a time
+    srv = helm.Server(workers=3, memory_budget=int(max(fp) * 1.2), precision="mixed")
+    ids = [srv.submit(r["n"], r["h"], r["m"], r["omega"], r["alpha"], r["F"], 1e-8) for r in reqs]
+    res = [srv.wait(i)[1] for i in ids]
+    for a, b in zip(res[:-1], res[1:]):
+        assert b.t_admit >= a.t_done - 1e-6          # strictly one after the other
+        assert b.t_admit >= a.t_admit                # first in, first out
+    big = make_requests(1, seed=9)[0]
+    srv2 = helm.Server(workers=1, memory_budget=1 << 20, precision="mixed")
+    rid = srv2.submit(big["n"], big["h"], big["m"], big["omega"], big["alpha"], big["F"], 1e-8)
+    st, r, _ = srv2.wait(rid, check=False)
+    assert st == 2                                    # HELM_ERR_NOMEM: can never fit
+    srv.close()
+    srv2.close()
+
+
+def test_requests_overlap_when_memory_allows(helm):
+    reqs = make_requests(6, seed=5)
+    srv = helm.Server(workers=3, memory_budget=16 << 30, precision="mixed")
+    ids = [srv.submit(r["n"], r["h"], r["m"], r["omega"], r["alpha"], r["F"], 1e-8) for r in reqs]
+    res = [srv.wait(i)[1] for i in ids]
+    # with three workers some request is admitted before an earlier one is done
+    assert any(res[k].t_admit < res[k - 1].t_done for k in range(1, len(res)))
+    srv.close()
