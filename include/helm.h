@@ -80,9 +80,10 @@ typedef struct {
     int nu1, nu2;            /* damped-Jacobi sweeps before / after coarse correction */
     double omega_jacobi;     /* Jacobi damping weight, (0, 1]; default 0.8            */
     int coarse_max;          /* coarsen while a level has more nodes than this         */
-    int reorth;              /* Gram-Schmidt: 0 classical once; 1 classical twice      */
-                             /* (default); 2 twice only where the first pass cancels  */
-                             /* more than half of ||w||^2 (DGKS test)                 */
+    int reorth;              /* Gram-Schmidt: 0 classical once (default); 1 classical  */
+                             /* twice; 2 twice only where the first pass cancels more */
+                             /* than half of ||w||^2 (DGKS test). The true residual   */
+                             /* is recomputed after every cycle in all three.        */
     int graphs;              /* 1: replay each Arnoldi step as a captured CUDA graph   */
                              /*    (default); 0: launch kernels one by one             */
 } helm_options;

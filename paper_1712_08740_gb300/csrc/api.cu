@@ -189,7 +189,7 @@ void helm_default_options(helm_options *o) {
     o->nu2 = 1;
     o->omega_jacobi = 0.8;
     o->coarse_max = 1500;
-    o->reorth = 1;
+    o->reorth = 0;
     o->graphs = 1;
 }
 

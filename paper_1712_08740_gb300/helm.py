@@ -271,7 +271,7 @@ class Grid:
     """Owns one helm_grid. ``n`` is the node count per axis, x first."""
 
     def __init__(self, n, h, *, restart=30, precond="mg", precision="f64", nu1=1, nu2=1,
-                 omega_jacobi=0.8, coarse_max=1500, reorth=True, max_iters=5000, graphs=True):
+                 omega_jacobi=0.8, coarse_max=1500, reorth=0, max_iters=5000, graphs=True):
         self.n = tuple(int(k) for k in n)
         self.N = int(np.prod(self.n))
         self.h = float(h)

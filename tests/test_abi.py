@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_defaults_and_argument_errors_without_gpu(lib):
     o = lib.helm_default_options()
     assert (o.restart, o.precond, o.precision, o.nu1, o.nu2) == (30, 0, 0, 1, 1)
-    assert o.omega_jacobi == 0.8 and o.coarse_max == 1500 and o.reorth == 1 and o.graphs == 1
+    assert o.omega_jacobi == 0.8 and o.coarse_max == 1500 and o.reorth == 0 and o.graphs == 1
     with pytest.raises(lib.HelmError) as e:
         lib.helm_create_grid(4, (3, 3, 3), 1.0)
     assert e.value.status == 1 and "dim" in e.value.message

@@ -300,6 +300,8 @@ def test_graph_replay_equals_direct_launches(helm, precision):
 
 @pytest.mark.parametrize("reorth", [0, 2])
 def test_gram_schmidt_variants_reach_tolerance(helm, reorth):
+    """Classical Gram-Schmidt once (default) and the DGKS-selective variant reach
+    the tolerance with the same iterations (+-2) as Gram-Schmidt twice."""
     w = workload("2d_smooth_small")
     ref = None
     for mode in (1, reorth):
