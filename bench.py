@@ -113,6 +113,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, or None when
+    the summary is missing or the kernel's source changed since it was captured."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", f"k_{kernel}_2d_smooth_401x201.md")
+    src = os.path.join(ROOT, "paper_1712_08740_gb300", "csrc", "krylov.cu")
+    try:
+        text = open(path).read()
+        code = open(src).read()
+    except OSError:
+        return None
+    mh = re.search(r"kernel_source_sha256_16: (\w+)", text)
+    mt = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
+    mk = re.search(r"__global__ void __launch_bounds__\(kThreads\)\nk_" + kernel + r"\(.*?\n}\n", code, re.S)
+    if not (mh and mt and mk):
+        return None
+    if hashlib.sha256(mk.group(0).encode()).hexdigest()[:16] != mh.group(1):
+        return None
+    return int(mt.group(1))
+
+
 def cpu_baseline(w, budget_s=12.0):
     """The oracle's sparse-LU solve (factor + solve) on the host, timed."""
     from oracle import direct
@@ -320,7 +342,7 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": kt["gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": kt["hbm_frac"], "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
-    roof.update({"kernel": f"{top} (Arnoldi step j={jmid}, N={N})", "traffic": None,
+    roof.update({"kernel": f"{top} (Arnoldi step j={jmid}, N={N})", "traffic": profiled_traffic(top),
                  "avg_launch_us": kt["us_per_launch"],
                  "algorithmic_bytes_per_launch": kt["bytes"], "fp64_flops_per_launch": kt["flops64"],
                  "hbm_frac": kt["hbm_frac"]})

@@ -65,11 +65,16 @@ typedef enum {
     HELM_PRECOND_NONE = 2    /* M = I: plain GMRES, the paper's comparison arm        */
 } helm_precond;
 
-/* Arithmetic of the preconditioner. The outer FGMRES (Arnoldi, Givens,
- * solution update, true residual) is always complex128. */
+/* Arithmetic. The Givens/Hessenberg least squares, the solution update and
+ * the true residual are always complex128. */
 typedef enum {
-    HELM_PREC_F64 = 0,       /* V-cycle in complex128                                 */
-    HELM_PREC_MIXED = 1      /* V-cycle in complex64, stored z in complex64           */
+    HELM_PREC_F64 = 0,       /* V-cycle and Arnoldi in complex128                      */
+    HELM_PREC_MIXED = 1,     /* V-cycle in complex64 (z stored in complex64), Arnoldi   */
+                             /* orthogonalisation in complex128                        */
+    HELM_PREC_MIXED_DS = 2   /* as MIXED, but the Arnoldi basis is stored and           */
+                             /* orthogonalised in double-single arithmetic (pairs of   */
+                             /* FP32 values, ~48-bit significands, FP32 pipe); H z,    */
+                             /* Hessenberg, norms and the true residual in complex128  */
 } helm_precision;
 
 typedef struct {

@@ -258,7 +258,7 @@ helm_status helm_set_options(helm_grid *g, const helm_options *o) {
     if (o->restart < 1 || o->restart > 256) return fail(HELM_ERR_ARG, "restart must be 1..256");
     if (o->max_iters < 1) return fail(HELM_ERR_ARG, "max_iters must be >= 1");
     if (o->precond < 0 || o->precond > 2) return fail(HELM_ERR_ARG, "bad precond");
-    if (o->precision < 0 || o->precision > 1) return fail(HELM_ERR_ARG, "bad precision");
+    if (o->precision < 0 || o->precision > 2) return fail(HELM_ERR_ARG, "bad precision");
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 > 16 || o->nu2 > 16)
         return fail(HELM_ERR_ARG, "nu1, nu2 must be 0..16");
     if (!(o->omega_jacobi > 0.0 && o->omega_jacobi <= 1.0))

@@ -90,19 +90,13 @@ __global__ void k_gj_elim(cplx_t<T> *__restrict__ A, const cplx_t<T> *__restrict
     A[(size_t)i * n + j] = a;
 }
 
-// z = Ainv r for one right-hand side: one warp per row, eight independent
-// accumulators so that each lane keeps eight row loads in flight.
+// One row of Ainv times one vector, by one warp: eight independent accumulators
+// per lane (column j + 32q) keep eight row loads in flight; the fixed
+// combination and shuffle tree make the result independent of how many
+// right-hand sides a launch covers (batched and single solves agree bitwise).
 template <typename T>
-__global__ void k_dense_gemv1(const cplx_t<T> *__restrict__ Ainv, int n,
-                              const cplx_t<T> *__restrict__ r, cplx_t<T> *__restrict__ z,
-                              const int *__restrict__ active) {
-    if (active && !active[0]) return;
-    // rows are split evenly over the grid (one block per SM), then over warps
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = (int)((long long)n * blockIdx.x / gridDim.x);
-    const int r1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
-    for (int i = r0 + warp; i < r1; i += (blockDim.x >> 5)) {
-    const cplx_t<T> *row = Ainv + (size_t)i * n;
+__device__ __forceinline__ cplx_t<T> row_dot(const cplx_t<T> *__restrict__ row,
+                                             const cplx_t<T> *__restrict__ r, int n, int lane) {
     T are[8] = {0, 0, 0, 0, 0, 0, 0, 0}, aim[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int j = lane;
     for (; j + 224 < n; j += 256) {
@@ -130,17 +124,31 @@ __global__ void k_dense_gemv1(const cplx_t<T> *__restrict__ Ainv, int n,
         sre += __shfl_xor_sync(0xffffffffu, sre, o);
         sim += __shfl_xor_sync(0xffffffffu, sim, o);
     }
-    if (lane == 0) {
-        cplx_t<T> out;
-        out.x = sre;
-        out.y = sim;
-        z[i] = out;
-    }
+    cplx_t<T> out;
+    out.x = sre;
+    out.y = sim;
+    return out;
+}
+
+// z = Ainv r for one right-hand side: rows split evenly over the grid (one
+// block per SM), then over warps.
+template <typename T>
+__global__ void k_dense_gemv1(const cplx_t<T> *__restrict__ Ainv, int n,
+                              const cplx_t<T> *__restrict__ r, cplx_t<T> *__restrict__ z,
+                              const int *__restrict__ active) {
+    if (active && !active[0]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = (int)((long long)n * blockIdx.x / gridDim.x);
+    const int r1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
+    for (int i = r0 + warp; i < r1; i += (blockDim.x >> 5)) {
+        const cplx_t<T> v = row_dot<T>(Ainv + (size_t)i * n, r, n, lane);
+        if (lane == 0) z[i] = v;
     }
 }
 
 // z_k = Ainv r_k for a tile of up to kRT right-hand sides per block: each warp
-// owns one row and reads it once for all right-hand sides of the tile.
+// owns one row and applies it to every right-hand side of the tile in turn
+// (the row stays in L1 between them).
 constexpr int kRT = 4;
 
 template <typename T>
@@ -151,55 +159,12 @@ __global__ void k_dense_gemv(const cplx_t<T> *__restrict__ Ainv, int n,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + warp;
     if (i >= n) return;
-    bool on[kRT];
-    int any = 0;
-#pragma unroll
-    for (int q = 0; q < kRT; ++q) {
-        on[q] = rhs0 + q < nb && (!active || active[rhs0 + q]);
-        any |= on[q];
-    }
-    if (!any) return;
     const cplx_t<T> *row = Ainv + (size_t)i * n;
-    T are[kRT][2], aim[kRT][2];
-#pragma unroll
-    for (int q = 0; q < kRT; ++q) are[q][0] = are[q][1] = aim[q][0] = aim[q][1] = 0;
-    int j = lane;
-    for (; j + 32 < n; j += 64) {
-        const cplx_t<T> a0 = row[j], a1 = row[j + 32];
-#pragma unroll
-        for (int q = 0; q < kRT; ++q) {
-            if (!on[q]) continue;
-            const cplx_t<T> *rq = r + (size_t)(rhs0 + q) * sr;
-            const cplx_t<T> v0 = rq[j], v1 = rq[j + 32];
-            are[q][0] += a0.x * v0.x - a0.y * v0.y;
-            aim[q][0] += a0.x * v0.y + a0.y * v0.x;
-            are[q][1] += a1.x * v1.x - a1.y * v1.y;
-            aim[q][1] += a1.x * v1.y + a1.y * v1.x;
-        }
-    }
-    for (; j < n; j += 32) {
-        const cplx_t<T> a = row[j];
-#pragma unroll
-        for (int q = 0; q < kRT; ++q) {
-            if (!on[q]) continue;
-            const cplx_t<T> v = r[(size_t)(rhs0 + q) * sr + j];
-            are[q][0] += a.x * v.x - a.y * v.y;
-            aim[q][0] += a.x * v.y + a.y * v.x;
-        }
-    }
-#pragma unroll
     for (int q = 0; q < kRT; ++q) {
-        T sre = are[q][0] + are[q][1], sim = aim[q][0] + aim[q][1];
-        for (int o = 16; o; o >>= 1) {
-            sre += __shfl_xor_sync(0xffffffffu, sre, o);
-            sim += __shfl_xor_sync(0xffffffffu, sim, o);
-        }
-        if (lane == 0 && on[q]) {
-            cplx_t<T> out;
-            out.x = sre;
-            out.y = sim;
-            z[(size_t)(rhs0 + q) * sz + i] = out;
-        }
+        const int k = rhs0 + q;
+        if (k >= nb || (active && !active[k])) continue;
+        const cplx_t<T> v = row_dot<T>(row, r + (size_t)k * sr, n, lane);
+        if (lane == 0) z[(size_t)k * sz + i] = v;
     }
 }
 

@@ -42,11 +42,11 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
     if ((s = g->V.ensure((size_t)nrhs * (m + 1) * N * sizeof(double2)))) return s;
     if (pc != HELM_PRECOND_NONE) {
         if ((s = g->Z.ensure((size_t)nrhs * m * N * zsz))) return s;
-        if (prec == HELM_PREC_MIXED && (s = g->Zin.ensure((size_t)nrhs * N * sizeof(float2))))
-            return s;
+
     }
     const int nv = m + 1;
     const size_t R = (size_t)nrhs;
+    if (prec == HELM_PREC_MIXED_DS && (s = g->rbuf.ensure(R * N * sizeof(double2)))) return s;
     if ((s = g->hbuf.ensure(R * 2 * nv * sizeof(double2)))) return s;
     if ((s = g->nrm.ensure(R * sizeof(double)))) return s;
     if ((s = g->yv.ensure(R * m * sizeof(double2)))) return s;
@@ -125,8 +125,11 @@ void apply_precond_j(helm_grid *g, int j, int nrhs, const int *act) {
     const double2 *vj = g->V.as<double2>() + (size_t)j * N;
     if (g->opt.precision == HELM_PREC_F64)
         vcycle<double, double2>(g, vj, sV, g->Z.as<double2>() + (size_t)j * N, sZ, nrhs, act);
-    else
+    else if (g->opt.precision == HELM_PREC_MIXED)
         vcycle<float, double2>(g, vj, sV, g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act);
+    else
+        vcycle<float, float4>(g, g->V.as<float4>() + (size_t)j * N, sV,
+                              g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act);
 }
 
 // w = H z_j into basis slot j+1
@@ -136,6 +139,20 @@ void apply_H_j(helm_grid *g, int j, int nrhs, const int *act) {
     const size_t sV = (size_t)(m + 1) * N, sZ = (size_t)m * N;
     double2 *w = g->V.as<double2>() + (size_t)(j + 1) * N;
     const LevelView<double> Lv = level_view<double>(g, 0);
+    if (g->opt.precision == HELM_PREC_MIXED_DS) {
+        float4 *wd = g->V.as<float4>() + (size_t)(j + 1) * N;
+        if (g->opt.precond == HELM_PRECOND_NONE)
+            launch_stencil<double, float4, float4>(ST_APPLY, Lv, shift_H(g),
+                                                   g->V.as<float4>() + (size_t)j * N, sV,
+                                                   (const float4 *)nullptr, 0, wd, sV, nrhs, 0.0, act,
+                                                   g->st);
+        else
+            launch_stencil<double, float2, float4>(ST_APPLY, Lv, shift_H(g),
+                                                   g->Z.as<float2>() + (size_t)j * N, sZ,
+                                                   (const float4 *)nullptr, 0, wd, sV, nrhs, 0.0, act,
+                                                   g->st);
+        return;
+    }
     if (g->opt.precond == HELM_PRECOND_NONE) {
         const double2 *z = g->V.as<double2>() + (size_t)j * N;
         launch_stencil<double, double2, double2>(ST_APPLY, Lv, shift_H(g), z, sV,
@@ -171,6 +188,30 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
     double2 *w = V + (size_t)(j + 1) * N;
     const int nvec = j + 1;
     const int mode = g->opt.reorth;      // 0: CGS once, 1: CGS twice, 2: twice only when needed
+    if (g->opt.precision == HELM_PREC_MIXED_DS) {
+        float4 *Vd = g->V.as<float4>();
+        float4 *wd = Vd + (size_t)(j + 1) * N;
+        if (mode == 2) {
+            int *act2 = g->act2.as<int>();
+            launch_multidot_ds(Vd, sV, nvec + 1, wd, sV, N, hb, 2 * nv, nrhs, act, ks, st);
+            launch_multiaxpy_ds(Vd, sV, nvec, hb, 2 * nv, wd, sV, N, nrm, nrhs, act, ks, st);
+            launch_reorth_flags(act, hb, hb + nv, 2 * nv, nvec, nrm, 0.5, act2, nvec, nrhs, st);
+            launch_multidot_ds(Vd, sV, nvec, wd, sV, N, hb + nv, 2 * nv, nrhs, act2, ks, st);
+            launch_multiaxpy_ds(Vd, sV, nvec, hb + nv, 2 * nv, wd, sV, N, nrm, nrhs, act2, ks, st);
+        } else {
+            launch_multidot_ds(Vd, sV, nvec, wd, sV, N, hb, 2 * nv, nrhs, act, ks, st);
+            launch_multiaxpy_ds(Vd, sV, nvec, hb, 2 * nv, wd, sV, N, mode ? nullptr : nrm, nrhs, act,
+                                ks, st);
+            if (mode) {
+                launch_multidot_ds(Vd, sV, nvec, wd, sV, N, hb + nv, 2 * nv, nrhs, act, ks, st);
+                launch_multiaxpy_ds(Vd, sV, nvec, hb + nv, 2 * nv, wd, sV, N, nrm, nrhs, act, ks, st);
+            }
+        }
+        launch_givens(cycle_state(g), j, hb, 2 * nv, mode ? 1 : 0, nrm, nrhs, tol, g->opt.max_iters,
+                      g->hflag, st);
+        launch_scale_ds<float4>(wd, sV, nrm, wd, sV, N, nrhs, act, st);
+        return;
+    }
     if (mode == 2) {
         // first pass also returns ||w||^2 (w = slot j+1 taken as one more vector)
         int *act2 = g->act2.as<int>();
@@ -289,7 +330,11 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
     cudaMemsetAsync(flag, 0, sizeof(int), st);
     launch_finite_check((const double *)f, 2 * N * (size_t)nrhs, flag, st);
     cudaMemsetAsync(u, 0, (size_t)nrhs * N * sizeof(double2), st);
-    launch_convert<double2, double2>(f, N, V, sV, N, nrhs, st);
+    // r = f: into basis slot 0 (complex128 basis) or the residual buffer (double-single basis)
+    const bool ds = g->opt.precision == HELM_PREC_MIXED_DS;
+    double2 *rvec = ds ? g->rbuf.as<double2>() : V;
+    const size_t sr = ds ? N : sV;
+    launch_convert<double2, double2>(f, N, rvec, sr, N, nrhs, st);
     launch_norm2(f, N, N, nrm, nrhs, nullptr, ks, st);
     launch_cycle_init(S, nrm, nrhs, g->hflag, st);
     int bad = 0;
@@ -298,8 +343,11 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
     if (bad) return fail(HELM_ERR_NONFINITE, "right-hand side contains NaN or Inf");
 
     while (*(volatile int *)g->hflag) {
-        // v_0 = r / ||r|| (r in slot 0, ||r||^2 in nrm)
-        launch_scale<double2>(V, sV, nrm, V, sV, N, nrhs, S.act_cy, st);
+        // v_0 = r / ||r|| (||r||^2 in nrm)
+        if (ds)
+            launch_scale_ds<double2>(rvec, sr, nrm, g->V.as<float4>(), sV, N, nrhs, S.act_cy, st);
+        else
+            launch_scale<double2>(V, sV, nrm, V, sV, N, nrhs, S.act_cy, st);
         for (int j = 0; j < m; ++j) {
             if (j >= kLookahead) {
                 cudaEvent_t e = g->ring[(j - kLookahead) % g->ring.size()];
@@ -319,7 +367,10 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         }
         // end of cycle: y = R^-1 g, x += Z y, r = f - H x into slot 0, ||r||^2
         launch_backsolve(S, g->yv.as<double2>(), nrhs, st);
-        if (g->opt.precond == HELM_PRECOND_NONE)
+        if (g->opt.precond == HELM_PRECOND_NONE && ds)
+            launch_update_ds(g->V.as<float4>(), sV, m, g->yv.as<double2>(), m, u, N, N, nrhs,
+                             S.act_cy, st);
+        else if (g->opt.precond == HELM_PRECOND_NONE)
             launch_update<double2>(V, sV, m, g->yv.as<double2>(), m, u, N, N, nrhs, S.act_cy, st);
         else if (g->opt.precision == HELM_PREC_F64)
             launch_update<double2>(g->Z.as<double2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u,
@@ -327,9 +378,9 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         else
             launch_update<float2>(g->Z.as<float2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u, N,
                                   N, nrhs, S.act_cy, st);
-        launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, V, sV, nrhs,
-                                                 0.0, S.act_cy, st);
-        launch_norm2(V, sV, N, nrm, nrhs, S.act_cy, ks, st);
+        launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, rvec, sr,
+                                                 nrhs, 0.0, S.act_cy, st);
+        launch_norm2(rvec, sr, N, nrm, nrhs, S.act_cy, ks, st);
         launch_cycle_check(S, nrm, nrhs, tol, g->opt.max_iters, g->hflag, st);
         if ((s = sync_stream(g, "cycle end"))) return s;
     }
@@ -548,7 +599,19 @@ extern "C" helm_status helm_time_kernel(helm_grid *g, const char *kernel, int j,
     const std::string name(kernel);
     double b = 0.0, fl = 0.0;
     auto one = [&]() -> bool {
-        if (name == "multidot") {
+        const bool dsb = g->opt.precision == HELM_PREC_MIXED_DS;
+        float4 *Vd = g->V.as<float4>();
+        if (name == "multidot" && dsb) {
+            launch_multidot_ds(Vd, sV, nvec, Vd + (size_t)(j + 1) * N, sV, N, hb, 2 * nv, nrhs, nullptr, ks,
+                               g->st);
+            b = (nvec + 1.0) * N * 16.0 * nrhs;
+            fl = 0.0;
+        } else if (name == "multiaxpy" && dsb) {
+            launch_multiaxpy_ds(Vd, sV, nvec, hb, 2 * nv, Vd + (size_t)(j + 1) * N, sV, N, nrm, nrhs,
+                                nullptr, ks, g->st);
+            b = (nvec + 2.0) * N * 16.0 * nrhs;
+            fl = 4.0 * N * nrhs;
+        } else if (name == "multidot") {
             launch_multidot(V, sV, nvec, V + (size_t)(j + 1) * N, sV, N, hb, 2 * nv, nrhs, nullptr, ks, g->st);
             b = (nvec + 1.0) * N * 16.0 * nrhs;
             fl = 8.0 * nvec * N * nrhs;

@@ -57,9 +57,10 @@ struct helm_grid {
 
     // Krylov workspace
     int cap_rhs = 0, cap_m = 0, cap_prec = -1;
-    helm::DevBuf V, Z, Zin, hbuf, nrm, yv, partial, counter, act_it, act_cy, act2, flag;
+    helm::DevBuf V, Z, hbuf, nrm, yv, partial, counter, act_it, act_cy, act2, flag;
     helm::DevBuf cR, cg, ccs, csn, cfn, cbeta, crel, ck, cits, cstat, cany, cQ;   // FGMRES state
     helm::DevBuf fst, ust, xst, yst;    // staging for host pointers / helper vectors
+    helm::DevBuf rbuf;                  // residuals in complex128 (double-single basis)
     int *hflag = nullptr;               // host-mapped "any right-hand side active" flag
     std::vector<cudaEvent_t> ring;      // look-ahead events of the Arnoldi loop
 

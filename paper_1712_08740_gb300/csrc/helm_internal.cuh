@@ -62,6 +62,28 @@ __device__ __forceinline__ float d2f_trunc(double d) {
 template <> __device__ __forceinline__ double2 cvt<double2, float2>(float2 a) {
     return make_double2(f2d_exact(a.x), f2d_exact(a.y));
 }
+
+// Double-single ("DS") complex numbers: float4 = (re_hi, re_lo, im_hi, im_lo),
+// value = hi + lo per part, |lo| <= ulp(hi); about 48 significant bits.
+// Splitting a double costs one FP64 subtraction (the rest is integer work):
+// hi is the mantissa truncated to 24 bits, so x - hi is exact in FP64.
+__device__ __forceinline__ float2 ds_split(double x) {
+    const float hi = d2f_trunc(x);
+    const float lo = d2f_trunc(x - f2d_exact(hi));
+    return make_float2(hi, lo);
+}
+__device__ __forceinline__ double ds_join(float hi, float lo) { return f2d_exact(hi) + f2d_exact(lo); }
+template <> __device__ __forceinline__ float4 cvt<float4, double2>(double2 a) {
+    const float2 r = ds_split(a.x), i = ds_split(a.y);
+    return make_float4(r.x, r.y, i.x, i.y);
+}
+template <> __device__ __forceinline__ double2 cvt<double2, float4>(float4 a) {
+    return make_double2(ds_join(a.x, a.y), ds_join(a.z, a.w));
+}
+template <> __device__ __forceinline__ float2 cvt<float2, float4>(float4 a) {
+    return make_float2(a.x + a.y, a.z + a.w);
+}
+template <> __device__ __forceinline__ float4 cvt<float4, float4>(float4 a) { return a; }
 template <> __device__ __forceinline__ float2 cvt<float2, double2>(double2 a) {
     return make_float2(d2f_trunc(a.x), d2f_trunc(a.y));
 }
@@ -198,6 +220,23 @@ void launch_convert(const CIn *x, size_t sx, COut *y, size_t sy, size_t N, int n
 void launch_reorth_flags(const int *act, const double2 *h1, double2 *h2, int hstride, int wslot,
                          const double *n1, double eta2, int *act2, int nvec, int nrhs,
                          cudaStream_t st);
+// ---- double-single basis (precision HELM_PREC_MIXED_DS): the same operations on
+// a basis stored as float4 (re_hi, re_lo, im_hi, im_lo), computed with FP32
+// error-free products and two-sums; results and coefficients stay complex128.
+void launch_multidot_ds(const float4 *V, size_t sV, int nvec, const float4 *w, size_t sw, size_t N,
+                        double2 *out, size_t out_stride, int nrhs, const int *active,
+                        KrylovScratch &ks, cudaStream_t st);
+void launch_multiaxpy_ds(const float4 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
+                         float4 *w, size_t sw, size_t N, double *norm2, int nrhs, const int *active,
+                         KrylovScratch &ks, cudaStream_t st);
+// y = x / sqrt(norm2[k]) with x complex128 or DS, y DS
+template <typename CIn>
+void launch_scale_ds(const CIn *x, size_t sx, const double *norm2, float4 *y, size_t sy, size_t N,
+                     int nrhs, const int *active, cudaStream_t st);
+// x += sum_i Z_i y_i where the basis is DS (no preconditioner: Z = V)
+void launch_update_ds(const float4 *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
+                      double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st);
+
 // finite check: flag[0] |= 1 if any entry is NaN/Inf
 void launch_finite_check(const double *x, size_t n, int *flag, cudaStream_t st);
 

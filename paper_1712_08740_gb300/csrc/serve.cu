@@ -96,6 +96,7 @@ size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o)
     b += levels_sum * (8.0 + 8.0 + 4.0);                 // slowness, coefficients
     if (o.precond != HELM_PRECOND_NONE) b += nc * nc * csz + nc * csz;   // coarse inverse
     b += 2.0 * nrhs * N * 16.0;                          // staging of host f and u
+    if (o.precision == HELM_PREC_MIXED_DS) b += nrhs * N * 16.0;   // complex128 residuals
     b += (double)nrhs * (m + 1.0) * (m + 1.0) * 16.0 * 3.0;   // Hessenberg, rotations
     b += (double)nrhs * (m + 1.0) * kMaxBlocks * 16.0;   // reduction partials
     b += 1 << 20;                                        // small buffers

@@ -301,6 +301,8 @@ void prepare_vfused() {
     set_attr<float, float2, 3>();
     set_attr<float, double2, 2>();
     set_attr<float, double2, 3>();
+    set_attr<float, float4, 2>();
+    set_attr<float, float4, 3>();
     done = true;
 }
 
@@ -348,6 +350,7 @@ void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, OpShift<T> s, T w
 HELM_INST_V(double, double2)
 HELM_INST_V(float, float2)
 HELM_INST_V(float, double2)
+HELM_INST_V(float, float4)
 #undef HELM_INST_V
 
 }  // namespace helm
