@@ -90,16 +90,16 @@ __global__ void k_gj_elim(cplx_t<T> *__restrict__ A, const cplx_t<T> *__restrict
     A[(size_t)i * n + j] = a;
 }
 
-// One row of Ainv times one vector, by one warp: eight independent accumulators
-// per lane (column j + 32q) keep eight row loads in flight; the fixed
-// combination and shuffle tree make the result independent of how many
-// right-hand sides a launch covers (batched and single solves agree bitwise).
+// One quarter of one row of Ainv times one vector, by one warp: columns
+// [c0, c1), eight independent accumulators per lane (column j + 32q) keep
+// eight row loads in flight, then a fixed combination and shuffle tree.
 template <typename T>
-__device__ __forceinline__ cplx_t<T> row_dot(const cplx_t<T> *__restrict__ row,
-                                             const cplx_t<T> *__restrict__ r, int n, int lane) {
+__device__ __forceinline__ cplx_t<T> quarter_dot(const cplx_t<T> *__restrict__ row,
+                                                 const cplx_t<T> *__restrict__ r, int c0, int c1,
+                                                 int lane) {
     T are[8] = {0, 0, 0, 0, 0, 0, 0, 0}, aim[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int j = lane;
-    for (; j + 224 < n; j += 256) {
+    int j = c0 + lane;
+    for (; j + 224 < c1; j += 256) {
         cplx_t<T> a[8], v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -112,7 +112,7 @@ __device__ __forceinline__ cplx_t<T> row_dot(const cplx_t<T> *__restrict__ row,
             aim[q] += a[q].x * v[q].y + a[q].y * v[q].x;
         }
     }
-    for (; j < n; j += 32) {
+    for (; j < c1; j += 32) {
         const cplx_t<T> a = row[j];
         const cplx_t<T> v = r[j];
         are[0] += a.x * v.x - a.y * v.y;
@@ -130,41 +130,82 @@ __device__ __forceinline__ cplx_t<T> row_dot(const cplx_t<T> *__restrict__ row,
     return out;
 }
 
-// z = Ainv r for one right-hand side: rows split evenly over the grid (one
-// block per SM), then over warps.
+// Work layout shared by both GEMV kernels: a block of 8 warps handles a pair
+// of rows; warp w takes quarter (w % 4) of row (w / 4), so each SM
+// sub-partition (warp w runs on sub-partition w % 4) gets the same share of
+// the FP64 work; the four quarter sums are added in a fixed order. Quarters
+// start on multiples of 32 columns. The arithmetic per row is the same in both
+// kernels, so batched and single solves agree bitwise.
+__device__ __forceinline__ void quarter_range(int n, int q, int &c0, int &c1) {
+    const int Q = ((n + 127) / 128) * 32;
+    c0 = min(q * Q, n);
+    c1 = min((q + 1) * Q, n);
+}
+
+// z = Ainv r for one right-hand side; row pairs strided over the grid
 template <typename T>
-__global__ void k_dense_gemv1(const cplx_t<T> *__restrict__ Ainv, int n,
-                              const cplx_t<T> *__restrict__ r, cplx_t<T> *__restrict__ z,
-                              const int *__restrict__ active) {
+__global__ void __launch_bounds__(256)
+k_dense_gemv1(const cplx_t<T> *__restrict__ Ainv, int n, const cplx_t<T> *__restrict__ r,
+              cplx_t<T> *__restrict__ z, const int *__restrict__ active) {
     if (active && !active[0]) return;
+    __shared__ cplx_t<T> part[2][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = (int)((long long)n * blockIdx.x / gridDim.x);
-    const int r1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
-    for (int i = r0 + warp; i < r1; i += (blockDim.x >> 5)) {
-        const cplx_t<T> v = row_dot<T>(Ainv + (size_t)i * n, r, n, lane);
-        if (lane == 0) z[i] = v;
+    const int q = warp & 3, half = warp >> 2;
+    int c0, c1;
+    quarter_range(n, q, c0, c1);
+    const int npairs = (n + 1) / 2;
+    for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        const int i = 2 * pr + half;
+        if (i < n) {
+            const cplx_t<T> v = quarter_dot<T>(Ainv + (size_t)i * n, r, c0, c1, lane);
+            if (lane == 0) part[half][q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2 && 2 * pr + (int)threadIdx.x < n) {
+            const int hh = threadIdx.x;
+            cplx_t<T> s = part[hh][0];
+            for (int k = 1; k < 4; ++k) {
+                s.x += part[hh][k].x;
+                s.y += part[hh][k].y;
+            }
+            z[2 * pr + hh] = s;
+        }
+        __syncthreads();
     }
 }
 
-// z_k = Ainv r_k for a tile of up to kRT right-hand sides per block: each warp
-// owns one row and applies it to every right-hand side of the tile in turn
-// (the row stays in L1 between them).
+// z_k = Ainv r_k for a tile of up to kRT right-hand sides per block (one row pair)
 constexpr int kRT = 4;
 
 template <typename T>
-__global__ void k_dense_gemv(const cplx_t<T> *__restrict__ Ainv, int n,
-                             const cplx_t<T> *__restrict__ r, size_t sr, cplx_t<T> *__restrict__ z,
-                             size_t sz, int nb, const int *__restrict__ active) {
+__global__ void __launch_bounds__(256)
+k_dense_gemv(const cplx_t<T> *__restrict__ Ainv, int n, const cplx_t<T> *__restrict__ r, size_t sr,
+             cplx_t<T> *__restrict__ z, size_t sz, int nb, const int *__restrict__ active) {
+    __shared__ cplx_t<T> part[kRT][2][4];
     const int rhs0 = blockIdx.y * kRT;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (i >= n) return;
-    const cplx_t<T> *row = Ainv + (size_t)i * n;
-    for (int q = 0; q < kRT; ++q) {
-        const int k = rhs0 + q;
-        if (k >= nb || (active && !active[k])) continue;
-        const cplx_t<T> v = row_dot<T>(row, r + (size_t)k * sr, n, lane);
-        if (lane == 0) z[(size_t)k * sz + i] = v;
+    const int q = warp & 3, half = warp >> 2;
+    const int i = 2 * blockIdx.x + half;
+    int c0, c1;
+    quarter_range(n, q, c0, c1);
+    for (int t = 0; t < kRT; ++t) {
+        const int k = rhs0 + t;
+        if (k >= nb || (active && !active[k]) || i >= n) continue;
+        const cplx_t<T> v = quarter_dot<T>(Ainv + (size_t)i * n, r + (size_t)k * sr, c0, c1, lane);
+        if (lane == 0) part[t][half][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kRT) {
+        const int t = threadIdx.x >> 1, hh = threadIdx.x & 1;
+        const int k = rhs0 + t, row = 2 * blockIdx.x + hh;
+        if (k < nb && (!active || active[k]) && row < n) {
+            cplx_t<T> s = part[t][hh][0];
+            for (int m = 1; m < 4; ++m) {
+                s.x += part[t][hh][m].x;
+                s.y += part[t][hh][m].y;
+            }
+            z[(size_t)k * sz + row] = s;
+        }
     }
 }
 
@@ -196,13 +237,13 @@ void launch_gauss_jordan(cplx_t<T> *A, cplx_t<T> *colbuf, int n, cudaStream_t st
 template <typename T>
 void launch_dense_gemv(const cplx_t<T> *Ainv, int n, const cplx_t<T> *r, size_t sr,
                        cplx_t<T> *z, size_t sz, int nb, const int *active, cudaStream_t st) {
-    const int warps = 8;
-    dim3 g((n + warps - 1) / warps, (nb + kRT - 1) / kRT);
+    const int npairs = (n + 1) / 2;
     prof_begin(st);
     if (nb == 1)
-        k_dense_gemv1<T><<<n < 152 * 4 ? (n + 3) / 4 : 152, warps * 32, 0, st>>>(Ainv, n, r, z, active);
+        k_dense_gemv1<T><<<npairs < 152 ? npairs : 152, 256, 0, st>>>(Ainv, n, r, z, active);
     else
-        k_dense_gemv<T><<<g, warps * 32, 0, st>>>(Ainv, n, r, sr, z, sz, nb, active);
+        k_dense_gemv<T><<<dim3(npairs, (nb + kRT - 1) / kRT), 256, 0, st>>>(Ainv, n, r, sr, z, sz, nb,
+                                                                             active);
     count_launch();
     if (prof_on())
         prof_end(sizeof(T) == 8 ? "coarse_gemv_f64" : "coarse_gemv_f32", st,

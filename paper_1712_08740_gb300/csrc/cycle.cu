@@ -86,9 +86,22 @@ __global__ void k_givens(CycleState S, int j, const double2 *__restrict__ hb, in
         const double hn = sqrt(nrm2[r]);
         finite = __all_sync(0xffffffffu, finite) && isfinite(hn);
         if (Qs) {
-            // columns c <= j of Q_j, rows i <= j (coalesced down each column)
-            for (int c = 0; c <= j; ++c)
-                for (int i = max(c - 1, 0) + lane; i <= j; i += 32) Qs[i + c * ld] = Q[i + (size_t)c * ld];
+            // columns c <= j of Q_j copied as one contiguous block of (j+1) * ld
+            // values (column-major), eight independent loads in flight per lane
+            const int nq = (j + 1) * ld;
+            for (int t0 = lane; t0 < nq; t0 += 32 * 8) {
+                double2 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int t = t0 + 32 * u;
+                    if (t < nq) v[u] = Q[t];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int t = t0 + 32 * u;
+                    if (t < nq) Qs[t] = v[u];
+                }
+            }
         }
         __syncwarp();
         const double2 *Qr = Qs ? Qs : Q;

@@ -367,17 +367,19 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         }
         // end of cycle: y = R^-1 g, x += Z y, r = f - H x into slot 0, ||r||^2
         launch_backsolve(S, g->yv.as<double2>(), nrhs, st);
+        // each right-hand side uses only the S.k columns it filled in this cycle
         if (g->opt.precond == HELM_PRECOND_NONE && ds)
             launch_update_ds(g->V.as<float4>(), sV, m, g->yv.as<double2>(), m, u, N, N, nrhs,
-                             S.act_cy, st);
+                             S.act_cy, st, S.k);
         else if (g->opt.precond == HELM_PRECOND_NONE)
-            launch_update<double2>(V, sV, m, g->yv.as<double2>(), m, u, N, N, nrhs, S.act_cy, st);
+            launch_update<double2>(V, sV, m, g->yv.as<double2>(), m, u, N, N, nrhs, S.act_cy, st,
+                                   S.k);
         else if (g->opt.precision == HELM_PREC_F64)
             launch_update<double2>(g->Z.as<double2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u,
-                                   N, N, nrhs, S.act_cy, st);
+                                   N, N, nrhs, S.act_cy, st, S.k);
         else
             launch_update<float2>(g->Z.as<float2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u, N,
-                                  N, nrhs, S.act_cy, st);
+                                  N, nrhs, S.act_cy, st, S.k);
         launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, rvec, sr,
                                                  nrhs, 0.0, S.act_cy, st);
         launch_norm2(rvec, sr, N, nrm, nrhs, S.act_cy, ks, st);

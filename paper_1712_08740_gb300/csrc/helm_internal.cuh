@@ -209,10 +209,12 @@ void launch_norm2(const double2 *x, size_t sx, size_t N, double *norm2, int nrhs
 template <typename COut>
 void launch_scale(const double2 *x, size_t sx, const double *scale, COut *y, size_t sy, size_t N,
                   int nrhs, const int *active, cudaStream_t st);
-// x += sum_i Z_i y[k * y_stride + i]   (Z complex128 or complex64)
+// x += sum_{i < min(nvec, kcount[k])} Z_i y[k * y_stride + i]   (Z complex128 or complex64;
+// kcount nullable: all nvec columns)
 template <typename CZ>
 void launch_update(const CZ *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
-                   double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st);
+                   double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st,
+                   const int *kcount = nullptr);
 template <typename CIn, typename COut>
 void launch_convert(const CIn *x, size_t sx, COut *y, size_t sy, size_t N, int nrhs,
                     cudaStream_t st);
@@ -235,7 +237,8 @@ void launch_scale_ds(const CIn *x, size_t sx, const double *norm2, float4 *y, si
                      int nrhs, const int *active, cudaStream_t st);
 // x += sum_i Z_i y_i where the basis is DS (no preconditioner: Z = V)
 void launch_update_ds(const float4 *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
-                      double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st);
+                      double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st,
+                      const int *kcount = nullptr);
 
 // finite check: flag[0] |= 1 if any entry is NaN/Inf
 void launch_finite_check(const double *x, size_t n, int *flag, cudaStream_t st);

@@ -247,9 +247,12 @@ template <typename CZ>
 __global__ void __launch_bounds__(kThreads)
 k_update(const CZ *__restrict__ Z, size_t sZ, int nvec, const double2 *__restrict__ yv,
          size_t ystride, double2 *__restrict__ x, size_t sx, size_t N,
-         const int *__restrict__ active) {
+         const int *__restrict__ active, const int *__restrict__ kcount) {
     const int r = blockIdx.y;
     if (active && !active[r]) return;
+    // only the columns this right-hand side filled in the cycle: the others may
+    // hold stale or uninitialised values (NaN * 0 would poison x)
+    if (kcount) nvec = min(nvec, kcount[r]);
     Z += r * sZ;
     x += r * sx;
     __shared__ double2 ys[kMaxVec];
@@ -373,10 +376,12 @@ void launch_scale(const double2 *x, size_t sx, const double *norm2, COut *y, siz
 
 template <typename CZ>
 void launch_update(const CZ *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
-                   double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st) {
+                   double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st,
+                   const int *kcount) {
     const int nb = blocks_for(N, kThreads, 1 << 16);
     prof_begin(st);
-    k_update<CZ><<<dim3(nb, nrhs), kThreads, 0, st>>>(Z, sZ, nvec, y, y_stride, x, sx, N, active);
+    k_update<CZ><<<dim3(nb, nrhs), kThreads, 0, st>>>(Z, sZ, nvec, y, y_stride, x, sx, N, active,
+                                                      kcount);
     count_launch();
     if (prof_on())
         prof_end("update_f64", st, ((double)nvec * sizeof(CZ) + 32.0) * N * nrhs,
@@ -412,9 +417,11 @@ template void launch_scale<double2>(const double2 *, size_t, const double *, dou
 template void launch_scale<float2>(const double2 *, size_t, const double *, float2 *, size_t,
                                    size_t, int, const int *, cudaStream_t);
 template void launch_update<double2>(const double2 *, size_t, int, const double2 *, size_t,
-                                     double2 *, size_t, size_t, int, const int *, cudaStream_t);
+                                     double2 *, size_t, size_t, int, const int *, cudaStream_t,
+                                     const int *);
 template void launch_update<float2>(const float2 *, size_t, int, const double2 *, size_t,
-                                    double2 *, size_t, size_t, int, const int *, cudaStream_t);
+                                    double2 *, size_t, size_t, int, const int *, cudaStream_t,
+                                    const int *);
 template void launch_convert<double2, float2>(const double2 *, size_t, float2 *, size_t, size_t,
                                               int, cudaStream_t);
 template void launch_convert<float2, double2>(const float2 *, size_t, double2 *, size_t, size_t,

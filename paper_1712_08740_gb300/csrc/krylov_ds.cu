@@ -274,9 +274,10 @@ k_scale_ds(const CIn *x, size_t sx, const double *__restrict__ norm2, float4 *y,
 __global__ void __launch_bounds__(kThreads)
 k_update_ds(const float4 *__restrict__ Z, size_t sZ, int nvec, const double2 *__restrict__ yv,
             size_t ystride, double2 *__restrict__ x, size_t sx, size_t N,
-            const int *__restrict__ active) {
+            const int *__restrict__ active, const int *__restrict__ kcount) {
     const int r = blockIdx.y;
     if (active && !active[r]) return;
+    if (kcount) nvec = min(nvec, kcount[r]);
     Z += r * sZ;
     x += r * sx;
     __shared__ double2 ys[kMaxVec];
@@ -347,10 +348,12 @@ void launch_scale_ds(const CIn *x, size_t sx, const double *norm2, float4 *y, si
 }
 
 void launch_update_ds(const float4 *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
-                      double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st) {
+                      double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st,
+                      const int *kcount) {
     const int nb = blocks_for(N, 1 << 16);
     prof_begin(st);
-    k_update_ds<<<dim3(nb, nrhs), kThreads, 0, st>>>(Z, sZ, nvec, y, y_stride, x, sx, N, active);
+    k_update_ds<<<dim3(nb, nrhs), kThreads, 0, st>>>(Z, sZ, nvec, y, y_stride, x, sx, N, active,
+                                                     kcount);
     count_launch();
     if (prof_on()) prof_end("update_ds", st, (16.0 * nvec + 32.0) * N * nrhs, 8.0 * nvec * N * nrhs);
 }

@@ -362,3 +362,23 @@ def test_double_single_batch_equals_single(helm):
         uk = torch.empty_like(fk)
         _, its, rr = g.solve(fk, 1e-8, uk)
         assert its == its_b[k] and np.array_equal(Ub[k], uk.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed", "mixed_ds"])
+def test_partial_cycle_update_ignores_unfilled_columns(helm, precision):
+    """A cycle that ends before `restart` steps (iteration cap or convergence)
+    must not read the unfilled basis columns: they may hold NaN bit patterns
+    left in device memory (NaN * 0 = NaN would poison the iterate)."""
+    junk = torch.full((256 << 20,), float("nan"), dtype=torch.float32, device=DEV)
+    del junk
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    w = workload("2d_smooth_small")
+    g = helm.Grid(w.n, w.h, restart=12, precision=precision, max_iters=5)
+    g.set_model(dev(w.slowness()), w.omega(), w.alpha)
+    g.set_shift(*w.beta)
+    fd = dev(w.rhs())
+    ud = torch.empty_like(fd)
+    st, its, rr = g.solve(fd, 1e-8, ud, check=False)
+    assert st == 4 and its == 5 and np.isfinite(rr) and 0 < rr < 1
+    assert torch.isfinite(ud).all()
