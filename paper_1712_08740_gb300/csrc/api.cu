@@ -299,6 +299,7 @@ helm_status helm_set_model(helm_grid *g, const double *m, double omega, double a
     if (s) return s;
     g->has_model = false;
     g->ready = false;
+    g->hdiag_ok = false;
     if (bad) return fail(HELM_ERR_NONFINITE, "slowness must be finite and > 0 at every node");
     g->omega = omega;
     g->alpha = alpha;

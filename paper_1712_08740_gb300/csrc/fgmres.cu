@@ -46,7 +46,9 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
     }
     const int nv = m + 1;
     const size_t R = (size_t)nrhs;
-    if (prec == HELM_PREC_MIXED_DS && (s = g->rbuf.ensure(R * N * sizeof(double2)))) return s;
+    if (prec == HELM_PREC_MIXED_DS && ((s = g->rbuf.ensure(R * N * sizeof(double2))) ||
+                                       (s = g->hdiag.ensure(N * sizeof(float4)))))
+        return s;
     if ((s = g->hbuf.ensure(R * 2 * nv * sizeof(double2)))) return s;
     if ((s = g->nrm.ensure(R * sizeof(double)))) return s;
     if ((s = g->yv.ensure(R * m * sizeof(double2)))) return s;
@@ -147,10 +149,8 @@ void apply_H_j(helm_grid *g, int j, int nrhs, const int *act) {
                                                    (const float4 *)nullptr, 0, wd, sV, nrhs, 0.0, act,
                                                    g->st);
         else
-            launch_stencil<double, float2, float4>(ST_APPLY, Lv, shift_H(g),
-                                                   g->Z.as<float2>() + (size_t)j * N, sZ,
-                                                   (const float4 *)nullptr, 0, wd, sV, nrhs, 0.0, act,
-                                                   g->st);
+            launch_apply_H_ds(Lv, g->hdiag.as<float4>(), g->Z.as<float2>() + (size_t)j * N, sZ, wd,
+                              sV, nrhs, act, g->st);
         return;
     }
     if (g->opt.precond == HELM_PRECOND_NONE) {
@@ -243,7 +243,7 @@ long long graph_key_of(const helm_grid *g, int nrhs, double tol) {
     mixp(g->V.p); mixp(g->Z.p); mixp(g->hbuf.p); mixp(g->nrm.p); mixp(g->partial.p); mixp(g->counter.p);
     mixp(g->act_it.p); mixp(g->act_cy.p); mixp(g->act2.p); mixp(g->Ainv.p); mixp(g->hflag);
     mixp(g->cR.p); mixp(g->cg.p); mixp(g->ccs.p); mixp(g->csn.p); mixp(g->cQ.p); mixp(g->cfn.p);
-    mixp(g->ck.p); mixp(g->cits.p); mixp(g->cstat.p); mixp(g->cany.p);
+    mixp(g->ck.p); mixp(g->cits.p); mixp(g->cstat.p); mixp(g->cany.p); mixp(g->hdiag.p); mixp(g->rbuf.p);
     for (const auto &L : g->lv) {
         mixp(L.w64.p); mixp(L.w32.p); mixp(L.u.p); mixp(L.t.p); mixp(L.b.p); mixp(L.r.p);
         mixu((unsigned long long)L.N);
@@ -321,6 +321,10 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
     double *nrm = g->nrm.as<double>();
     const CycleState S = cycle_state(g);
     const LevelView<double> L0 = level_view<double>(g, 0);
+    if (g->opt.precision == HELM_PREC_MIXED_DS && !g->hdiag_ok) {
+        launch_make_hdiag_ds(level_view<double>(g, 0), shift_H(g), g->hdiag.as<float4>(), g->st);
+        g->hdiag_ok = true;
+    }
     const bool graphs = g->use_graphs;
     if (graphs && (s = capture_steps(g, nrhs, tol))) return s;
     g->last_nrhs = nrhs;

@@ -61,6 +61,8 @@ struct helm_grid {
     helm::DevBuf cR, cg, ccs, csn, cfn, cbeta, crel, ck, cits, cstat, cany, cQ;   // FGMRES state
     helm::DevBuf fst, ust, xst, yst;    // staging for host pointers / helper vectors
     helm::DevBuf rbuf;                  // residuals in complex128 (double-single basis)
+    helm::DevBuf hdiag;                 // diagonal of H as double-single pairs
+    bool hdiag_ok = false;              // hdiag matches the current model
     int *hflag = nullptr;               // host-mapped "any right-hand side active" flag
     std::vector<cudaEvent_t> ring;      // look-ahead events of the Arnoldi loop
 

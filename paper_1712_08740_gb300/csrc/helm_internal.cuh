@@ -240,6 +240,12 @@ void launch_update_ds(const float4 *Z, size_t sZ, int nvec, const double2 *y, si
                       double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st,
                       const int *kcount = nullptr);
 
+// diagonal of H on the fine grid as double-single pairs, and w = H z in
+// double-single arithmetic (z complex64, w double-single)
+void launch_make_hdiag_ds(const LevelView<double> &L, OpShift<double> s, float4 *hd, cudaStream_t st);
+void launch_apply_H_ds(const LevelView<double> &L, const float4 *hd, const float2 *z, size_t sz,
+                       float4 *w, size_t sw, int nb, const int *active, cudaStream_t st);
+
 // finite check: flag[0] |= 1 if any entry is NaN/Inf
 void launch_finite_check(const double *x, size_t n, int *flag, cudaStream_t st);
 
