@@ -153,6 +153,26 @@ def cpu_baseline(w, budget_s=12.0):
                       f"single-threaded) of the same 401x201 system; mean {mean * 1e3:.1f} ms"}
 
 
+def tune_summary(helm, dim, rep):
+    """Compact record of an autotuner report: per level the chosen (down, up)
+    tile extents and their speed-up over the default shapes, and the smoother
+    counts with each candidate's time to solution."""
+    lv = []
+    for k in range(rep["levels"]):
+        d, u = rep["down_shape"][k], rep["up_shape"][k]
+        lv.append({"down": list(helm.helm_tile_shape(dim, 0, d)[0][:dim]),
+                   "up": list(helm.helm_tile_shape(dim, 1, u)[0][:dim]),
+                   "down_us": round(rep["down_us"][k], 2), "up_us": round(rep["up_us"][k], 2),
+                   "default_us": [round(rep["down_default_us"][k], 2),
+                                  round(rep["up_default_us"][k], 2)]})
+    out = {"levels": lv, "nu": [rep["nu1"], rep["nu2"]]}
+    if rep["nu_candidates"]:
+        out["nu_trials"] = [{"nu": list(c), "ms": round(t, 2), "iterations": it}
+                            for c, t, it in zip(rep["nu_candidates"], rep["nu_ms"],
+                                                rep["nu_iterations"])]
+    return out
+
+
 def serving_run(helm, n_req=16, rate_hz=200.0, seed=0, workers=4):
     """Poisson stream of 2D solves through the serving loop (helm_server_*).
 
@@ -359,6 +379,9 @@ def main():
         gb.set_stream(stream.cuda_stream)
         gb.set_model(md, w.omega(), w.alpha)
         gb.set_shift(*w.beta)
+        # set-up, untimed: the autotuner picks each level's tile shapes and the
+        # smoother counts on this batch
+        tune = gb.autotune(BATCH_SOURCES, Fd, w.tol)
         gb.solve_batch(BATCH_SOURCES, Fd, w.tol, Ud)
         torch.cuda.synchronize()
         bt = []
@@ -376,7 +399,8 @@ def main():
             "solves_per_s": world * BATCH_SOURCES / (bms / 1e3), "nrhs": BATCH_SOURCES,
             "ms_per_batch": bms, "iterations_max": int(bits.max()),
             "iterations_mean": float(bits.mean()), "true_rel_residual_max": float(brr.max()),
-            "vs_plain": (world * BATCH_SOURCES / (bms / 1e3)) / value}
+            "vs_plain": (world * BATCH_SOURCES / (bms / 1e3)) / value,
+            "autotune": tune_summary(helm, 2, tune)}
         del gb
     batched = dict(batched_forms["mixed_ds"])
     batched["precision"] = ("complex64 V-cycle, double-single Arnoldi basis, complex128 "
@@ -390,6 +414,11 @@ def main():
     m2 = torch.from_numpy(wb.slowness().ravel().copy()).to(dev)
     g2 = helm.Grid(wb.n, wb.h, restart=wb.restart, precond="mg", precision="mixed_ds")
     g2.set_stream(stream.cuda_stream)
+    # tile shapes tuned once for this grid and batch (set-up, untimed); the
+    # smoother counts stay (1, 1): trial solves at 20 Hz would take minutes
+    g2.set_model(m2, wb.omega(0), wb.alpha)
+    g2.set_shift(*wb.beta)
+    tune2 = g2.autotune(len(wb.sources), None, wb.tol, tiles=True, smoother=False)
     per_f = []
     torch.cuda.synchronize()
     t_all = time.perf_counter()
@@ -411,7 +440,7 @@ def main():
                                  "sources x {5,10,15,20} Hz, FGMRES(30), complex64 V-cycle, "
                                  "double-single Arnoldi basis, complex128 Hessenberg and residual",
                      "solves": nsol, "wall_s": t_all, "solves_per_s": world * nsol / t_all,
-                     "per_frequency": per_f}
+                     "per_frequency": per_f, "autotune": tune_summary(helm, 2, tune2)}
     del g2, F2, U2
 
     serving = serving_run(helm)

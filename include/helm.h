@@ -195,6 +195,66 @@ helm_status helm_true_residual(helm_grid *g, const helm_c128 *f, const helm_c128
 helm_status helm_true_residual_noalloc(helm_grid *g, int nrhs, const helm_c128 *f,
                                        const helm_c128 *u, double *rel);
 
+/* ------------------------------------------------------------ autotuning
+ * Tile shapes and smoother counts of the multigrid preconditioner (the paper
+ * applies P^-1 approximately without fixing how; these are implementation
+ * parameters, chosen by measurement).
+ *
+ * Tile shapes. The fused V(1,1) level kernels of 2D/3D grids ("down":
+ * pre-smoothing, residual and restriction; "up": prolongation and
+ * post-smoothing) are compiled for helm_num_tile_shapes(dim) shapes each
+ * (0 for 1D). helm_tile_shape gives a shape's extents and block size: for
+ * kernel 0 (down) the block's tile of coarse nodes, for kernel 1 (up) its
+ * tile of fine nodes. The arithmetic per node does not depend on the shape:
+ * results are bitwise identical for every choice. helm_set_tiles /
+ * helm_get_tiles set and read the shapes used on fine level `level` (the
+ * pair level, level+1); every level starts at shape 0.
+ *
+ * helm_autotune(g, nrhs, f, tol, flags, report) measures on the grid's
+ * current model, shift, options and batch size nrhs:
+ *   HELM_TUNE_TILES     every down and up shape on every level, each timed
+ *                       with CUDA events over a graph of 20 launches on the
+ *                       level's own buffers; the fastest is kept per level.
+ *   HELM_TUNE_SMOOTHER  (nu1, nu2) in {(1,1), (2,1), (1,2), (2,2)}: each is
+ *                       used for one untimed and one timed helm_solve_batch of
+ *                       f (nrhs x N, host or device, not modified) to tol; the
+ *                       fastest converged one is kept in the grid's options
+ *                       (only nu = (1,1) runs the fused kernels).
+ * The basis, work vectors and the solution scratch are overwritten; the
+ * model and hierarchy are kept. report (caller-owned) receives the chosen
+ * shapes with their times and the default shape's times per level, and each
+ * smoother candidate's time to solution (-1 if it did not converge) and
+ * largest iteration count. Errors: HELM_ERR_ARG, HELM_ERR_STATE (no model),
+ * HELM_ERR_UNSUPPORTED (preconditioner other than HELM_PRECOND_MG),
+ * HELM_ERR_NOT_CONVERGED (no smoother candidate converged; options kept),
+ * HELM_ERR_NOMEM, HELM_ERR_CUDA. */
+#define HELM_TUNE_TILES 1
+#define HELM_TUNE_SMOOTHER 2
+#define HELM_TUNE_MAX_LEVELS 16
+#define HELM_TUNE_MAX_NU 4
+
+typedef struct {
+    int levels;                                   /* fine levels with a down/up pair */
+    int down_shape[HELM_TUNE_MAX_LEVELS];         /* chosen shape per fine level     */
+    int up_shape[HELM_TUNE_MAX_LEVELS];
+    double down_us[HELM_TUNE_MAX_LEVELS];         /* us per launch, chosen shape     */
+    double up_us[HELM_TUNE_MAX_LEVELS];
+    double down_default_us[HELM_TUNE_MAX_LEVELS]; /* us per launch, shape 0          */
+    double up_default_us[HELM_TUNE_MAX_LEVELS];
+    int n_nu;                                     /* smoother candidates tried       */
+    int nu[HELM_TUNE_MAX_NU][2];
+    double nu_ms[HELM_TUNE_MAX_NU];               /* time to solution, -1 = failed   */
+    int nu_iterations[HELM_TUNE_MAX_NU];
+    int nu1, nu2;                                 /* smoother counts now in use      */
+} helm_tune_report;
+
+int         helm_num_tile_shapes(int dim);
+helm_status helm_tile_shape(int dim, int kernel, int shape, int extent[3], int *threads);
+helm_status helm_set_tiles(helm_grid *g, int level, int down_shape, int up_shape);
+helm_status helm_get_tiles(const helm_grid *g, int level, int *down_shape, int *up_shape);
+helm_status helm_autotune(helm_grid *g, int nrhs, const helm_c128 *f, double tol, int flags,
+                          helm_tune_report *report);
+
 /* Number of multigrid levels (1 = no coarsening; 0 before helm_set_shift)
  * and the node counts and spacing of one level. */
 int         helm_num_levels(const helm_grid *g);

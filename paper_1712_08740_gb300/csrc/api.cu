@@ -126,6 +126,17 @@ helm_status build_hierarchy(helm_grid *g) {
         launch_make_w(C.m.as<double>(), C.N, g->omega, C.w64.as<double>(), C.w32.as<float>(),
                       g->flag.as<int>(), g->st);
     }
+    // inverse diagonal of M per level, in the V-cycle's precision (fused kernels)
+    for (size_t l = 0; l < g->lv.size(); ++l) {
+        MGLevel &L = g->lv[l];
+        const size_t esz = (prec == HELM_PREC_F64) ? sizeof(double2) : sizeof(float2);
+        if ((s = L.dinv.ensure(L.N * esz))) return s;
+        LevelView<double> v = level_view<double>(g, (int)l);
+        if (prec == HELM_PREC_F64)
+            launch_make_dinv<double2>(v, shift_M<double>(g), L.dinv.as<double2>(), g->st);
+        else
+            launch_make_dinv<float2>(v, shift_M<double>(g), L.dinv.as<float2>(), g->st);
+    }
     // coarse inverse
     g->nc = 0;
     if (pc != HELM_PRECOND_NONE) {

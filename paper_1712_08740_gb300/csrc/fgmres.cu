@@ -3,7 +3,7 @@
 //
 // Everything runs on the device. One Arnoldi step j is: the V-cycle
 // z_j = M^-1 v_j (complex64 in the mixed form), w = H z_j written straight
-// into basis slot v_{j+1}, classical Gram-Schmidt (twice by default) as fused
+// into basis slot v_{j+1}, classical Gram-Schmidt (once by default) as fused
 // multi-dot / multi-axpy kernels with the norm fused into the last axpy, the
 // Givens update of the least-squares problem (cycle.cu), and the scaling of
 // v_{j+1}. A cycle ends with y = R^-1 g, x += Z y and the true residual
@@ -245,9 +245,11 @@ long long graph_key_of(const helm_grid *g, int nrhs, double tol) {
     mixp(g->cR.p); mixp(g->cg.p); mixp(g->ccs.p); mixp(g->csn.p); mixp(g->cQ.p); mixp(g->cfn.p);
     mixp(g->ck.p); mixp(g->cits.p); mixp(g->cstat.p); mixp(g->cany.p); mixp(g->hdiag.p); mixp(g->rbuf.p);
     for (const auto &L : g->lv) {
-        mixp(L.w64.p); mixp(L.w32.p); mixp(L.u.p); mixp(L.t.p); mixp(L.b.p); mixp(L.r.p);
+        mixp(L.w64.p); mixp(L.w32.p); mixp(L.dinv.p); mixp(L.u.p); mixp(L.t.p); mixp(L.b.p); mixp(L.r.p);
         mixu((unsigned long long)L.N);
     }
+    for (int t : g->tile_dn) mixu((unsigned long long)t + 17);
+    for (int t : g->tile_up) mixu((unsigned long long)t + 31);
     mixu(g->lv.size()); mixu((unsigned long long)g->nc);
     mixd(g->alpha); mixd(g->beta1); mixd(g->beta2); mixd(g->opt.omega_jacobi); mixd(tol);
     mixu((unsigned long long)nrhs); mixu(g->opt.restart); mixu(g->opt.precond); mixu(g->opt.precision);
@@ -305,6 +307,9 @@ helm_status capture_steps(helm_grid *g, int nrhs, double tol) {
 }
 
 }  // namespace
+
+// Krylov workspace of the grid sized for nrhs right-hand sides.
+helm_status workspace_for(helm_grid *g, int nrhs) { return ensure_workspace(g, nrhs); }
 
 // Core solver on device arrays f (nrhs x N) and u (nrhs x N), stride N.
 helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, double2 *u,
@@ -381,6 +386,9 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         else if (g->opt.precision == HELM_PREC_F64)
             launch_update<double2>(g->Z.as<double2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u,
                                    N, N, nrhs, S.act_cy, st, S.k);
+        else if (ds)
+            launch_update_zds(g->Z.as<float2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u, N, N,
+                              nrhs, S.act_cy, st, S.k);
         else
             launch_update<float2>(g->Z.as<float2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u, N,
                                   N, nrhs, S.act_cy, st, S.k);

@@ -34,6 +34,7 @@ struct MGLevel {
     size_t N = 0;
     DevBuf m;                  // slowness on this level (injected)
     DevBuf w64, w32;           // omega^2 m^2
+    DevBuf dinv;               // 1 / diagonal of M, V-cycle precision (complex)
     DevBuf u, t, b, r;         // V-cycle work vectors, [cap_rhs][N] in the V-cycle type
 };
 
@@ -51,6 +52,7 @@ struct helm_grid {
     double omega = 0.0, alpha = 0.0, beta1 = 1.0, beta2 = 0.5;
 
     std::vector<helm::MGLevel> lv;      // lv[0] is the fine grid
+    std::vector<int> tile_dn, tile_up;  // fused-kernel tile shape per fine level (helm_autotune)
     int vc_prec = -1;                   // precision the hierarchy was built for
     int nc = 0;                         // coarse inverse order
     helm::DevBuf Ainv, colbuf;

@@ -96,6 +96,7 @@ template <typename T> struct LevelView {
     T inv_h2;                // 1 / h^2
     T two_over_h;            // 2 / h
     const T *w;              // omega^2 m^2 per node
+    const cplx_t<T> *dinv;   // 1 / diagonal of M per node (fused V-cycle), or null
 };
 
 // Shift of the zero-order term and the boundary factor q = sqrt(1 - j alpha).
@@ -149,17 +150,26 @@ void launch_prolong_add(const LevelView<T> &fine, const LevelView<T> &coarse,
                         const cplx_t<T> *ec, size_t sc, const cplx_t<T> *uin, size_t sin,
                         cplx_t<T> *uf, size_t sf, int nb, const int *active, cudaStream_t st);
 
+// dinv = 1 / diag(M) on a level (diagonal from Eq. 6 with the absorbing
+// boundary term), computed in FP64 and stored as C (double2 or float2).
+template <typename C>
+void launch_make_dinv(const LevelView<double> &L, OpShift<double> s, C *dinv, cudaStream_t st);
+
 // Fused V(1,1) level kernels for 2D/3D (vfused.cu). CB: type of the level's
 // right-hand side (complex128 basis vector at level 0 of the mixed form).
 template <typename T, typename CB>
-void launch_vdown(const LevelView<T> &F, const LevelView<T> &Cv, OpShift<T> s, T wj, const CB *b,
+void launch_vdown(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB *b,
                   size_t sb, cplx_t<T> *u, size_t su, cplx_t<T> *bc, size_t sbc, int nb,
-                  const int *active, cudaStream_t st);
+                  const int *active, cudaStream_t st, int shape);
 template <typename T, typename CB>
-void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, OpShift<T> s, T wj,
+void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
                 const cplx_t<T> *uin, size_t sin, const cplx_t<T> *ec, size_t sec, const CB *b,
                 size_t sb, cplx_t<T> *uout, size_t sout, int nb, const int *active,
-                cudaStream_t st);
+                cudaStream_t st, int shape);
+// tile shapes of the fused kernels: count per dimension (down and up lists
+// have equal length) and the extents/threads of one (kernel 0 down, 1 up)
+int num_tile_shapes(int dim);
+bool tile_shape(int dim, int kernel, int shape, int ext[3], int *threads);
 void prepare_vfused();   // sets shared-memory attributes; call outside graph capture
 
 // ------------------------------------------------------------ set-up kernels
@@ -236,6 +246,10 @@ template <typename CIn>
 void launch_scale_ds(const CIn *x, size_t sx, const double *norm2, float4 *y, size_t sy, size_t N,
                      int nrhs, const int *active, cudaStream_t st);
 // x += sum_i Z_i y_i where the basis is DS (no preconditioner: Z = V)
+// x += Z y for complex64 Z, the sum formed in double-single (HELM_PREC_MIXED_DS)
+void launch_update_zds(const float2 *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
+                       double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st,
+                       const int *kcount);
 void launch_update_ds(const float4 *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
                       double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st,
                       const int *kcount = nullptr);

@@ -104,17 +104,36 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
         float h[16], l[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) h[q] = l[q] = 0.f;
-        for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N; p += step) {
-            const float4 x = w[p];
+        // two of the thread's nodes per round, all their loads issued before
+        // use; each accumulator still sums the thread's nodes in index order
+        // (a missing second node adds an exact zero)
+        for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N; p += 2 * step) {
+            const size_t p2 = p + step;
+            const bool two = p2 < N;
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 x0 = w[p], x1 = two ? w[p2] : zero;
+            float4 va[kGroup], vb[kGroup];
 #pragma unroll
             for (int q = 0; q < kGroup; ++q) {
                 if (i0 + q < nvec) {
-                    const float4 v = V[(size_t)(i0 + q) * N + p];
+                    va[q] = V[(size_t)(i0 + q) * N + p];
+                    vb[q] = two ? V[(size_t)(i0 + q) * N + p2] : zero;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) {
+                if (i0 + q < nvec) {
                     // conj(v) x: re = vr xr + vi xi, im = vr xi - vi xr
-                    ds_fma(h[2 * q], l[2 * q], v.x, v.y, x.x, x.y);
-                    ds_fma(h[2 * q], l[2 * q], v.z, v.w, x.z, x.w);
-                    ds_fma(h[2 * q + 1], l[2 * q + 1], v.x, v.y, x.z, x.w);
-                    ds_fma(h[2 * q + 1], l[2 * q + 1], -v.z, -v.w, x.x, x.y);
+                    const float4 v = va[q];
+                    ds_fma(h[2 * q], l[2 * q], v.x, v.y, x0.x, x0.y);
+                    ds_fma(h[2 * q], l[2 * q], v.z, v.w, x0.z, x0.w);
+                    ds_fma(h[2 * q + 1], l[2 * q + 1], v.x, v.y, x0.z, x0.w);
+                    ds_fma(h[2 * q + 1], l[2 * q + 1], -v.z, -v.w, x0.x, x0.y);
+                    const float4 u = vb[q];
+                    ds_fma(h[2 * q], l[2 * q], u.x, u.y, x1.x, x1.y);
+                    ds_fma(h[2 * q], l[2 * q], u.z, u.w, x1.z, x1.w);
+                    ds_fma(h[2 * q + 1], l[2 * q + 1], u.x, u.y, x1.z, x1.w);
+                    ds_fma(h[2 * q + 1], l[2 * q + 1], -u.z, -u.w, x1.x, x1.y);
                 }
             }
         }
@@ -192,20 +211,31 @@ k_multiaxpy_ds(const float4 *__restrict__ V, size_t sV, int nvec, const double2 
         cs[i] = cvt<float4>(make_double2(-ci.x, -ci.y));
     }
     __syncthreads();
-    double n2 = 0.0;
+    // ||w||^2 accumulates in double-single as well (the FP64 pipe would spend
+    // four instructions per node on it); it is joined into a double once per
+    // thread, before the deterministic block and grid reductions.
+    float nh = 0.f, nl = 0.f;
     for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N;
          p += (size_t)gridDim.x * kThreads) {
         const float4 x = w[p];
         float rh = x.x, rl = x.y, ih = x.z, il = x.w;
-#pragma unroll 2
-        for (int i = 0; i < nvec; ++i) {
-            const float4 v = V[(size_t)i * N + p];
-            const float4 m = cs[i];   // -c_i
-            // w += v * (-c): re = vr mr - vi mi, im = vr mi + vi mr
-            ds_fma(rh, rl, v.x, v.y, m.x, m.y);
-            ds_fma(rh, rl, -v.z, -v.w, m.z, m.w);
-            ds_fma(ih, il, v.x, v.y, m.z, m.w);
-            ds_fma(ih, il, v.z, v.w, m.x, m.y);
+        // eight basis loads in flight before they are used
+        for (int i0 = 0; i0 < nvec; i0 += kGroup) {
+            float4 v[kGroup];
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q)
+                if (i0 + q < nvec) v[q] = V[(size_t)(i0 + q) * N + p];
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) {
+                if (i0 + q < nvec) {
+                    const float4 m = cs[i0 + q];   // -c_i
+                    // w += v * (-c): re = vr mr - vi mi, im = vr mi + vi mr
+                    ds_fma(rh, rl, v[q].x, v[q].y, m.x, m.y);
+                    ds_fma(rh, rl, -v[q].z, -v[q].w, m.z, m.w);
+                    ds_fma(ih, il, v[q].x, v[q].y, m.z, m.w);
+                    ds_fma(ih, il, v[q].z, v[q].w, m.x, m.y);
+                }
+            }
         }
         // renormalise (h, l) and store
         float th = rh + rl;
@@ -216,11 +246,11 @@ k_multiaxpy_ds(const float4 *__restrict__ V, size_t sV, int nvec, const double2 
         ih = th;
         w[p] = make_float4(rh, rl, ih, il);
         if (norm2) {
-            const double a = ds_join(rh, rl), b = ds_join(ih, il);
-            n2 = fma(a, a, fma(b, b, n2));
+            ds_fma(nh, nl, rh, rl, rh, rl);
+            ds_fma(nh, nl, ih, il, ih, il);
         }
     }
-    if (norm2) reduce_norm(n2, partial_d, counter, norm2, r);
+    if (norm2) reduce_norm(ds_join(nh, nl), partial_d, counter, norm2, r);
 }
 
 template <typename CIn> __device__ __forceinline__ float4 ds_scaled(CIn x, float sh, float sl, double s);
@@ -298,6 +328,60 @@ k_update_ds(const float4 *__restrict__ Z, size_t sZ, int nvec, const double2 *__
     }
 }
 
+// acc += a * b with a exact in FP32 and b double-single (acc unnormalised)
+__device__ __forceinline__ void ds_fma1(float &h, float &l, float a, float bh, float bl) {
+    const float p = a * bh;
+    float e = fmaf(a, bh, -p);
+    e = fmaf(a, bl, e);
+    const float s = h + p;
+    const float bb = s - h;
+    const float err = (h - (s - bb)) + (p - bb);
+    h = s;
+    l += err + e;
+}
+
+// x += sum_i Z_i y_i for complex64 z_i (exact in FP32): the sum is formed in
+// double-single on the FP32 pipe and added to the complex128 x once per node
+// (two FP64 additions per component instead of 4 FMAs per basis vector).
+__global__ void __launch_bounds__(kThreads)
+k_update_zds(const float2 *__restrict__ Z, size_t sZ, int nvec, const double2 *__restrict__ yv,
+             size_t ystride, double2 *__restrict__ x, size_t sx, size_t N,
+             const int *__restrict__ active, const int *__restrict__ kcount) {
+    const int r = blockIdx.y;
+    if (active && !active[r]) return;
+    if (kcount) nvec = min(nvec, kcount[r]);
+    Z += r * sZ;
+    x += r * sx;
+    __shared__ float4 ys[kMaxVec];   // (re_hi, re_lo, im_hi, im_lo) of y_i
+    for (int i = threadIdx.x; i < nvec; i += kThreads) ys[i] = cvt<float4>(yv[r * ystride + i]);
+    __syncthreads();
+    for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N;
+         p += (size_t)gridDim.x * kThreads) {
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        for (int i0 = 0; i0 < nvec; i0 += kGroup) {
+            float2 z[kGroup];
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q)
+                if (i0 + q < nvec) z[q] = Z[(size_t)(i0 + q) * N + p];
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) {
+                if (i0 + q < nvec) {
+                    const float4 y = ys[i0 + q];
+                    // re += zr yr - zi yi, im += zr yi + zi yr
+                    ds_fma1(rh, rl, z[q].x, y.x, y.y);
+                    ds_fma1(rh, rl, -z[q].y, y.z, y.w);
+                    ds_fma1(ih, il, z[q].x, y.z, y.w);
+                    ds_fma1(ih, il, z[q].y, y.x, y.y);
+                }
+            }
+        }
+        double2 acc = x[p];
+        acc.x += ds_join(rh, rl);
+        acc.y += ds_join(ih, il);
+        x[p] = acc;
+    }
+}
+
 inline int sm_blocks_for(size_t N, int per_thread, int cap) {
     const size_t per_wave = (size_t)152 * kThreads * per_thread;
     int k = 1;
@@ -356,6 +440,17 @@ void launch_update_ds(const float4 *Z, size_t sZ, int nvec, const double2 *y, si
                                                      kcount);
     count_launch();
     if (prof_on()) prof_end("update_ds", st, (16.0 * nvec + 32.0) * N * nrhs, 8.0 * nvec * N * nrhs);
+}
+
+void launch_update_zds(const float2 *Z, size_t sZ, int nvec, const double2 *y, size_t y_stride,
+                       double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st,
+                       const int *kcount) {
+    const int nb = blocks_for(N, 1 << 16);
+    prof_begin(st);
+    k_update_zds<<<dim3(nb, nrhs), kThreads, 0, st>>>(Z, sZ, nvec, y, y_stride, x, sx, N, active,
+                                                      kcount);
+    count_launch();
+    if (prof_on()) prof_end("update_zds", st, (8.0 * nvec + 32.0) * N * nrhs, 4.0 * N * nrhs);
 }
 
 template void launch_scale_ds<double2>(const double2 *, size_t, const double *, float4 *, size_t,

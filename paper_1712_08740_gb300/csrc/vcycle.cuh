@@ -24,6 +24,9 @@ helm_status check_cuda(const char *where);
 helm_status sync_stream(helm_grid *g, const char *where);
 helm_status ensure_ready(helm_grid *g);
 helm_status ensure_level_work(helm_grid *g, int nrhs);
+helm_status workspace_for(helm_grid *g, int nrhs);
+helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, double2 *u,
+                         int *iterations, double *relres_out);
 const char *last_error();
 
 template <typename T> inline LevelView<T> level_view(const helm_grid *g, int l) {
@@ -36,7 +39,18 @@ template <typename T> inline LevelView<T> level_view(const helm_grid *g, int l) 
     v.inv_h2 = (T)(1.0 / (L.h * L.h));
     v.two_over_h = (T)(2.0 / L.h);
     v.w = (sizeof(T) == sizeof(double)) ? (const T *)L.w64.p : (const T *)L.w32.p;
+    // the inverse diagonal exists in the V-cycle's own precision only
+    const bool match = (sizeof(T) == sizeof(double)) == (g->vc_prec == HELM_PREC_F64);
+    v.dinv = match ? (const cplx_t<T> *)L.dinv.p : nullptr;
     return v;
+}
+
+// tile shape of the fused kernels on fine level l (0 = default shape)
+inline int tile_down(const helm_grid *g, int l) {
+    return l < (int)g->tile_dn.size() ? g->tile_dn[l] : 0;
+}
+inline int tile_up(const helm_grid *g, int l) {
+    return l < (int)g->tile_up.size() ? g->tile_up[l] : 0;
 }
 
 inline std::complex<double> q_of(double alpha) {
@@ -74,12 +88,12 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
             const LevelView<T> F = level_view<T>(g, l), Cv = level_view<T>(g, l + 1);
             C *bc = g->lv[l + 1].b.template as<C>();
             if (l == 0)
-                launch_vdown<T, CB0>(F, Cv, sM, wj, b0, sb0, g->lv[0].t.template as<C>(), g->lv[0].N,
-                                     bc, g->lv[1].N, nb, act, st);
+                launch_vdown<T, CB0>(F, Cv, wj, b0, sb0, g->lv[0].t.template as<C>(), g->lv[0].N,
+                                     bc, g->lv[1].N, nb, act, st, tile_down(g, 0));
             else
-                launch_vdown<T, C>(F, Cv, sM, wj, g->lv[l].b.template as<C>(), g->lv[l].N,
+                launch_vdown<T, C>(F, Cv, wj, g->lv[l].b.template as<C>(), g->lv[l].N,
                                    g->lv[l].t.template as<C>(), g->lv[l].N, bc, g->lv[l + 1].N, nb,
-                                   act, st);
+                                   act, st, tile_down(g, l));
         }
         C *uc = (L - 1 == 0) ? u0 : g->lv[L - 1].u.template as<C>();
         launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, g->lv[L - 1].b.template as<C>(),
@@ -89,12 +103,12 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
             const LevelView<T> F = level_view<T>(g, l), Cv = level_view<T>(g, l + 1);
             const C *ec = g->lv[l + 1].u.template as<C>();
             if (l == 0)
-                launch_vup<T, CB0>(F, Cv, sM, wj, g->lv[0].t.template as<C>(), g->lv[0].N, ec,
-                                   g->lv[1].N, b0, sb0, u0, su0, nb, act, st);
+                launch_vup<T, CB0>(F, Cv, wj, g->lv[0].t.template as<C>(), g->lv[0].N, ec,
+                                   g->lv[1].N, b0, sb0, u0, su0, nb, act, st, tile_up(g, 0));
             else
-                launch_vup<T, C>(F, Cv, sM, wj, g->lv[l].t.template as<C>(), g->lv[l].N, ec,
+                launch_vup<T, C>(F, Cv, wj, g->lv[l].t.template as<C>(), g->lv[l].N, ec,
                                  g->lv[l + 1].N, g->lv[l].b.template as<C>(), g->lv[l].N,
-                                 g->lv[l].u.template as<C>(), g->lv[l].N, nb, act, st);
+                                 g->lv[l].u.template as<C>(), g->lv[l].N, nb, act, st, tile_up(g, l));
         }
         return;
     }

@@ -31,7 +31,8 @@ EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "he
             "helm_last_error", "helm_kernel_launches", "helm_profile_start", "helm_profile_stop",
             "helm_time_kernel", "helm_true_residual_noalloc", "helm_solve_footprint",
             "helm_server_create", "helm_server_submit", "helm_server_wait", "helm_server_poll",
-            "helm_server_clock", "helm_server_destroy")
+            "helm_server_clock", "helm_server_destroy", "helm_num_tile_shapes", "helm_tile_shape",
+            "helm_set_tiles", "helm_get_tiles", "helm_autotune")
 
 
 class helm_options(ctypes.Structure):
@@ -57,6 +58,26 @@ class helm_result(ctypes.Structure):
                 ("iterations_max", ctypes.c_int), ("true_rel_residual_max", ctypes.c_double),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t)]
+
+
+HELM_TUNE_TILES, HELM_TUNE_SMOOTHER = 1, 2
+HELM_TUNE_MAX_LEVELS, HELM_TUNE_MAX_NU = 16, 4
+
+
+class helm_tune_report(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int),
+                ("down_shape", ctypes.c_int * HELM_TUNE_MAX_LEVELS),
+                ("up_shape", ctypes.c_int * HELM_TUNE_MAX_LEVELS),
+                ("down_us", ctypes.c_double * HELM_TUNE_MAX_LEVELS),
+                ("up_us", ctypes.c_double * HELM_TUNE_MAX_LEVELS),
+                ("down_default_us", ctypes.c_double * HELM_TUNE_MAX_LEVELS),
+                ("up_default_us", ctypes.c_double * HELM_TUNE_MAX_LEVELS),
+                ("n_nu", ctypes.c_int),
+                ("nu", (ctypes.c_int * 2) * HELM_TUNE_MAX_NU),
+                ("nu_ms", ctypes.c_double * HELM_TUNE_MAX_NU),
+                ("nu_iterations", ctypes.c_int * HELM_TUNE_MAX_NU),
+                ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int)]
 
 
 class HelmError(RuntimeError):
@@ -104,6 +125,11 @@ def _load():
         "helm_server_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(I)]),
         "helm_server_clock": (D, [P]),
         "helm_server_destroy": (None, [P]),
+        "helm_num_tile_shapes": (I, [I]),
+        "helm_tile_shape": (I, [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "helm_set_tiles": (I, [P, I, I, I]),
+        "helm_get_tiles": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "helm_autotune": (I, [P, I, P, D, I, ctypes.POINTER(helm_tune_report)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -265,6 +291,45 @@ def helm_time_kernel(g, kernel, j, reps):
     return us.value, b.value, fl.value
 
 
+def helm_num_tile_shapes(dim):
+    return _lib.helm_num_tile_shapes(int(dim))
+
+
+def helm_tile_shape(dim, kernel, shape):
+    """((sx, sy, sz), threads) of a fused-kernel tile shape; kernel 0 = down, 1 = up."""
+    ext, nt = (ctypes.c_int * 3)(), ctypes.c_int()
+    _check(_lib.helm_tile_shape(int(dim), int(kernel), int(shape), ext, ctypes.byref(nt)))
+    return tuple(ext), nt.value
+
+
+def helm_set_tiles(g, level, down_shape, up_shape):
+    _check(_lib.helm_set_tiles(g, int(level), int(down_shape), int(up_shape)))
+
+
+def helm_get_tiles(g, level):
+    d, u = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.helm_get_tiles(g, int(level), ctypes.byref(d), ctypes.byref(u)))
+    return d.value, u.value
+
+
+def helm_autotune(g, nrhs, f, tol, flags):
+    """Runs the autotuner; returns its report as a dict."""
+    rep = helm_tune_report()
+    fp = _ptr(f, np.complex128) if f is not None else None
+    _check(_lib.helm_autotune(g, int(nrhs), fp, float(tol), int(flags), ctypes.byref(rep)))
+    L = rep.levels
+    return {
+        "levels": L,
+        "down_shape": list(rep.down_shape[:L]), "up_shape": list(rep.up_shape[:L]),
+        "down_us": list(rep.down_us[:L]), "up_us": list(rep.up_us[:L]),
+        "down_default_us": list(rep.down_default_us[:L]),
+        "up_default_us": list(rep.up_default_us[:L]),
+        "nu_candidates": [tuple(rep.nu[k]) for k in range(rep.n_nu)],
+        "nu_ms": list(rep.nu_ms[:rep.n_nu]), "nu_iterations": list(rep.nu_iterations[:rep.n_nu]),
+        "nu1": rep.nu1, "nu2": rep.nu2,
+    }
+
+
 # ------------------------------------------------------------------ convenience wrapper
 
 class Grid:
@@ -323,6 +388,16 @@ class Grid:
 
     def time_kernel(self, kernel, j, reps=50):
         return helm_time_kernel(self._g, kernel, j, reps)
+
+    def autotune(self, nrhs, f, tol, tiles=True, smoother=True):
+        flags = (HELM_TUNE_TILES if tiles else 0) | (HELM_TUNE_SMOOTHER if smoother else 0)
+        return helm_autotune(self._g, nrhs, f, tol, flags)
+
+    def set_tiles(self, level, down_shape, up_shape):
+        helm_set_tiles(self._g, level, down_shape, up_shape)
+
+    def get_tiles(self, level):
+        return helm_get_tiles(self._g, level)
 
     @property
     def num_levels(self):

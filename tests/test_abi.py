@@ -72,3 +72,26 @@ def test_solve_footprint_scales(lib):
     o.precision = 1
     assert lib.helm_solve_footprint(2, (401, 201), 8, o) < b
     assert lib.helm_solve_footprint(0, (401, 201), 8, o) == 0
+
+
+def test_tile_shape_queries_without_gpu(lib):
+    assert lib.helm_num_tile_shapes(1) == 0
+    for dim in (2, 3):
+        n = lib.helm_num_tile_shapes(dim)
+        assert n >= 2
+        seen = set()
+        for kernel in (0, 1):
+            for s in range(n):
+                ext, nt = lib.helm_tile_shape(dim, kernel, s)
+                assert nt in (64, 128, 256, 512) and all(e >= 1 for e in ext)
+                if dim == 2:
+                    assert ext[2] == 1
+                if kernel == 1:                      # up tiles start on even fine nodes
+                    assert all(e % 2 == 0 for e in ext[:dim])
+                seen.add((kernel, ext, nt))
+        assert len(seen) == 2 * n                    # no duplicate shapes
+        with pytest.raises(lib.HelmError) as e:
+            lib.helm_tile_shape(dim, 0, n)
+        assert e.value.status == 1
+    with pytest.raises(lib.HelmError):
+        lib.helm_tile_shape(2, 2, 0)
