@@ -9,8 +9,10 @@ raises at import: there is no other code path.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -139,6 +141,24 @@ def _load():
 
 
 _lib = _load()
+
+
+# Grids and servers still open at interpreter exit are closed by an atexit
+# hook, while the CUDA runtime is still up: left to the garbage collector they
+# would free device memory during interpreter teardown, after the runtime may
+# have begun unloading.
+_live = weakref.WeakSet()
+
+
+def _close_live():
+    for obj in list(_live):
+        try:
+            obj.close()
+        except Exception:
+            pass
+
+
+atexit.register(_close_live)
 
 
 def _check(status):
@@ -341,6 +361,7 @@ class Grid:
         self.N = int(np.prod(self.n))
         self.h = float(h)
         self._g = helm_create_grid(len(self.n), self.n, h)
+        _live.add(self)
         self.set_options(restart=restart, precond=precond, precision=precision, nu1=nu1,
                          nu2=nu2, omega_jacobi=omega_jacobi, coarse_max=coarse_max,
                          reorth=reorth, max_iters=max_iters, graphs=graphs)
@@ -474,6 +495,7 @@ class Server:
         cfg = helm_server_config(int(workers), int(memory_budget), o, float(beta[0]), float(beta[1]))
         self._s = helm_server_create(cfg)
         self._keep = {}
+        _live.add(self)
 
     def submit(self, n, h, m, omega, alpha, f, tol):
         """Queues one request; f is (nrhs, N) complex128, m (N,) float64 (host)."""
