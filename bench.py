@@ -281,6 +281,9 @@ def main():
     fd = torch.from_numpy(f.ravel().copy()).to(dev)
     ud = torch.empty_like(fd)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    # set-up, untimed: tile shapes of the fused V-cycle kernels timed per level
+    # (shapes do not change the arithmetic); smoother counts stay (1, 1)
+    tune_plain = g.autotune(1, None, w.tol, tiles=True, smoother=False)
 
     for _ in range(args.warmup):
         g.solve(fd, w.tol, ud)
@@ -489,7 +492,7 @@ def main():
             "config": {"workload": WORKLOAD_DESC, "unknowns": N, "restart": w.restart,
                        "l2": "256 MiB buffer written between timed steps",
                        "parallelism": f"replicas x{world} (independent solves, no collective)",
-                       "setup_ms": setup_ms},
+                       "setup_ms": setup_ms, "tiles": tune_summary(helm, 2, tune_plain)},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "iterations": int(np.median(its_l)), "true_rel_residual_max": float(max(rr_l)),
             "clocks": clk,

@@ -208,7 +208,9 @@ helm_status helm_true_residual_noalloc(helm_grid *g, int nrhs, const helm_c128 *
  * tile of fine nodes. The arithmetic per node does not depend on the shape:
  * results are bitwise identical for every choice. helm_set_tiles /
  * helm_get_tiles set and read the shapes used on fine level `level` (the
- * pair level, level+1); every level starts at shape 0.
+ * pair level, level+1); -1 (the initial setting) selects the shape
+ * automatically per solve: the first shape whose grid has at least 2 x 152
+ * blocks for the batch, else the shape with the most blocks.
  *
  * helm_autotune(g, nrhs, f, tol, flags, report) measures on the grid's
  * current model, shift, options and batch size nrhs:
@@ -239,7 +241,7 @@ typedef struct {
     int up_shape[HELM_TUNE_MAX_LEVELS];
     double down_us[HELM_TUNE_MAX_LEVELS];         /* us per launch, chosen shape     */
     double up_us[HELM_TUNE_MAX_LEVELS];
-    double down_default_us[HELM_TUNE_MAX_LEVELS]; /* us per launch, shape 0          */
+    double down_default_us[HELM_TUNE_MAX_LEVELS]; /* us per launch, automatic shape  */
     double up_default_us[HELM_TUNE_MAX_LEVELS];
     int n_nu;                                     /* smoother candidates tried       */
     int nu[HELM_TUNE_MAX_NU][2];

@@ -142,47 +142,52 @@ __device__ __forceinline__ cplx_t<T> quarter_dot(const cplx_t<T> *__restrict__ r
     return out;
 }
 
-// Work layout shared by both GEMV kernels: a block of 8 warps handles a pair
-// of rows; warp w takes quarter (w % 4) of row (w / 4), so each SM
-// sub-partition (warp w runs on sub-partition w % 4) gets the same share of
-// the FP64 work; the four quarter sums are added in a fixed order. Quarters
-// start on multiples of 32 columns. The arithmetic per row is the same in both
-// kernels, so batched and single solves agree bitwise.
+// Arithmetic per row shared by both GEMV kernels: each row is split into four
+// quarters (starting on multiples of 32 columns), a warp forms each quarter's
+// dot product (quarter_dot), and the four quarter sums are added in order
+// 0..3. The kernels differ only in which warps and blocks handle which rows,
+// so batched and single solves agree bitwise.
 __device__ __forceinline__ void quarter_range(int n, int q, int &c0, int &c1) {
     const int Q = ((n + 127) / 128) * 32;
     c0 = min(q * Q, n);
     c1 = min((q + 1) * Q, n);
 }
 
-// z = Ainv r for one right-hand side; row pairs strided over the grid
+// z = Ainv r for one right-hand side. The rows are split into one contiguous
+// range per block (one block per SM, 152 blocks), so every SM gets the same
+// number of rows up to one; a block of 16 warps runs four rows at a time,
+// warp w taking quarter (w % 4) of row slot (w / 4), so each SM sub-partition
+// (warp w runs on sub-partition w % 4) gets the same share of the FP64 work
+// and four warps per sub-partition hide the load latency.
+constexpr int kG1Warps = 16;
+
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kG1Warps * 32, 1)
 k_dense_gemv1(const cplx_t<T> *__restrict__ Ainv, int n, const cplx_t<T> *__restrict__ r,
               cplx_t<T> *__restrict__ z, const int *__restrict__ active) {
     if (active && !active[0]) return;
-    __shared__ cplx_t<T> part[2][4];
+    extern __shared__ unsigned char smem_raw[];
+    cplx_t<T> *part = reinterpret_cast<cplx_t<T> *>(smem_raw);   // [row of the block][quarter]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = warp & 3, half = warp >> 2;
+    const int q = warp & 3, slot = warp >> 2;
+    const int r0 = (int)((long long)blockIdx.x * n / gridDim.x);
+    const int r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
     int c0, c1;
     quarter_range(n, q, c0, c1);
-    const int npairs = (n + 1) / 2;
-    for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
-        const int i = 2 * pr + half;
-        if (i < n) {
-            const cplx_t<T> v = quarter_dot<T>(Ainv + (size_t)i * n, r, c0, c1, lane);
-            if (lane == 0) part[half][q] = v;
+    for (int i = r0 + slot; i < r1; i += kG1Warps / 4) {
+        const cplx_t<T> v = quarter_dot<T>(Ainv + (size_t)i * n, r, c0, c1, lane);
+        if (lane == 0) part[(i - r0) * 4 + q] = v;
+    }
+    __syncthreads();
+    // quarters added in order 0..3, as in k_dense_gemv
+    for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
+        const cplx_t<T> *pq = part + (size_t)(i - r0) * 4;
+        cplx_t<T> s = pq[0];
+        for (int k = 1; k < 4; ++k) {
+            s.x += pq[k].x;
+            s.y += pq[k].y;
         }
-        __syncthreads();
-        if (threadIdx.x < 2 && 2 * pr + (int)threadIdx.x < n) {
-            const int hh = threadIdx.x;
-            cplx_t<T> s = part[hh][0];
-            for (int k = 1; k < 4; ++k) {
-                s.x += part[hh][k].x;
-                s.y += part[hh][k].y;
-            }
-            z[2 * pr + hh] = s;
-        }
-        __syncthreads();
+        z[i] = s;
     }
 }
 
@@ -251,9 +256,11 @@ void launch_dense_gemv(const cplx_t<T> *Ainv, int n, const cplx_t<T> *r, size_t 
                        cplx_t<T> *z, size_t sz, int nb, const int *active, cudaStream_t st) {
     const int npairs = (n + 1) / 2;
     prof_begin(st);
-    if (nb == 1)
-        k_dense_gemv1<T><<<npairs < 152 ? npairs : 152, 256, 0, st>>>(Ainv, n, r, z, active);
-    else
+    if (nb == 1) {
+        const int blocks = n < 152 ? n : 152;
+        const size_t sm = (size_t)((n + blocks - 1) / blocks) * 4 * sizeof(cplx_t<T>);
+        k_dense_gemv1<T><<<blocks, kG1Warps * 32, sm, st>>>(Ainv, n, r, z, active);
+    } else
         k_dense_gemv<T><<<dim3(npairs, (nb + kRT - 1) / kRT), 256, 0, st>>>(Ainv, n, r, sr, z, sz, nb,
                                                                              active);
     count_launch();

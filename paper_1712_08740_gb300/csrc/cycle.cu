@@ -1,10 +1,11 @@
 // Device-side bookkeeping of restarted flexible GMRES (Eq. 7), so that a whole
 // Arnoldi cycle runs without a host round trip:
 //   k_cycle_init   ||f|| and the first cycle's beta, flags
-//   k_givens       after each Arnoldi step: new Hessenberg column (from the
-//                  two Gram-Schmidt passes and the norm), earlier rotations,
-//                  a new complex Givens rotation (real cosine), the residual
-//                  estimate |g_{j+1}|, and the stop decision
+//   k_givens_scale after each Arnoldi step: new Hessenberg column (from the
+//                  Gram-Schmidt passes and the norm), earlier rotations, a
+//                  new complex Givens rotation (real cosine), the residual
+//                  estimate |g_{j+1}| and the stop decision, side by side
+//                  with the scaling of the new basis vector
 //   k_backsolve    y = R^-1 g for the steps taken in the cycle
 //   k_cycle_check  true residual -> converged / give up / next cycle
 // Each kernel publishes "any right-hand side still active" to a host-mapped
@@ -47,92 +48,148 @@ __global__ void k_cycle_init(CycleState S, const double *__restrict__ nrm2, int 
     if (threadIdx.x == 0 && host_flag) *(volatile int *)host_flag = any;
 }
 
-// One warp per right-hand side. The product of the rotations so far is kept
+// Scaling of the new basis vector v_{j+1} = w / ||w|| in the basis type.
+template <typename SV> struct ScaleOp;
+template <> struct ScaleOp<double2> {
+    __device__ static double2 apply(double2 x, double s, float, float) {
+        return make_double2(x.x * s, x.y * s);
+    }
+};
+template <> struct ScaleOp<float4> {       // double-single x times double-single s
+    __device__ static float4 apply(float4 x, double, float sh, float sl) {
+        float4 o;
+        {
+            const float p = x.x * sh;
+            float e = fmaf(x.x, sh, -p);
+            e = fmaf(x.x, sl, fmaf(x.y, sh, e));
+            o.x = p + e;
+            o.y = e - (o.x - p);
+        }
+        {
+            const float p = x.z * sh;
+            float e = fmaf(x.z, sh, -p);
+            e = fmaf(x.z, sl, fmaf(x.w, sh, e));
+            o.z = p + e;
+            o.w = e - (o.z - p);
+        }
+        return o;
+    }
+};
+
+constexpr int kGivensThreads = 256;
+
+// The end of an Arnoldi step, one launch: one block per right-hand side
+// updates its least-squares problem, the other blocks scale w = slot j+1 into
+// v_{j+1} = w / ||w||. The two parts only read what the
+// Gram-Schmidt kernels wrote, so they run side by side.
+//
+// Least-squares update. The product of the rotations so far is kept
 // explicitly, Q_j = G_{j-1} ... G_0 (lower Hessenberg, column-major per
-// right-hand side), so rotating the new Hessenberg column is a lane-parallel
-// product Q_j h instead of a serial chain of j rotations: on GB300 every FP64
-// warp instruction holds the SM's FP64 pipe for ~16 cycles whatever the lane
-// mask, so short dependent chains matter. Lane 0 builds the new complex
-// rotation (real cosine) from the last two entries; the warp then writes the
-// rotated column into R and the two new rows of Q. Entries of Q outside the
+// right-hand side), so rotating the new Hessenberg column h is the product
+// Q_j h rather than a serial chain of j rotations: on GB300 the FP64 pipe
+// takes ~16 cycles per warp instruction, so long dependent chains are slow.
+// The block stages Q_j in shared memory with every load in flight, forms
+// Q_j h with 8 threads per row, and thread 0 builds the new complex rotation
+// (real cosine) from the last two entries; the block then writes the rotated
+// column into R and the two new rows of Q. Entries of Q outside the
 // Hessenberg profile are never read, so Q needs no clearing between cycles:
 // only Q[0][0] = 1 is set when a cycle starts. "Any right-hand side still
-// stepping" is combined across blocks with an atomic and a last-block ticket,
-// whose block publishes it to the host-mapped flag.
-__global__ void k_givens(CycleState S, int j, const double2 *__restrict__ hb, int hstride, int two,
-                         const double *__restrict__ nrm2, int nrhs, double tol, int max_iters,
-                         int *host_flag, int *any_dev, unsigned *ticket, int q_in_smem) {
+// stepping" is combined over the right-hand sides with an atomic and a ticket;
+// the last least-squares block publishes it to the host-mapped flag.
+//
+// A scaling block that reads the stop decision of its right-hand side before
+// or after block 0 writes it produces the same result for every vector that
+// is ever used again: a stopped right-hand side's v_{j+1} is never read.
+template <typename SV>
+__global__ void __launch_bounds__(kGivensThreads)
+k_givens_scale(CycleState S, int j, const double2 *__restrict__ hb, int hstride, int two,
+               const double *__restrict__ nrm2, int nrhs, double tol, int max_iters,
+               int *host_flag, int q_in_smem, SV *__restrict__ w, size_t sw, size_t N) {
+    // blocks in launch order: the nrhs least-squares blocks first (their
+    // latency then overlaps the scaling), then nbs scaling blocks per
+    // right-hand side
+    const int nbs = gridDim.x - 1;
+    const long long lin = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    const int tid = threadIdx.x;
+    if (lin >= nrhs) {
+        const long long ls = lin - nrhs;
+        const int r = (int)(ls / nbs);
+        const int bx = (int)(ls % nbs);
+        if (!S.act_it[r]) return;
+        __shared__ double s_sh;
+        __shared__ float2 s_ds;
+        if (tid == 0) {
+            s_sh = 1.0 / sqrt(nrm2[r]);
+            s_ds = ds_split(s_sh);
+        }
+        __syncthreads();
+        const double s = s_sh;
+        const float2 sd = s_ds;
+        SV *wr = w + (size_t)r * sw;
+        for (size_t p = (size_t)bx * kGivensThreads + tid; p < N; p += (size_t)nbs * kGivensThreads)
+            wr[p] = ScaleOp<SV>::apply(wr[p], s, sd.x, sd.y);
+        return;
+    }
+    const int r = (int)lin;
     extern __shared__ unsigned char smem_raw[];
     const int m = S.m;
     const int ld = m + 1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.x * (blockDim.x >> 5) + warp;
-    double2 *h = reinterpret_cast<double2 *>(smem_raw) + (size_t)warp * (2 * ld);
+    double2 *h = reinterpret_cast<double2 *>(smem_raw);
     double2 *rot = h + ld;
-    // with one warp per block, Q_j (its Hessenberg profile) is staged in shared memory
-    double2 *Qs = (blockDim.x == 32 && q_in_smem) ? rot + ld : nullptr;
+    double2 *Qs = q_in_smem ? rot + ld : nullptr;
+    __shared__ double sh_cs;
+    __shared__ double2 sh_sv;
+    __shared__ int sh_stop;
     int live = 0;
-    if (r < nrhs && S.act_it[r]) {
+    if (S.act_it[r]) {                       // block-uniform
         double2 *R = S.R + (size_t)r * ld * m + (size_t)j * ld;
         double2 *Q = S.Q + (size_t)r * ld * ld;
         double2 *g = S.g + (size_t)r * ld;
-        bool finite = true;
-        for (int i = lane; i <= j; i += 32) {
+        int fin = 1;
+        for (int i = tid; i <= j; i += kGivensThreads) {
             double2 v = hb[(size_t)r * hstride + i];
             if (two) v = cadd(v, hb[(size_t)r * hstride + ld + i]);
-            finite = finite && isfinite(v.x) && isfinite(v.y);
+            fin &= isfinite(v.x) && isfinite(v.y);
             h[i] = v;
         }
-        const double hn = sqrt(nrm2[r]);
-        finite = __all_sync(0xffffffffu, finite) && isfinite(hn);
         if (Qs) {
-            // columns c <= j of Q_j copied as one contiguous block of (j+1) * ld
-            // values (column-major), eight independent loads in flight per lane
+            // columns c <= j of Q_j, one contiguous block of (j + 1) * ld values
             const int nq = (j + 1) * ld;
-            for (int t0 = lane; t0 < nq; t0 += 32 * 8) {
-                double2 v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int t = t0 + 32 * u;
-                    if (t < nq) v[u] = Q[t];
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int t = t0 + 32 * u;
-                    if (t < nq) Qs[t] = v[u];
-                }
-            }
+            for (int t = tid; t < nq; t += kGivensThreads) Qs[t] = Q[t];
         }
-        __syncwarp();
+        const double hn = sqrt(nrm2[r]);
+        const int finite = __syncthreads_and(fin) && isfinite(hn);
         const double2 *Qr = Qs ? Qs : Q;
         if (!finite) {
-            if (lane == 0) {
+            if (tid == 0) {
                 S.status[r] = ST_BROKE;
                 S.act_it[r] = 0;
                 S.act_cy[r] = 0;
             }
         } else {
-            // rotated h: rot[i] = sum_{c <= min(i+1, j)} Q[i][c] h[c]
-            for (int i = lane; i <= j; i += 32) {
-                const int cmax = min(i + 1, j);
-                double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
-                int c = 0;
-                for (; c + 1 <= cmax; c += 2) {
-                    a0 = cadd(a0, cmul(Qr[i + (size_t)c * ld], h[c]));
-                    a1 = cadd(a1, cmul(Qr[i + (size_t)(c + 1) * ld], h[c + 1]));
+            // rot[i] = sum_{c <= min(i+1, j)} Q[i][c] h[c]; a group of 8 lanes per
+            // row, every lane of a warp takes the same number of rounds
+            const int sub = tid & 7;
+            for (int base = 0; base <= j; base += kGivensThreads / 8) {
+                const int i = base + (tid >> 3);
+                double2 a = make_double2(0.0, 0.0);
+                if (i <= j) {
+                    const int cmax = min(i + 1, j);
+                    for (int c = sub; c <= cmax; c += 8) a = cadd(a, cmul(Qr[i + (size_t)c * ld], h[c]));
                 }
-                if (c <= cmax) a0 = cadd(a0, cmul(Qr[i + (size_t)c * ld], h[c]));
-                rot[i] = cadd(a0, a1);
+                for (int o = 4; o; o >>= 1) {
+                    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+                    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+                }
+                if (sub == 0 && i <= j) rot[i] = a;
             }
-            __syncwarp();
-            int stop = 0;
-            double cs = 0.0;
-            double2 sv = make_double2(0.0, 0.0);
-            if (lane == 0) {
+            __syncthreads();
+            if (tid == 0) {
                 const double2 a = rot[j];
                 const double2 b = make_double2(hn, 0.0);
                 const double aa = cabs2(a), bb = hn;
-                double2 rr;
+                double cs;
+                double2 sv, rr;
                 if (aa == 0.0) {
                     cs = 0.0;
                     sv = make_double2(1.0, 0.0);
@@ -154,35 +211,36 @@ __global__ void k_givens(CycleState S, int j, const double2 *__restrict__ hb, in
                 const int its = S.its[r] + 1;
                 S.its[r] = its;
                 const double est = cabs2(g[j + 1]);
-                stop = (est <= tol * S.fnorm[r] || hn <= 1e-300 || its >= max_iters || j + 1 >= m);
+                const int stop = (est <= tol * S.fnorm[r] || hn <= 1e-300 || its >= max_iters || j + 1 >= m);
                 if (stop) S.act_it[r] = 0;
+                sh_cs = cs;
+                sh_sv = sv;
+                sh_stop = stop;
             }
-            cs = __shfl_sync(0xffffffffu, cs, 0);
-            sv.x = __shfl_sync(0xffffffffu, sv.x, 0);
-            sv.y = __shfl_sync(0xffffffffu, sv.y, 0);
-            __syncwarp();
+            __syncthreads();
+            const double cs = sh_cs;
+            const double2 sv = sh_sv;
             // rotated column into R (R[j+1][j] = 0)
-            for (int i = lane; i <= j + 1; i += 32) R[i] = (i <= j) ? rot[i] : make_double2(0.0, 0.0);
+            for (int i = tid; i <= j + 1; i += kGivensThreads) R[i] = (i <= j) ? rot[i] : make_double2(0.0, 0.0);
             // rows j and j+1 of Q_{j+1} = G_j diag(Q_j, 1)
-            for (int c = lane; c <= j + 1; c += 32) {
+            for (int c = tid; c <= j + 1; c += kGivensThreads) {
                 const double2 qj = (c <= j) ? Qr[j + (size_t)c * ld] : make_double2(0.0, 0.0);
                 const double2 e = (c == j + 1) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
                 Q[j + (size_t)c * ld] = cadd(cscale(cs, qj), cmul(sv, e));
                 Q[j + 1 + (size_t)c * ld] = cadd(cscale(-1.0, cconjmul(sv, qj)), cscale(cs, e));
             }
-            live = __shfl_sync(0xffffffffu, stop, 0) ? 0 : 1;
+            live = !sh_stop;
         }
     }
-    // any right-hand side still stepping, over all blocks
-    const int blk_any = __syncthreads_or(live);
-    if (threadIdx.x == 0) {
-        if (blk_any) atomicOr(any_dev, 1);
+    // any right-hand side still stepping, over the least-squares blocks
+    if (tid == 0) {
+        if (live) atomicOr(S.any_dev, 1);
         __threadfence();
-        const unsigned t = atomicAdd(ticket, 1u);
-        if (t == gridDim.x - 1) {
-            const int a = atomicExch(any_dev, 0);
+        const unsigned t = atomicAdd(S.ticket, 1u);
+        if (t == (unsigned)nrhs - 1) {
+            const int a = atomicExch(S.any_dev, 0);
             if (host_flag) *(volatile int *)host_flag = a;
-            *ticket = 0;
+            *S.ticket = 0;
         }
     }
 }
@@ -263,21 +321,28 @@ void launch_cycle_init(const CycleState &S, const double *nrm2, int nrhs, int *h
     count_launch();
 }
 
-void launch_givens(const CycleState &S, int j, const double2 *hb, int hstride, int two,
-                   const double *nrm2, int nrhs, double tol, int max_iters, int *host_flag,
-                   cudaStream_t st) {
-    // small batches: one warp per block with Q_j staged in shared memory
+template <typename SV>
+void launch_givens_scale(const CycleState &S, int j, const double2 *hb, int hstride, int two,
+                         const double *nrm2, int nrhs, double tol, int max_iters, int *host_flag,
+                         SV *w, size_t sw, size_t N, cudaStream_t st) {
     const size_t ld = S.m + 1;
     const size_t qsm = (2 * ld + ld * ld) * sizeof(double2);
-    const bool qs = nrhs <= 2 * 152 && qsm <= 96 * 1024;
-    const int warps = qs ? 1 : 4;
-    const size_t sm = qs ? qsm : (size_t)warps * 2 * ld * sizeof(double2);
+    const bool qs = qsm <= 96 * 1024;
+    const size_t sm = qs ? qsm : 2 * ld * sizeof(double2);
+    size_t nbs = (N + kGivensThreads - 1) / kGivensThreads;
+    if (nbs > 65535) nbs = 65535;
     prof_begin(st);
-    k_givens<<<(nrhs + warps - 1) / warps, warps * 32, sm, st>>>(
-        S, j, hb, hstride, two, nrm2, nrhs, tol, max_iters, host_flag, S.any_dev, S.ticket, qs ? 1 : 0);
+    k_givens_scale<SV><<<dim3(1 + (unsigned)nbs, nrhs), kGivensThreads, sm, st>>>(
+        S, j, hb, hstride, two, nrm2, nrhs, tol, max_iters, host_flag, qs ? 1 : 0, w, sw, N);
     count_launch();
-    if (prof_on()) prof_end("givens", st, 0.0, 0.0);
+    if (prof_on()) prof_end("givens_scale", st, 32.0 * N * nrhs, 0.0);
 }
+template void launch_givens_scale<double2>(const CycleState &, int, const double2 *, int, int,
+                                           const double *, int, double, int, int *, double2 *,
+                                           size_t, size_t, cudaStream_t);
+template void launch_givens_scale<float4>(const CycleState &, int, const double2 *, int, int,
+                                          const double *, int, double, int, int *, float4 *,
+                                          size_t, size_t, cudaStream_t);
 
 void launch_backsolve(const CycleState &S, double2 *y, int nrhs, cudaStream_t st) {
     const size_t full = ((size_t)(S.m + 1) * S.m + S.m) * sizeof(double2);
@@ -291,7 +356,8 @@ void launch_backsolve(const CycleState &S, double2 *y, int nrhs, cudaStream_t st
 
 void prepare_cycle_kernels() {
     cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 8192);
-    cudaFuncSetAttribute(k_givens, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 8192);
+    cudaFuncSetAttribute(k_givens_scale<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 8192);
+    cudaFuncSetAttribute(k_givens_scale<float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 8192);
 }
 
 void launch_cycle_check(const CycleState &S, const double *nrm2, int nrhs, double tol,

@@ -24,16 +24,19 @@ struct CycleState {
     int *act_it;           // [nrhs] 1 while the right-hand side takes Arnoldi steps
     int *act_cy;           // [nrhs] 1 while it is part of the current cycle
     int *any_dev;          // [1] scratch for the cross-block "any active" flag (zero at rest)
-    unsigned *ticket;      // [1] last-block ticket of k_givens (zero at rest)
+    unsigned *ticket;      // [1] ticket of the least-squares blocks (zero at rest)
 };
 
 void prepare_cycle_kernels();   // shared-memory attributes; call outside graph capture
 
 void launch_cycle_init(const CycleState &S, const double *nrm2, int nrhs, int *host_flag,
                        cudaStream_t st);
-void launch_givens(const CycleState &S, int j, const double2 *hb, int hstride, int two,
-                   const double *nrm2, int nrhs, double tol, int max_iters, int *host_flag,
-                   cudaStream_t st);
+// least-squares update of step j and v_{j+1} = w / ||w|| in one launch;
+// SV: basis type (double2, or float4 for the double-single basis)
+template <typename SV>
+void launch_givens_scale(const CycleState &S, int j, const double2 *hb, int hstride, int two,
+                         const double *nrm2, int nrhs, double tol, int max_iters, int *host_flag,
+                         SV *w, size_t sw, size_t N, cudaStream_t st);
 void launch_backsolve(const CycleState &S, double2 *y, int nrhs, cudaStream_t st);
 void launch_cycle_check(const CycleState &S, const double *nrm2, int nrhs, double tol,
                         int max_iters, int *host_flag, cudaStream_t st);

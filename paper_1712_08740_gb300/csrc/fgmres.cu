@@ -207,9 +207,8 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
                 launch_multiaxpy_ds(Vd, sV, nvec, hb + nv, 2 * nv, wd, sV, N, nrm, nrhs, act, ks, st);
             }
         }
-        launch_givens(cycle_state(g), j, hb, 2 * nv, mode ? 1 : 0, nrm, nrhs, tol, g->opt.max_iters,
-                      g->hflag, st);
-        launch_scale_ds<float4>(wd, sV, nrm, wd, sV, N, nrhs, act, st);
+        launch_givens_scale<float4>(cycle_state(g), j, hb, 2 * nv, mode ? 1 : 0, nrm, nrhs, tol,
+                                    g->opt.max_iters, g->hflag, wd, sV, N, st);
         return;
     }
     if (mode == 2) {
@@ -228,9 +227,8 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
             launch_multiaxpy(V, sV, nvec, hb + nv, 2 * nv, w, sV, N, nrm, nrhs, act, ks, st);
         }
     }
-    launch_givens(cycle_state(g), j, hb, 2 * nv, mode ? 1 : 0, nrm, nrhs, tol, g->opt.max_iters,
-                  g->hflag, st);
-    launch_scale<double2>(w, sV, nrm, w, sV, N, nrhs, act, st);
+    launch_givens_scale<double2>(cycle_state(g), j, hb, 2 * nv, mode ? 1 : 0, nrm, nrhs, tol,
+                                 g->opt.max_iters, g->hflag, w, sV, N, st);
 }
 
 long long graph_key_of(const helm_grid *g, int nrhs, double tol) {

@@ -170,6 +170,10 @@ void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
 // have equal length) and the extents/threads of one (kernel 0 down, 1 up)
 int num_tile_shapes(int dim);
 bool tile_shape(int dim, int kernel, int shape, int ext[3], int *threads);
+// automatic shape for a fine level of `fine` nodes and nb right-hand sides:
+// the first shape in list order whose grid has at least 2 x 152 blocks, else
+// the shape with the most blocks (small levels need every SM)
+int auto_tile_shape(int dim, int kernel, const int fine[3], int nb);
 void prepare_vfused();   // sets shared-memory attributes; call outside graph capture
 
 // ------------------------------------------------------------ set-up kernels

@@ -80,7 +80,7 @@ helm_status tune_tiles(helm_grid *g, int nrhs, helm_tune_report *rep) {
         cudaMemsetAsync(g->lv[l].t.p, 0, b, st);
         cudaMemsetAsync(g->lv[l].b.p, 0, b, st);
     }
-    std::vector<int> dn(L, 0), up(L, 0);
+    std::vector<int> dn(L, -1), up(L, -1);
     helm_status s;
     rep->levels = L - 1;
     for (int l = 0; l + 1 < L && l < HELM_TUNE_MAX_LEVELS; ++l) {
@@ -98,7 +98,7 @@ helm_status tune_tiles(helm_grid *g, int nrhs, helm_tune_report *rep) {
             };
             double us = 0.0;
             if ((s = time_launches(g, down, &us))) return s;
-            if (sh == 0) rep->down_default_us[l] = us;
+            if (sh == auto_tile_shape(g->dim, 0, Lf.n, nrhs)) rep->down_default_us[l] = us;
             if (us < best) {
                 best = us;
                 dn[l] = sh;
@@ -120,7 +120,7 @@ helm_status tune_tiles(helm_grid *g, int nrhs, helm_tune_report *rep) {
             };
             double us = 0.0;
             if ((s = time_launches(g, upk, &us))) return s;
-            if (sh == 0) rep->up_default_us[l] = us;
+            if (sh == auto_tile_shape(g->dim, 1, Lf.n, nrhs)) rep->up_default_us[l] = us;
             if (us < best) {
                 best = us;
                 up[l] = sh;
@@ -158,11 +158,11 @@ helm_status helm_set_tiles(helm_grid *g, int level, int down_shape, int up_shape
     const int ns = num_tile_shapes(g->dim);
     if (ns == 0) return fail(HELM_ERR_UNSUPPORTED, "tile shapes exist for 2D and 3D grids only");
     if (level < 0 || level >= HELM_TUNE_MAX_LEVELS) return fail(HELM_ERR_ARG, "level out of range");
-    if (down_shape < 0 || down_shape >= ns || up_shape < 0 || up_shape >= ns)
-        return fail(HELM_ERR_ARG, "shape index must be in [0, %d)", ns);
+    if (down_shape < -1 || down_shape >= ns || up_shape < -1 || up_shape >= ns)
+        return fail(HELM_ERR_ARG, "shape index must be -1 (automatic) or in [0, %d)", ns);
     if ((int)g->tile_dn.size() <= level) {
-        g->tile_dn.resize(level + 1, 0);
-        g->tile_up.resize(level + 1, 0);
+        g->tile_dn.resize(level + 1, -1);
+        g->tile_up.resize(level + 1, -1);
     }
     g->tile_dn[level] = down_shape;
     g->tile_up[level] = up_shape;
@@ -173,8 +173,8 @@ helm_status helm_get_tiles(const helm_grid *g, int level, int *down_shape, int *
     clear_error();
     if (!g || !down_shape || !up_shape) return fail(HELM_ERR_ARG, "null argument");
     if (level < 0 || level >= HELM_TUNE_MAX_LEVELS) return fail(HELM_ERR_ARG, "level out of range");
-    *down_shape = tile_down(g, level);
-    *up_shape = tile_up(g, level);
+    *down_shape = tile_setting(g->tile_dn, level);
+    *up_shape = tile_setting(g->tile_up, level);
     return HELM_OK;
 }
 

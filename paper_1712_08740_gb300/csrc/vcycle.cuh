@@ -45,12 +45,19 @@ template <typename T> inline LevelView<T> level_view(const helm_grid *g, int l) 
     return v;
 }
 
-// tile shape of the fused kernels on fine level l (0 = default shape)
-inline int tile_down(const helm_grid *g, int l) {
-    return l < (int)g->tile_dn.size() ? g->tile_dn[l] : 0;
+// tile shape of the fused kernels on fine level l: the one set by
+// helm_set_tiles / helm_autotune, else (-1) the automatic choice for nb
+// right-hand sides
+inline int tile_setting(const std::vector<int> &v, int l) {
+    return l < (int)v.size() ? v[l] : -1;
 }
-inline int tile_up(const helm_grid *g, int l) {
-    return l < (int)g->tile_up.size() ? g->tile_up[l] : 0;
+inline int tile_down(const helm_grid *g, int l, int nb) {
+    const int t = tile_setting(g->tile_dn, l);
+    return t >= 0 ? t : auto_tile_shape(g->dim, 0, g->lv[l].n, nb);
+}
+inline int tile_up(const helm_grid *g, int l, int nb) {
+    const int t = tile_setting(g->tile_up, l);
+    return t >= 0 ? t : auto_tile_shape(g->dim, 1, g->lv[l].n, nb);
 }
 
 inline std::complex<double> q_of(double alpha) {
@@ -89,11 +96,11 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
             C *bc = g->lv[l + 1].b.template as<C>();
             if (l == 0)
                 launch_vdown<T, CB0>(F, Cv, wj, b0, sb0, g->lv[0].t.template as<C>(), g->lv[0].N,
-                                     bc, g->lv[1].N, nb, act, st, tile_down(g, 0));
+                                     bc, g->lv[1].N, nb, act, st, tile_down(g, 0, nb));
             else
                 launch_vdown<T, C>(F, Cv, wj, g->lv[l].b.template as<C>(), g->lv[l].N,
                                    g->lv[l].t.template as<C>(), g->lv[l].N, bc, g->lv[l + 1].N, nb,
-                                   act, st, tile_down(g, l));
+                                   act, st, tile_down(g, l, nb));
         }
         C *uc = (L - 1 == 0) ? u0 : g->lv[L - 1].u.template as<C>();
         launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, g->lv[L - 1].b.template as<C>(),
@@ -104,11 +111,11 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
             const C *ec = g->lv[l + 1].u.template as<C>();
             if (l == 0)
                 launch_vup<T, CB0>(F, Cv, wj, g->lv[0].t.template as<C>(), g->lv[0].N, ec,
-                                   g->lv[1].N, b0, sb0, u0, su0, nb, act, st, tile_up(g, 0));
+                                   g->lv[1].N, b0, sb0, u0, su0, nb, act, st, tile_up(g, 0, nb));
             else
                 launch_vup<T, C>(F, Cv, wj, g->lv[l].t.template as<C>(), g->lv[l].N, ec,
                                  g->lv[l + 1].N, g->lv[l].b.template as<C>(), g->lv[l].N,
-                                 g->lv[l].u.template as<C>(), g->lv[l].N, nb, act, st, tile_up(g, l));
+                                 g->lv[l].u.template as<C>(), g->lv[l].N, nb, act, st, tile_up(g, l, nb));
         }
         return;
     }

@@ -465,6 +465,26 @@ bool tile_shape(int dim, int kernel, int shape, int ext[3], int *threads) {
     return true;
 }
 
+int auto_tile_shape(int dim, int kernel, const int fine[3], int nb) {
+    const int ns = num_tile_shapes(dim);
+    const int cn[3] = {(fine[0] + 1) / 2, (fine[1] + 1) / 2, (fine[2] + 1) / 2};
+    const int *ext_of = kernel == 0 ? cn : fine;   // down tiles cover coarse nodes, up tiles fine
+    long long best_blocks = -1;
+    int best = 0;
+    for (int sh = 0; sh < ns; ++sh) {
+        int e[3], nt;
+        tile_shape(dim, kernel, sh, e, &nt);
+        long long blocks = (long long)nb * ((ext_of[0] + e[0] - 1) / e[0]) * ((ext_of[1] + e[1] - 1) / e[1]);
+        if (dim == 3) blocks *= (ext_of[2] + e[2] - 1) / e[2];
+        if (blocks >= 2 * 152) return sh;
+        if (blocks > best_blocks) {
+            best_blocks = blocks;
+            best = sh;
+        }
+    }
+    return best;
+}
+
 void prepare_vfused() {
     static bool done = false;
     if (done) return;

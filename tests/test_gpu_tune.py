@@ -53,6 +53,7 @@ def test_every_tile_shape_gives_the_same_preconditioner(helm, name, precision):
     assert g.num_levels >= 3
     rng = np.random.default_rng(7)
     r = dev(rng.standard_normal(g.N) + 1j * rng.standard_normal(g.N))
+    assert g.get_tiles(0) == (-1, -1)                   # automatic until set
     outs = []
     for s in range(helm.helm_num_tile_shapes(len(w.n))):
         for lev in range(g.num_levels - 1):
