@@ -149,16 +149,20 @@ helm_status build_hierarchy(helm_grid *g) {
             LevelView<double> v = level_view<double>(g, (int)g->lv.size() - 1);
             launch_assemble_dense<double>(v, shift_M<double>(g), g->Ainv.as<double2>(), g->st);
             launch_gauss_jordan<double>(g->Ainv.as<double2>(), g->colbuf.as<double2>(), nc, g->st);
+            launch_transpose_square<double>(g->Ainv.as<double2>(), nc, g->st);
         } else {
             LevelView<float> v = level_view<float>(g, (int)g->lv.size() - 1);
             launch_assemble_dense<float>(v, shift_M<float>(g), g->Ainv.as<float2>(), g->st);
             launch_gauss_jordan<float>(g->Ainv.as<float2>(), g->colbuf.as<float2>(), nc, g->st);
+            launch_transpose_square<float>(g->Ainv.as<float2>(), nc, g->st);
         }
         g->nc = nc;
     }
+    prepare_coarse_kernels();
     if ((s = check_cuda("build_hierarchy"))) return s;
     g->vc_prec = prec;
     g->cap_rhs = 0;   // level work vectors must be re-sized for the new hierarchy
+    g->cpart_rhs = 0;
     g->ready = true;
     return HELM_OK;
 }
@@ -179,6 +183,13 @@ helm_status ensure_level_work(helm_grid *g, int nrhs) {
         if ((s = L.t.ensure(b)) || (s = L.r.ensure(b))) return s;
         if (l > 0 && ((s = L.u.ensure(b)) || (s = L.b.ensure(b)))) return s;
         if (l == 0 && ((s = L.u.ensure(b)) || (s = L.b.ensure(b)))) return s;
+    }
+    if (g->nc > 0 && g->cpart_rhs < nrhs) {
+        if ((s = g->cpart.ensure(coarse_part_elems(g->nc, nrhs) * esz)) ||
+            (s = g->cticket.ensure(coarse_tickets(g->nc, nrhs) * sizeof(unsigned))))
+            return s;
+        cudaMemsetAsync(g->cticket.p, 0, coarse_tickets(g->nc, nrhs) * sizeof(unsigned), g->st);
+        g->cpart_rhs = nrhs;
     }
     return HELM_OK;
 }

@@ -1,7 +1,7 @@
 // Coarsest-level solve of the shifted Laplacian (Eq. 6): the level's matrix is
 // assembled densely on the device, inverted once per (model, omega, shift) by
-// Gauss-Jordan elimination, and applied in every V-cycle as a dense
-// matrix-vector product (one warp per row).
+// Gauss-Jordan elimination, stored transposed, and applied in every V-cycle
+// as a dense product with the level's right-hand sides.
 //
 // Gauss-Jordan runs without pivoting. D M (D halves boundary rows per face)
 // is complex symmetric with a positive-definite imaginary part (beta2 > 0 and
@@ -90,13 +90,10 @@ __global__ void k_gj_elim(cplx_t<T> *__restrict__ A, const cplx_t<T> *__restrict
     A[(size_t)i * n + j] = a;
 }
 
-// One quarter of one row of Ainv times one vector, by one warp: columns
-// [c0, c1), eight independent accumulators per lane (column j + 32q) keep
-// eight row loads in flight, then a fixed combination and shuffle tree.
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 
-// (re, im) += a v as two FMA chains: four FP64 instructions per complex
+// (re, im) += a v as two FMA chains: four FMA instructions per complex
 // multiply-add (the form "re += a.x v.x - a.y v.y" compiles to a multiply, an
 // FMA and an add, 1.5x the issue time on GB300's narrow FP64 pipe)
 template <typename T>
@@ -107,122 +104,162 @@ __device__ __forceinline__ void cmac(T &re, T &im, cplx_t<T> a, cplx_t<T> v) {
     im = fmaT(a.y, v.x, im);
 }
 
+// In-place transpose of the n x n inverse (row-major -> column-major), so
+// that consecutive rows of one column are contiguous for the product below.
 template <typename T>
-__device__ __forceinline__ cplx_t<T> quarter_dot(const cplx_t<T> *__restrict__ row,
-                                                 const cplx_t<T> *__restrict__ r, int c0, int c1,
-                                                 int lane) {
-    T are[8] = {0, 0, 0, 0, 0, 0, 0, 0}, aim[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int j = c0 + lane;
-    for (; j + 224 < c1; j += 256) {
-        cplx_t<T> a[8], v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            a[q] = row[j + 32 * q];
-            v[q] = r[j + 32 * q];
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            cmac(are[q], aim[q], a[q], v[q]);
-        }
-    }
-    for (; j < c1; j += 32) {
-        const cplx_t<T> a = row[j];
-        const cplx_t<T> v = r[j];
-        cmac(are[0], aim[0], a, v);
-    }
-    T sre = ((are[0] + are[1]) + (are[2] + are[3])) + ((are[4] + are[5]) + (are[6] + are[7]));
-    T sim = ((aim[0] + aim[1]) + (aim[2] + aim[3])) + ((aim[4] + aim[5]) + (aim[6] + aim[7]));
-    for (int o = 16; o; o >>= 1) {
-        sre += __shfl_xor_sync(0xffffffffu, sre, o);
-        sim += __shfl_xor_sync(0xffffffffu, sim, o);
-    }
-    cplx_t<T> out;
-    out.x = sre;
-    out.y = sim;
-    return out;
+__global__ void k_transpose_square(cplx_t<T> *__restrict__ A, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= n || j >= n || j <= i) return;
+    const cplx_t<T> a = A[(size_t)i * n + j];
+    A[(size_t)i * n + j] = A[(size_t)j * n + i];
+    A[(size_t)j * n + i] = a;
 }
 
-// Arithmetic per row shared by both GEMV kernels: each row is split into four
-// quarters (starting on multiples of 32 columns), a warp forms each quarter's
-// dot product (quarter_dot), and the four quarter sums are added in order
-// 0..3. The kernels differ only in which warps and blocks handle which rows,
-// so batched and single solves agree bitwise.
-__device__ __forceinline__ void quarter_range(int n, int q, int &c0, int &c1) {
-    const int Q = ((n + 127) / 128) * 32;
-    c0 = min(q * Q, n);
-    c1 = min((q + 1) * Q, n);
+// Z_k = Ainv R_k for nb right-hand sides, Ainv stored column-major (At).
+//
+// The arithmetic per (row i, right-hand side k) depends only on n: the
+// columns are split into G(n) groups of width cw = ceil(n / G); in a group
+// one lane forms sum_c Ainv[i][c] R_k[c] in column order with two
+// accumulators (columns at even and odd offsets from the group start, added
+// at the end of the group); the G group sums are then added in group order.
+// So batched and single solves agree bitwise whatever tile of right-hand
+// sides a warp takes.
+//
+// Work: a warp owns 32 consecutive rows (one per lane, so each column read is
+// one coalesced row of At), one column group and a tile of RT (1 or 4) right-hand
+// sides, whose slice of R it stages in shared memory. G is chosen so that
+// the single-right-hand-side grid is about one wave of 152 x 8 warps with
+// every SM given the same number of warps up to one (contiguous task ranges
+// per block). Each warp writes its group sums to `part`; the last of the G
+// warps of a (row group, right-hand-side tile) to finish (atomic ticket)
+// adds them in group order and writes Z.
+constexpr int kGemmWarps = 8;
+
+__host__ __device__ inline int gemm_groups(int n) {
+    const int rgs = (n + 31) / 32;
+    int G = (152 * kGemmWarps) / rgs;
+    if (G < 1) G = 1;
+    if (G > 64) G = 64;
+    const int gmin = (n + 127) / 128;      // groups of at most 128 columns (shared-memory slice)
+    if (G < gmin) G = gmin;
+    if (G > n) G = n;
+    return G;
 }
 
-// z = Ainv r for one right-hand side. The rows are split into one contiguous
-// range per block (one block per SM, 152 blocks), so every SM gets the same
-// number of rows up to one; a block of 16 warps runs four rows at a time,
-// warp w taking quarter (w % 4) of row slot (w / 4), so each SM sub-partition
-// (warp w runs on sub-partition w % 4) gets the same share of the FP64 work
-// and four warps per sub-partition hide the load latency.
-constexpr int kG1Warps = 16;
-
-template <typename T>
-__global__ void __launch_bounds__(kG1Warps * 32, 1)
-k_dense_gemv1(const cplx_t<T> *__restrict__ Ainv, int n, const cplx_t<T> *__restrict__ r,
-              cplx_t<T> *__restrict__ z, const int *__restrict__ active) {
-    if (active && !active[0]) return;
+template <typename T, int RT>
+__global__ void __launch_bounds__(kGemmWarps * 32, 1)
+k_coarse_gemm(const cplx_t<T> *__restrict__ At, int n, const cplx_t<T> *__restrict__ R, size_t sr,
+              cplx_t<T> *__restrict__ Z, size_t sz, int nb, const int *__restrict__ active,
+              cplx_t<T> *__restrict__ part, unsigned *__restrict__ ticket, int ntask) {
+    using C = cplx_t<T>;
     extern __shared__ unsigned char smem_raw[];
-    cplx_t<T> *part = reinterpret_cast<cplx_t<T> *>(smem_raw);   // [row of the block][quarter]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = warp & 3, slot = warp >> 2;
-    const int r0 = (int)((long long)blockIdx.x * n / gridDim.x);
-    const int r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
-    int c0, c1;
-    quarter_range(n, q, c0, c1);
-    for (int i = r0 + slot; i < r1; i += kG1Warps / 4) {
-        const cplx_t<T> v = quarter_dot<T>(Ainv + (size_t)i * n, r, c0, c1, lane);
-        if (lane == 0) part[(i - r0) * 4 + q] = v;
+    const int G = gemm_groups(n);
+    const int cw = (n + G - 1) / G;
+    const int rgs = (n + 31) / 32;
+    // contiguous task range of this block: every SM gets the same count up to one
+    const int t0 = (int)((long long)blockIdx.x * ntask / gridDim.x);
+    const int t1 = (int)((long long)(blockIdx.x + 1) * ntask / gridDim.x);
+    const int task = t0 + warp;
+    if (task >= t1) return;                                  // warp-uniform
+    const int cg = task % G;
+    const int rg = (task / G) % rgs;
+    const int kt = task / (G * rgs);
+    const int c0 = min(cg * cw, n), c1 = min(c0 + cw, n);
+    const int len = c1 - c0;
+    const int i = rg * 32 + lane;
+    bool use[RT];
+#pragma unroll
+    for (int k = 0; k < RT; ++k) {
+        const int rhs = kt * RT + k;
+        use[k] = rhs < nb && (!active || active[rhs]);
     }
-    __syncthreads();
-    // quarters added in order 0..3, as in k_dense_gemv
-    for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
-        const cplx_t<T> *pq = part + (size_t)(i - r0) * 4;
-        cplx_t<T> s = pq[0];
-        for (int k = 1; k < 4; ++k) {
-            s.x += pq[k].x;
-            s.y += pq[k].y;
+    // this warp's slice of the right-hand sides: xs[k * cw + (c - c0)]
+    C *xs = reinterpret_cast<C *>(smem_raw) + (size_t)warp * RT * cw;
+#pragma unroll
+    for (int k = 0; k < RT; ++k) {
+        const C *rk = R + (size_t)(kt * RT + k) * sr + c0;
+        for (int c = lane; c < len; c += 32) {
+            C v;
+            v.x = T(0);
+            v.y = T(0);
+            if (use[k]) v = rk[c];
+            xs[k * cw + c] = v;
         }
-        z[i] = s;
     }
-}
-
-// z_k = Ainv r_k for a tile of up to kRT right-hand sides per block (one row pair)
-constexpr int kRT = 4;
-
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_dense_gemv(const cplx_t<T> *__restrict__ Ainv, int n, const cplx_t<T> *__restrict__ r, size_t sr,
-             cplx_t<T> *__restrict__ z, size_t sz, int nb, const int *__restrict__ active) {
-    __shared__ cplx_t<T> part[kRT][2][4];
-    const int rhs0 = blockIdx.y * kRT;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = warp & 3, half = warp >> 2;
-    const int i = 2 * blockIdx.x + half;
-    int c0, c1;
-    quarter_range(n, q, c0, c1);
-    for (int t = 0; t < kRT; ++t) {
-        const int k = rhs0 + t;
-        if (k >= nb || (active && !active[k]) || i >= n) continue;
-        const cplx_t<T> v = quarter_dot<T>(Ainv + (size_t)i * n, r + (size_t)k * sr, c0, c1, lane);
-        if (lane == 0) part[t][half][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 2 * kRT) {
-        const int t = threadIdx.x >> 1, hh = threadIdx.x & 1;
-        const int k = rhs0 + t, row = 2 * blockIdx.x + hh;
-        if (k < nb && (!active || active[k]) && row < n) {
-            cplx_t<T> s = part[t][hh][0];
-            for (int m = 1; m < 4; ++m) {
-                s.x += part[t][hh][m].x;
-                s.y += part[t][hh][m].y;
+    __syncwarp();
+    T er[RT], ei[RT], orr[RT], oi[RT];
+#pragma unroll
+    for (int k = 0; k < RT; ++k) er[k] = ei[k] = orr[k] = oi[k] = T(0);
+    if (i < n) {
+        const C *col = At + (size_t)c0 * n + i;
+        const int full = len & ~7;
+        // the next chunk of 8 columns is loaded while the current one is used
+        C an[8];
+        if (full > 0) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) an[u] = col[(size_t)u * n];
+        }
+        int c = 0;
+        for (; c < full; c += 8) {
+            C a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = an[u];
+            if (c + 8 < full) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) an[u] = col[(size_t)(c + 8 + u) * n];
             }
-            z[(size_t)k * sz + row] = s;
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+#pragma unroll
+                for (int k = 0; k < RT; ++k) {
+                    cmac(er[k], ei[k], a[u], xs[k * cw + c + u]);
+                    cmac(orr[k], oi[k], a[u + 1], xs[k * cw + c + u + 1]);
+                }
+            }
         }
+        for (; c < len; ++c) {
+            const C a = col[(size_t)c * n];
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                if (c & 1) cmac(orr[k], oi[k], a, xs[k * cw + c]);
+                else cmac(er[k], ei[k], a, xs[k * cw + c]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            if (!use[k]) continue;
+            C v;
+            v.x = er[k] + orr[k];
+            v.y = ei[k] + oi[k];
+            part[((size_t)(kt * RT + k) * G + cg) * n + i] = v;
+        }
+    }
+    // the last warp of this (row group, tile) adds the G group sums in order
+    __syncwarp();
+    unsigned last = 0;
+    if (lane == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&ticket[kt * rgs + rg], 1u);
+        last = (t == (unsigned)G - 1);
+        if (last) ticket[kt * rgs + rg] = 0;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    if (i >= n) return;
+#pragma unroll
+    for (int k = 0; k < RT; ++k) {
+        if (!use[k]) continue;
+        const C *pk = part + (size_t)(kt * RT + k) * G * n + i;
+        C s = __ldcg(pk);
+        for (int q = 1; q < G; ++q) {
+            const C v = __ldcg(pk + (size_t)q * n);
+            s.x += v.x;
+            s.y += v.y;
+        }
+        Z[(size_t)(kt * RT + k) * sz + i] = s;
     }
 }
 
@@ -251,22 +288,59 @@ void launch_gauss_jordan(cplx_t<T> *A, cplx_t<T> *colbuf, int n, cudaStream_t st
                  2.0 * n * (double)n * n * sizeof(cplx_t<T>), sizeof(T) == 8 ? 8.0 * n * n * (double)n : 0.0);
 }
 
+namespace {
+
+template <typename T, int RT>
+void gemm_impl(const cplx_t<T> *At, int n, const cplx_t<T> *r, size_t sr, cplx_t<T> *z, size_t sz,
+               int nb, const int *active, cplx_t<T> *part, unsigned *ticket, cudaStream_t st) {
+    const int G = gemm_groups(n);
+    const int cw = (n + G - 1) / G;
+    const int ntask = ((n + 31) / 32) * G * ((nb + RT - 1) / RT);
+    const int per_sm = (ntask + 151) / 152;
+    // up to 8 warps (tasks) per block; when one wave suffices, one block per SM
+    const int blocks = per_sm <= kGemmWarps ? (ntask < 152 ? ntask : 152)
+                                            : (ntask + kGemmWarps - 1) / kGemmWarps;
+    const size_t sm = (size_t)kGemmWarps * RT * cw * sizeof(cplx_t<T>);
+    k_coarse_gemm<T, RT><<<blocks, kGemmWarps * 32, sm, st>>>(At, n, r, sr, z, sz, nb, active, part,
+                                                              ticket, ntask);
+}
+
+}  // namespace
+
+void prepare_coarse_kernels() {
+    static bool done = false;
+    if (done) return;
+    const int big = 100 * 1024;
+    cudaFuncSetAttribute(k_coarse_gemm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_coarse_gemm<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_coarse_gemm<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_coarse_gemm<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    done = true;
+}
+
+size_t coarse_part_elems(int n, int nb) { return (size_t)nb * gemm_groups(n) * n; }
+size_t coarse_tickets(int n, int nb) { return (size_t)((n + 31) / 32) * (size_t)nb; }
+
 template <typename T>
-void launch_dense_gemv(const cplx_t<T> *Ainv, int n, const cplx_t<T> *r, size_t sr,
-                       cplx_t<T> *z, size_t sz, int nb, const int *active, cudaStream_t st) {
-    const int npairs = (n + 1) / 2;
+void launch_transpose_square(cplx_t<T> *A, int n, cudaStream_t st) {
+    const dim3 blk(32, 8);
+    const dim3 grd((n + 31) / 32, (n + 7) / 8);
+    k_transpose_square<T><<<grd, blk, 0, st>>>(A, n);
+    count_launch();
+}
+
+template <typename T>
+void launch_dense_gemv(const cplx_t<T> *At, int n, const cplx_t<T> *r, size_t sr,
+                       cplx_t<T> *z, size_t sz, int nb, const int *active, void *part,
+                       unsigned *ticket, cudaStream_t st) {
     prof_begin(st);
-    if (nb == 1) {
-        const int blocks = n < 152 ? n : 152;
-        const size_t sm = (size_t)((n + blocks - 1) / blocks) * 4 * sizeof(cplx_t<T>);
-        k_dense_gemv1<T><<<blocks, kG1Warps * 32, sm, st>>>(Ainv, n, r, z, active);
-    } else
-        k_dense_gemv<T><<<dim3(npairs, (nb + kRT - 1) / kRT), 256, 0, st>>>(Ainv, n, r, sr, z, sz, nb,
-                                                                             active);
+    cplx_t<T> *pp = static_cast<cplx_t<T> *>(part);
+    if (nb == 1) gemm_impl<T, 1>(At, n, r, sr, z, sz, nb, active, pp, ticket, st);
+    else gemm_impl<T, 4>(At, n, r, sr, z, sz, nb, active, pp, ticket, st);
     count_launch();
     if (prof_on())
         prof_end(sizeof(T) == 8 ? "coarse_gemv_f64" : "coarse_gemv_f32", st,
-                 ((double)n * n * ((nb + kRT - 1) / kRT) + 2.0 * n * nb) * sizeof(cplx_t<T>),
+                 ((double)n * n + 2.0 * n * nb) * sizeof(cplx_t<T>),
                  sizeof(T) == 8 ? 8.0 * n * n * nb : 0.0);
 }
 
@@ -277,8 +351,10 @@ template void launch_assemble_dense<double>(const LevelView<double> &, OpShift<d
 template void launch_gauss_jordan<float>(float2 *, float2 *, int, cudaStream_t);
 template void launch_gauss_jordan<double>(double2 *, double2 *, int, cudaStream_t);
 template void launch_dense_gemv<float>(const float2 *, int, const float2 *, size_t, float2 *,
-                                       size_t, int, const int *, cudaStream_t);
+                                       size_t, int, const int *, void *, unsigned *, cudaStream_t);
 template void launch_dense_gemv<double>(const double2 *, int, const double2 *, size_t, double2 *,
-                                        size_t, int, const int *, cudaStream_t);
+                                        size_t, int, const int *, void *, unsigned *, cudaStream_t);
+template void launch_transpose_square<float>(float2 *, int, cudaStream_t);
+template void launch_transpose_square<double>(double2 *, int, cudaStream_t);
 
 }  // namespace helm

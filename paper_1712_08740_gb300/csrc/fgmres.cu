@@ -240,6 +240,7 @@ long long graph_key_of(const helm_grid *g, int nrhs, double tol) {
     auto mixd = [&](double d) { unsigned long long b; memcpy(&b, &d, 8); mixu(b); };
     mixp(g->V.p); mixp(g->Z.p); mixp(g->hbuf.p); mixp(g->nrm.p); mixp(g->partial.p); mixp(g->counter.p);
     mixp(g->act_it.p); mixp(g->act_cy.p); mixp(g->act2.p); mixp(g->Ainv.p); mixp(g->hflag);
+    mixp(g->cpart.p); mixp(g->cticket.p);
     mixp(g->cR.p); mixp(g->cg.p); mixp(g->ccs.p); mixp(g->csn.p); mixp(g->cQ.p); mixp(g->cfn.p);
     mixp(g->ck.p); mixp(g->cits.p); mixp(g->cstat.p); mixp(g->cany.p); mixp(g->hdiag.p); mixp(g->rbuf.p);
     for (const auto &L : g->lv) {

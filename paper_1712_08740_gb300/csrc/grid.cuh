@@ -55,7 +55,9 @@ struct helm_grid {
     std::vector<int> tile_dn, tile_up;  // fused-kernel tile shape per fine level (helm_autotune)
     int vc_prec = -1;                   // precision the hierarchy was built for
     int nc = 0;                         // coarse inverse order
-    helm::DevBuf Ainv, colbuf;
+    helm::DevBuf Ainv, colbuf;          // coarse inverse (transposed) and Gauss-Jordan column
+    helm::DevBuf cpart, cticket;        // coarse product scratch: group sums, tickets
+    int cpart_rhs = 0;                  // right-hand sides cpart/cticket are sized for
 
     // Krylov workspace
     int cap_rhs = 0, cap_m = 0, cap_prec = -1;

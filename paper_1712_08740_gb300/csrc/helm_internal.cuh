@@ -193,8 +193,17 @@ template <typename T>
 void launch_gauss_jordan(cplx_t<T> *A, cplx_t<T> *colbuf, int n, cudaStream_t st);
 // z = Ainv r for nb right-hand sides
 template <typename T>
-void launch_dense_gemv(const cplx_t<T> *Ainv, int n, const cplx_t<T> *r, size_t sr,
-                       cplx_t<T> *z, size_t sz, int nb, const int *active, cudaStream_t st);
+void launch_dense_gemv(const cplx_t<T> *At, int n, const cplx_t<T> *r, size_t sr,
+                       cplx_t<T> *z, size_t sz, int nb, const int *active, void *part,
+                       unsigned *ticket, cudaStream_t st);
+// the inverse is stored transposed (column-major) for launch_dense_gemv
+template <typename T>
+void launch_transpose_square(cplx_t<T> *A, int n, cudaStream_t st);
+// scratch of launch_dense_gemv for nb right-hand sides: group sums (complex
+// elements of the V-cycle type) and tickets (unsigned, zero at rest)
+size_t coarse_part_elems(int n, int nb);
+size_t coarse_tickets(int n, int nb);
+void prepare_coarse_kernels();   // shared-memory attributes; call outside graph capture
 
 // ------------------------------------------------------------ Krylov (complex128 outer)
 // All vectors of right-hand side k sit at base + k * stride_rhs; basis vector i

@@ -93,8 +93,11 @@ size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o)
     b += nrhs * (m + 1.0) * N * 16.0;                    // basis V
     b += nrhs * (double)m * N * zsz;                     // preconditioned vectors Z
     b += 4.0 * nrhs * levels_sum * csz;                  // V-cycle work vectors
-    b += levels_sum * (8.0 + 8.0 + 4.0);                 // slowness, coefficients
-    if (o.precond != HELM_PRECOND_NONE) b += nc * nc * csz + nc * csz;   // coarse inverse
+    b += levels_sum * (8.0 + 8.0 + 4.0 + csz);           // slowness, coefficients, 1/diag(M)
+    if (o.precond != HELM_PRECOND_NONE) {
+        b += nc * nc * csz + nc * csz;                   // coarse inverse
+        b += (double)coarse_part_elems((int)nc, nrhs) * csz + coarse_tickets((int)nc, nrhs) * 4.0;
+    }
     b += 2.0 * nrhs * N * 16.0;                          // staging of host f and u
     if (o.precision == HELM_PREC_MIXED_DS) b += nrhs * N * 16.0;   // complex128 residuals
     b += (double)nrhs * (m + 1.0) * (m + 1.0) * 16.0 * 3.0;   // Hessenberg, rotations

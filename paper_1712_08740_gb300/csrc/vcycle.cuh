@@ -104,7 +104,8 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
         }
         C *uc = (L - 1 == 0) ? u0 : g->lv[L - 1].u.template as<C>();
         launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, g->lv[L - 1].b.template as<C>(),
-                             g->lv[L - 1].N, uc, g->lv[L - 1].N, nb, act, st);
+                             g->lv[L - 1].N, uc, g->lv[L - 1].N, nb, act, g->cpart.p,
+                             g->cticket.template as<unsigned>(), st);
         // up: u_l = Jacobi(u_pre + P e_{l+1})
         for (int l = L - 2; l >= 0; --l) {
             const LevelView<T> F = level_view<T>(g, l), Cv = level_view<T>(g, l + 1);
@@ -131,7 +132,8 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
         sb0c = g->lv[0].N;
     }
     if (L == 1) {
-        launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, b0c, sb0c, u0, su0, nb, act, st);
+        launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, b0c, sb0c, u0, su0, nb, act, g->cpart.p,
+                             g->cticket.template as<unsigned>(), st);
         return;
     }
     std::vector<const C *> B(L);
@@ -178,7 +180,7 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
                            g->lv[l + 1].N, nb, act, st);
     }
     launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, B[L - 1], SB[L - 1], U[L - 1], SU[L - 1], nb,
-                         act, st);
+                         act, g->cpart.p, g->cticket.template as<unsigned>(), st);
     for (int l = L - 2; l >= 0; --l) {
         const LevelView<T> Lv = level_view<T>(g, l);
         const LevelView<T> Cv = level_view<T>(g, l + 1);
