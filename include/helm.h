@@ -203,9 +203,10 @@ helm_status helm_true_residual_noalloc(helm_grid *g, int nrhs, const helm_c128 *
  * Tile shapes. The fused V(1,1) level kernels of 2D/3D grids ("down":
  * pre-smoothing, residual and restriction; "up": prolongation and
  * post-smoothing) are compiled for helm_num_tile_shapes(dim) shapes each
- * (0 for 1D). helm_tile_shape gives a shape's extents and block size: for
- * kernel 0 (down) the block's tile of coarse nodes, for kernel 1 (up) its
- * tile of fine nodes. The arithmetic per node does not depend on the shape:
+ * (0 for 1D). helm_tile_shape gives a shape's extents and block size: the
+ * block's tile of coarse nodes (one thread per coarse node, each computing
+ * the node's 2^d fine children), for both kernels. The arithmetic per node
+ * does not depend on the shape:
  * results are bitwise identical for every choice. helm_set_tiles /
  * helm_get_tiles set and read the shapes used on fine level `level` (the
  * pair level, level+1); -1 (the initial setting) selects the shape

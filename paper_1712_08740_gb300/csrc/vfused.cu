@@ -5,14 +5,19 @@
 //         r  = b - M u = (1 - wj) b + (1/h^2) sum_nbr c u_nbr
 //         bc = full-weighting restriction of r    (mirrored outside nodes)
 //       and writes u (the pre-smoothed iterate) and bc (the coarse
-//       right-hand side). A block owns a tile of coarse nodes; it stages b
-//       and u for the tile's fine footprint plus a halo of two fine nodes in
-//       shared memory, so each fine u and r is computed once.
+//       right-hand side).
 // up:   from the pre-smoothed u, the coarse correction e and b, one kernel
-//       computes v = u + P e (multilinear prolongation) on a fine tile plus a
-//       halo of one node in shared memory and writes one damped-Jacobi sweep
-//       of v. Up and down never read what they write (u comes from the
-//       level's scratch vector, the result goes to the iterate).
+//       computes v = u + P e (multilinear prolongation) and writes one
+//       damped-Jacobi sweep of v. Up and down never read what they write (u
+//       comes from the level's scratch vector, the result goes to the
+//       iterate).
+//
+// In both kernels a block owns a tile of coarse nodes, one thread per coarse
+// node, and each thread computes the values of that node's 2^d fine
+// children; the tile's fine footprint plus a halo (two fine nodes below,
+// one above for down; one on each side for up) is staged in shared memory,
+// and the halo nodes are shared out among the block's threads, so every fine
+// value is computed once per block with no per-node index search.
 //
 // Both sweeps are written with the inverse diagonal alone, precomputed per
 // level (no division, square root or boundary test per node):
@@ -49,6 +54,12 @@ __device__ __forceinline__ void diag_of(const LevelView<T> &L, const OpShift<T> 
     }
 }
 
+// Explicit fused multiply-adds: a node's value is computed in the block that
+// owns it and again as halo in a neighbouring block, so the arithmetic must
+// not depend on how the compiler contracts a*b + c at each site.
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
 __device__ __forceinline__ int mirror(int i, int n) {
     return i < 0 ? -i : (i > n - 1 ? 2 * (n - 1) - i : i);
 }
@@ -75,26 +86,76 @@ __global__ void k_make_dinv(LevelView<double> L, OpShift<double> s, C *__restric
     }
 }
 
-// Tile shapes. A down shape is the block's tile of coarse nodes (SX x SY x SZ;
-// the block covers twice that on the fine level plus a halo), an up shape the
-// block's tile of fine nodes (even extents); NT is the block size. Index 0 of
-// each list is the default; helm_autotune times every shape on each level and
+// Tile shapes: a block owns a tile of SX x SY x SZ coarse nodes, one thread
+// per coarse node (NT = SX SY SZ threads), and each thread owns the node's
+// fine children (2I + {0,1}, 2J + {0,1}, 2K + {0,1}), so a tile covers twice
+// its extent on the fine level. Index 0 of each list is the first candidate
+// of the automatic choice; helm_autotune times every shape on each level and
 // keeps the fastest. The arithmetic per node does not depend on the shape, so
 // all shapes give bitwise identical results.
-template <int X, int Y, int Z, int NT_> struct Shape {
-    static constexpr int SX = X, SY = Y, SZ = Z, NT = NT_;
+// QP threads share a coarse node's children (QP = 1: one thread computes all
+// 2^d children; QP = 2^d: one thread per fine node, for small levels where
+// latency rather than issue rate bounds the kernel).
+template <int X, int Y, int Z, int NT_, int QP_> struct Shape {
+    static constexpr int SX = X, SY = Y, SZ = Z, NT = NT_, QP = QP_;
+    static_assert(X * Y * Z * QP_ == NT_, "QP threads per coarse node");
 };
 template <int DIM> struct Shapes;
 template <> struct Shapes<2> {
-    using Down = std::tuple<Shape<16, 8, 1, 256>, Shape<8, 8, 1, 128>, Shape<8, 4, 1, 128>,
-                            Shape<32, 4, 1, 256>>;
-    using Up = std::tuple<Shape<32, 8, 1, 256>, Shape<16, 16, 1, 256>, Shape<16, 8, 1, 128>,
-                          Shape<64, 4, 1, 256>>;
+    using Down = std::tuple<Shape<16, 16, 1, 256, 1>, Shape<32, 8, 1, 256, 1>, Shape<16, 8, 1, 128, 1>,
+                            Shape<8, 8, 1, 256, 4>, Shape<8, 4, 1, 128, 4>, Shape<4, 4, 1, 64, 4>>;
+    using Up = Down;
 };
 template <> struct Shapes<3> {
-    using Down = std::tuple<Shape<8, 4, 4, 256>, Shape<8, 4, 2, 128>, Shape<16, 4, 2, 256>>;
-    using Up = std::tuple<Shape<32, 4, 4, 256>, Shape<16, 4, 4, 128>, Shape<32, 8, 2, 256>>;
+    using Down = std::tuple<Shape<8, 4, 4, 128, 1>, Shape<8, 8, 2, 128, 1>, Shape<4, 4, 4, 64, 1>,
+                            Shape<4, 4, 2, 256, 8>>;
+    using Up = Down;
 };
+
+// Halo shells. A block's local box has U = (UX, UY, UZ) nodes per axis; its
+// threads own the interior [L, U - H) of every axis, and the shell (the
+// first L and last H nodes of any axis) is shared out round-robin. shell_pos
+// maps a shell index to local coordinates: whole z-planes first (3D), then
+// y-rows, then x-columns of the remaining rows.
+template <int DIM, int UX, int UY, int UZ, int L, int H> __host__ __device__ constexpr int shell_count() {
+    return DIM == 3 ? UX * UY * UZ - (UX - L - H) * (UY - L - H) * (UZ - L - H)
+                    : UX * UY - (UX - L - H) * (UY - L - H);
+}
+
+template <int DIM, int UX, int UY, int UZ, int L, int H>
+__device__ __forceinline__ void shell_pos(int h, int &lx, int &ly, int &lz) {
+    constexpr int S = L + H;
+    int zlo = 0, zn = 1;
+    if (DIM == 3) {
+        constexpr int A = S * UX * UY;
+        if (h < A) {
+            const int s = h / (UX * UY), rem = h % (UX * UY);
+            lz = s < L ? s : UZ - H + (s - L);
+            ly = rem / UX;
+            lx = rem % UX;
+            return;
+        }
+        h -= A;
+        zlo = L;
+        zn = UZ - S;
+    } else {
+        lz = 0;
+    }
+    const int B = S * UX * zn;
+    if (h < B) {
+        const int s = h / (UX * zn), rem = h % (UX * zn);
+        ly = s < L ? s : UY - H + (s - L);
+        lz = zlo + rem / UX;
+        lx = rem % UX;
+        return;
+    }
+    h -= B;
+    constexpr int NYI = UY - S;
+    const int s = h / (NYI * zn), rem = h % (NYI * zn);
+    lx = s < L ? s : UX - H + (s - L);
+    ly = L + rem % NYI;
+    lz = zlo + rem / NYI;
+}
 
 template <typename T, typename CB, int DIM, typename TL>
 __global__ void __launch_bounds__(TL::NT)
@@ -102,116 +163,158 @@ k_down(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t s
        cplx_t<T> *__restrict__ u, size_t su, cplx_t<T> *__restrict__ bc, size_t sbc,
        const int *__restrict__ active) {
     using C = cplx_t<T>;
-    const int r = blockIdx.z / ((Cv.nz + TL::SZ - 1) / TL::SZ);
-    const int bz = blockIdx.z % ((Cv.nz + TL::SZ - 1) / TL::SZ);
-    if (active && !active[r]) return;
-    b += r * sb;
-    u += r * su;
-    bc += r * sbc;
-    const int I0 = blockIdx.x * TL::SX, J0 = blockIdx.y * TL::SY, K0 = bz * TL::SZ;
-    // u region: fine [2*I0-2, 2*I0+2*CX] per axis (2*CX+3 nodes); r region one node inside
-    constexpr int UX = 2 * TL::SX + 3, UY = 2 * TL::SY + 3, UZ = DIM == 3 ? 2 * TL::SZ + 3 : 1;
+    constexpr int SX = TL::SX, SY = TL::SY, SZ = DIM == 3 ? TL::SZ : 1;
+    // local box of u: fine [2 I0 - 2, 2 I0 + 2 SX] per axis; own children at [2, U - 1)
+    constexpr int UX = 2 * SX + 3, UY = 2 * SY + 3, UZ = DIM == 3 ? 2 * SZ + 3 : 1;
+    constexpr int NQ = DIM == 3 ? 8 : 4;
+    constexpr int NH = shell_count<DIM, UX, UY, UZ, 2, 1>();
+    // r is needed on [2 I0 - 1, 2 I0 + 2 SX - 1]: local [1, U - 1), own part [2, U - 1)
     constexpr int RX = UX - 2, RY = UY - 2, RZ = DIM == 3 ? UZ - 2 : 1;
+    constexpr int NR = shell_count<DIM, RX, RY, RZ, 1, 0>();
+    constexpr int HP = (NH + TL::NT - 1) / TL::NT;
+    const int gz = DIM == 3 ? (Cv.nz + SZ - 1) / SZ : 1;
+    const int rr = blockIdx.z / gz, bz = blockIdx.z % gz;
+    if (active && !active[rr]) return;
+    b += rr * sb;
+    u += rr * su;
+    bc += rr * sbc;
+    const int I0 = blockIdx.x * SX, J0 = blockIdx.y * SY, K0 = bz * SZ;
+    const int X0 = 2 * I0 - 2, Y0 = 2 * J0 - 2, Z0 = DIM == 3 ? 2 * K0 - 2 : 0;
+    constexpr int QP = TL::QP;
+    constexpr int NQL = NQ / QP;                 // children per thread
+    const int cn = threadIdx.x / QP, q0 = threadIdx.x % QP;
+    const int tx = cn % SX, ty = (cn / SX) % SY, tz = DIM == 3 ? cn / (SX * SY) : 0;
+    const size_t fxy = (size_t)F.nx * F.ny;
     extern __shared__ unsigned char smem_raw[];
     C *su_ = reinterpret_cast<C *>(smem_raw);
     C *sb_ = su_ + UX * UY * UZ;
     C *sr_ = sb_ + UX * UY * UZ;
-    const int X0 = 2 * I0 - 2, Y0 = 2 * J0 - 2, Z0 = DIM == 3 ? 2 * K0 - 2 : 0;
-    const size_t fxy = (size_t)F.nx * F.ny;
-    // phase 1: b and u = wj b / d on the u region (in-range nodes). All of a
-    // thread's loads are issued before any of them is used, so a block waits
-    // on one memory latency, not one per node it owns.
-    constexpr int NU = (UX * UY * UZ + TL::NT - 1) / TL::NT;
-    CB bq[NU];
-    C dq[NU];
+    auto in_f = [&](int x, int y, int z) {
+        return x >= 0 && x < F.nx && y >= 0 && y < F.ny && (DIM != 3 || (z >= 0 && z < F.nz));
+    };
+    // loads first: own children, then this thread's share of the halo shell
+    CB bq[NQL], bh[HP];
+    C dq[NQL], dh[HP];
 #pragma unroll
-    for (int k = 0; k < NU; ++k) {
-        const int t = threadIdx.x + k * TL::NT;
-        const int lx = t % UX, ly = (t / UX) % UY, lz = t / (UX * UY);
-        const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
-        if (t < UX * UY * UZ && x >= 0 && x < F.nx && y >= 0 && y < F.ny &&
-            (DIM != 3 || (z >= 0 && z < F.nz))) {
+    for (int k = 0; k < NQL; ++k) {
+        const int q = q0 + k * QP;
+        const int x = 2 * (I0 + tx) + (q & 1), y = 2 * (J0 + ty) + ((q >> 1) & 1),
+                  z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
+        if (in_f(x, y, z)) {
             const size_t p = (size_t)z * fxy + (size_t)y * F.nx + x;
             bq[k] = b[p];
             dq[k] = F.dinv[p];
         }
     }
 #pragma unroll
-    for (int k = 0; k < NU; ++k) {
-        const int t = threadIdx.x + k * TL::NT;
-        const int lx = t % UX, ly = (t / UX) % UY, lz = t / (UX * UY);
-        const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
-        if (t >= UX * UY * UZ || x < 0 || x >= F.nx || y < 0 || y >= F.ny ||
-            (DIM == 3 && (z < 0 || z >= F.nz)))
-            continue;
-        const C bp = cvt<C>(bq[k]);
-        const C di = dq[k];
-        C up;
-        up.x = wj * (di.x * bp.x - di.y * bp.y);
-        up.y = wj * (di.x * bp.y + di.y * bp.x);
-        su_[t] = up;
-        sb_[t] = bp;
-        // owned fine nodes: [2*I0, 2*I0 + 2*CX) per axis
-        if (lx >= 2 && lx < 2 + 2 * TL::SX && ly >= 2 && ly < 2 + 2 * TL::SY &&
-            (DIM == 2 || (lz >= 2 && lz < 2 + 2 * TL::SZ)))
-            u[(size_t)z * fxy + (size_t)y * F.nx + x] = up;
-    }
-    __syncthreads();
-    // phase 2: r = (1 - wj) b + (1/h^2) sum c u_nbr on the r region (in-range nodes)
-    for (int t = threadIdx.x; t < RX * RY * RZ; t += TL::NT) {
-        const int lx = t % RX + 1, ly = (t / RX) % RY + 1, lz = DIM == 3 ? t / (RX * RY) + 1 : 0;
-        const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
-        if (x < 0 || x >= F.nx || y < 0 || y >= F.ny || (DIM == 3 && (z < 0 || z >= F.nz))) continue;
-        const int q = (lz * UY + ly) * UX + lx;
-        T sx = 0, sy = 0;
-        // x axis
-        if (x > 0) { const T c = (x == F.nx - 1) ? T(2) : T(1); sx += c * su_[q - 1].x; sy += c * su_[q - 1].y; }
-        if (x < F.nx - 1) { const T c = (x == 0) ? T(2) : T(1); sx += c * su_[q + 1].x; sy += c * su_[q + 1].y; }
-        if (y > 0) { const T c = (y == F.ny - 1) ? T(2) : T(1); sx += c * su_[q - UX].x; sy += c * su_[q - UX].y; }
-        if (y < F.ny - 1) { const T c = (y == 0) ? T(2) : T(1); sx += c * su_[q + UX].x; sy += c * su_[q + UX].y; }
-        if (DIM == 3) {
-            if (z > 0) { const T c = (z == F.nz - 1) ? T(2) : T(1); sx += c * su_[q - UX * UY].x; sy += c * su_[q - UX * UY].y; }
-            if (z < F.nz - 1) { const T c = (z == 0) ? T(2) : T(1); sx += c * su_[q + UX * UY].x; sy += c * su_[q + UX * UY].y; }
-        }
-        const C bp = sb_[q];
-        C rr;
-        rr.x = (T(1) - wj) * bp.x + F.inv_h2 * sx;
-        rr.y = (T(1) - wj) * bp.y + F.inv_h2 * sy;
-        sr_[t] = rr;
-    }
-    __syncthreads();
-    // phase 3: full weighting onto the tile's coarse nodes
-    const size_t cxy = (size_t)Cv.nx * Cv.ny;
-    for (int t = threadIdx.x; t < TL::SX * TL::SY * TL::SZ; t += TL::NT) {
-        const int I = I0 + t % TL::SX, J = J0 + (t / TL::SX) % TL::SY,
-                  K = K0 + (DIM == 3 ? t / (TL::SX * TL::SY) : 0);
-        if (I >= Cv.nx || J >= Cv.ny || (DIM == 3 && K >= Cv.nz)) continue;
-        T ax = 0, ay = 0;
-#pragma unroll
-        for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz) {
-            const int fz = DIM == 3 ? mirror(2 * K + oz, F.nz) : 0;
-            const T wz = DIM == 3 ? (oz == 0 ? T(0.5) : T(0.25)) : T(1);
-            const int rz = DIM == 3 ? fz - (Z0 + 1) : 0;
-#pragma unroll
-            for (int oy = -1; oy <= 1; ++oy) {
-                const int fy = mirror(2 * J + oy, F.ny);
-                const T wy = oy == 0 ? T(0.5) : T(0.25);
-                const int ry = fy - (Y0 + 1);
-#pragma unroll
-                for (int ox = -1; ox <= 1; ++ox) {
-                    const int fx = mirror(2 * I + ox, F.nx);
-                    const T wgt = (ox == 0 ? T(0.5) : T(0.25)) * wy * wz;
-                    const C v = sr_[(rz * RY + ry) * RX + (fx - (X0 + 1))];
-                    ax += wgt * v.x;
-                    ay += wgt * v.y;
-                }
+    for (int k = 0; k < HP; ++k) {
+        const int hidx = threadIdx.x + k * TL::NT;
+        if (hidx < NH) {
+            int lx, ly, lz;
+            shell_pos<DIM, UX, UY, UZ, 2, 1>(hidx, lx, ly, lz);
+            const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
+            if (in_f(x, y, z)) {
+                const size_t p = (size_t)z * fxy + (size_t)y * F.nx + x;
+                bh[k] = b[p];
+                dh[k] = F.dinv[p];
             }
         }
-        C o;
-        o.x = ax;
-        o.y = ay;
-        bc[(size_t)K * cxy + (size_t)J * Cv.nx + I] = o;
     }
+    // u = wj D^-1 b (first Jacobi sweep from zero) on the whole box
+    auto put_u = [&](int t, CB braw, C di) {
+        const C bp = cvt<C>(braw);
+        C up;
+        up.x = wj * fmaT(di.x, bp.x, -(di.y * bp.y));
+        up.y = wj * fmaT(di.x, bp.y, di.y * bp.x);
+        su_[t] = up;
+        sb_[t] = bp;
+        return up;
+    };
+#pragma unroll
+    for (int k = 0; k < HP; ++k) {
+        const int hidx = threadIdx.x + k * TL::NT;
+        if (hidx < NH) {
+            int lx, ly, lz;
+            shell_pos<DIM, UX, UY, UZ, 2, 1>(hidx, lx, ly, lz);
+            if (in_f(X0 + lx, Y0 + ly, Z0 + lz)) put_u((lz * UY + ly) * UX + lx, bh[k], dh[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NQL; ++k) {
+        const int q = q0 + k * QP;
+        const int x = 2 * (I0 + tx) + (q & 1), y = 2 * (J0 + ty) + ((q >> 1) & 1),
+                  z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
+        if (in_f(x, y, z)) {
+            const int t = ((z - Z0) * UY + (y - Y0)) * UX + (x - X0);
+            u[(size_t)z * fxy + (size_t)y * F.nx + x] = put_u(t, bq[k], dq[k]);
+        }
+    }
+    __syncthreads();
+    // r = (1 - wj) b + (1/h^2) sum_nbr c u_nbr on the r box
+    auto put_r = [&](int lx, int ly, int lz) {
+        const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
+        const int q = (lz * UY + ly) * UX + lx;
+        T sx = 0, sy = 0;
+        if (x > 0) { const T c = (x == F.nx - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - 1].x, sx); sy = fmaT(c, su_[q - 1].y, sy); }
+        if (x < F.nx - 1) { const T c = (x == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + 1].x, sx); sy = fmaT(c, su_[q + 1].y, sy); }
+        if (y > 0) { const T c = (y == F.ny - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - UX].x, sx); sy = fmaT(c, su_[q - UX].y, sy); }
+        if (y < F.ny - 1) { const T c = (y == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + UX].x, sx); sy = fmaT(c, su_[q + UX].y, sy); }
+        if (DIM == 3) {
+            if (z > 0) { const T c = (z == F.nz - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - UX * UY].x, sx); sy = fmaT(c, su_[q - UX * UY].y, sy); }
+            if (z < F.nz - 1) { const T c = (z == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + UX * UY].x, sx); sy = fmaT(c, su_[q + UX * UY].y, sy); }
+        }
+        const C bp = sb_[q];
+        const T omw = T(1) - wj;
+        C o;
+        o.x = fmaT(F.inv_h2, sx, omw * bp.x);
+        o.y = fmaT(F.inv_h2, sy, omw * bp.y);
+        sr_[q] = o;
+    };
+    for (int hidx = threadIdx.x; hidx < NR; hidx += TL::NT) {
+        int lx, ly, lz;
+        shell_pos<DIM, RX, RY, RZ, 1, 0>(hidx, lx, ly, lz);
+        ++lx;
+        ++ly;
+        if (DIM == 3) ++lz;
+        if (in_f(X0 + lx, Y0 + ly, Z0 + lz)) put_r(lx, ly, lz);
+    }
+#pragma unroll
+    for (int k = 0; k < NQL; ++k) {
+        const int q = q0 + k * QP;
+        const int x = 2 * (I0 + tx) + (q & 1), y = 2 * (J0 + ty) + ((q >> 1) & 1),
+                  z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
+        if (in_f(x, y, z)) put_r(x - X0, y - Y0, z - Z0);
+    }
+    __syncthreads();
+    // full weighting, one coarse node per thread: threads 0 .. SX SY SZ - 1
+    // (whole warps; r is in shared memory), outside nodes mirrored
+    if (threadIdx.x >= SX * SY * SZ) return;
+    const int rx = threadIdx.x % SX, ry = (threadIdx.x / SX) % SY, rz = DIM == 3 ? threadIdx.x / (SX * SY) : 0;
+    const int I = I0 + rx, J = J0 + ry, K = K0 + rz;
+    if (I >= Cv.nx || J >= Cv.ny || (DIM == 3 && K >= Cv.nz)) return;
+    T ax = 0, ay = 0;
+#pragma unroll
+    for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz) {
+        const int lz = DIM == 3 ? mirror(2 * K + oz, F.nz) - Z0 : 0;
+        const T wz = DIM == 3 ? (oz == 0 ? T(0.5) : T(0.25)) : T(1);
+#pragma unroll
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int ly = mirror(2 * J + oy, F.ny) - Y0;
+            const T wy = oy == 0 ? T(0.5) : T(0.25);
+#pragma unroll
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int lx = mirror(2 * I + ox, F.nx) - X0;
+                const T wgt = (ox == 0 ? T(0.5) : T(0.25)) * wy * wz;
+                const C v = sr_[(lz * UY + ly) * UX + lx];
+                ax = fmaT(wgt, v.x, ax);
+                ay = fmaT(wgt, v.y, ay);
+            }
+        }
+    }
+    C o;
+    o.x = ax;
+    o.y = ay;
+    bc[(size_t)K * Cv.nx * Cv.ny + (size_t)J * Cv.nx + I] = o;
 }
 
 template <typename T, typename CB, int DIM, typename TL>
@@ -220,78 +323,81 @@ k_up(LevelView<T> F, LevelView<T> Cv, T wj, const cplx_t<T> *__restrict__ uin,
      size_t sin, const cplx_t<T> *__restrict__ ec, size_t sec, const CB *__restrict__ b, size_t sb,
      cplx_t<T> *__restrict__ uout, size_t sout, const int *__restrict__ active) {
     using C = cplx_t<T>;
-    const int nzb = (F.nz + TL::SZ - 1) / TL::SZ;
-    const int r = blockIdx.z / nzb;
-    const int bz = blockIdx.z % nzb;
-    if (active && !active[r]) return;
-    uin += r * sin;
-    ec += r * sec;
-    b += r * sb;
-    uout += r * sout;
-    const int x0 = blockIdx.x * TL::SX, y0 = blockIdx.y * TL::SY, z0 = bz * TL::SZ;
-    constexpr int VX = TL::SX + 2, VY = TL::SY + 2, VZ = DIM == 3 ? TL::SZ + 2 : 1;
-    constexpr int EX = TL::SX / 2 + 2, EY = TL::SY / 2 + 2, EZ = DIM == 3 ? TL::SZ / 2 + 2 : 1;
+    constexpr int SX = TL::SX, SY = TL::SY, SZ = DIM == 3 ? TL::SZ : 1;
+    // local box of v: fine [2 I0 - 1, 2 I0 + 2 SX] per axis; own children at [1, V - 1)
+    constexpr int VX = 2 * SX + 2, VY = 2 * SY + 2, VZ = DIM == 3 ? 2 * SZ + 2 : 1;
+    // coarse correction needed on [I0 - 1, I0 + SX]
+    constexpr int EX = SX + 2, EY = SY + 2, EZ = DIM == 3 ? SZ + 2 : 1;
+    constexpr int NQ = DIM == 3 ? 8 : 4;
+    constexpr int NH = shell_count<DIM, VX, VY, VZ, 1, 1>();
+    constexpr int HP = (NH + TL::NT - 1) / TL::NT;
+    constexpr int EP = (EX * EY * EZ + TL::NT - 1) / TL::NT;
+    const int gz = DIM == 3 ? (Cv.nz + SZ - 1) / SZ : 1;
+    const int rr = blockIdx.z / gz, bz = blockIdx.z % gz;
+    if (active && !active[rr]) return;
+    uin += rr * sin;
+    ec += rr * sec;
+    b += rr * sb;
+    uout += rr * sout;
+    const int I0 = blockIdx.x * SX, J0 = blockIdx.y * SY, K0 = bz * SZ;
+    const int X0 = 2 * I0 - 1, Y0 = 2 * J0 - 1, Z0 = DIM == 3 ? 2 * K0 - 1 : 0;
+    const int CX0 = I0 - 1, CY0 = J0 - 1, CZ0 = DIM == 3 ? K0 - 1 : 0;
+    constexpr int QP = TL::QP;
+    constexpr int NQL = NQ / QP;                 // children per thread
+    const int cn = threadIdx.x / QP, q0 = threadIdx.x % QP;
+    const int tx = cn % SX, ty = (cn / SX) % SY, tz = DIM == 3 ? cn / (SX * SY) : 0;
+    const size_t fxy = (size_t)F.nx * F.ny, cxy = (size_t)Cv.nx * Cv.ny;
     extern __shared__ unsigned char smem_raw[];
     C *sv_ = reinterpret_cast<C *>(smem_raw);
     C *se_ = sv_ + VX * VY * VZ;
-    const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1, cz0 = DIM == 3 ? z0 / 2 - 1 : 0;
-    const size_t cxy = (size_t)Cv.nx * Cv.ny, fxy = (size_t)F.nx * F.ny;
-    // All global loads of the three phases are issued up front (coarse
-    // correction, pre-smoothed iterate with its halo, and b and w of the owned
-    // nodes), so a block waits on one memory latency instead of three.
-    constexpr int NE = (EX * EY * EZ + TL::NT - 1) / TL::NT;
-    constexpr int NV = (VX * VY * VZ + TL::NT - 1) / TL::NT;
-    constexpr int NO = (TL::SX * TL::SY * TL::SZ + TL::NT - 1) / TL::NT;
-    C eq[NE], uq[NV];
-    CB bq[NO];
-    C dq[NO];
+    auto in_f = [&](int x, int y, int z) {
+        return x >= 0 && x < F.nx && y >= 0 && y < F.ny && (DIM != 3 || (z >= 0 && z < F.nz));
+    };
+    // loads first: coarse correction tile, own children (u, b, D^-1), halo u
+    C eq[EP], uq[NQL], dq[NQL], uh[HP];
+    CB bq[NQL];
 #pragma unroll
-    for (int k = 0; k < NE; ++k) {
+    for (int k = 0; k < EP; ++k) {
         const int t = threadIdx.x + k * TL::NT;
-        const int X = cx0 + t % EX, Y = cy0 + (t / EX) % EY, Z = cz0 + (DIM == 3 ? t / (EX * EY) : 0);
+        const int X = CX0 + t % EX, Y = CY0 + (t / EX) % EY, Z = CZ0 + (DIM == 3 ? t / (EX * EY) : 0);
         if (t < EX * EY * EZ && X >= 0 && X < Cv.nx && Y >= 0 && Y < Cv.ny &&
             (DIM != 3 || (Z >= 0 && Z < Cv.nz)))
             eq[k] = ec[(size_t)Z * cxy + (size_t)Y * Cv.nx + X];
     }
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int t = threadIdx.x + k * TL::NT;
-        const int x = x0 - 1 + t % VX, y = y0 - 1 + (t / VX) % VY,
-                  z = DIM == 3 ? z0 - 1 + t / (VX * VY) : 0;
-        if (t < VX * VY * VZ && x >= 0 && x < F.nx && y >= 0 && y < F.ny &&
-            (DIM != 3 || (z >= 0 && z < F.nz)))
-            uq[k] = uin[(size_t)z * fxy + (size_t)y * F.nx + x];
-    }
-#pragma unroll
-    for (int k = 0; k < NO; ++k) {
-        const int t = threadIdx.x + k * TL::NT;
-        const int x = x0 + t % TL::SX, y = y0 + (t / TL::SX) % TL::SY,
-                  z = DIM == 3 ? z0 + t / (TL::SX * TL::SY) : 0;
-        if (t < TL::SX * TL::SY * TL::SZ && x < F.nx && y < F.ny && (DIM != 3 || z < F.nz)) {
+    for (int k = 0; k < NQL; ++k) {
+        const int q = q0 + k * QP;
+        const int x = 2 * (I0 + tx) + (q & 1), y = 2 * (J0 + ty) + ((q >> 1) & 1),
+                  z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
+        if (in_f(x, y, z)) {
             const size_t p = (size_t)z * fxy + (size_t)y * F.nx + x;
+            uq[k] = uin[p];
             bq[k] = b[p];
             dq[k] = F.dinv[p];
         }
     }
-    // phase 1: coarse correction around the tile
 #pragma unroll
-    for (int k = 0; k < NE; ++k) {
+    for (int k = 0; k < HP; ++k) {
+        const int hidx = threadIdx.x + k * TL::NT;
+        if (hidx < NH) {
+            int lx, ly, lz;
+            shell_pos<DIM, VX, VY, VZ, 1, 1>(hidx, lx, ly, lz);
+            const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
+            if (in_f(x, y, z)) uh[k] = uin[(size_t)z * fxy + (size_t)y * F.nx + x];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < EP; ++k) {
         const int t = threadIdx.x + k * TL::NT;
         if (t < EX * EY * EZ) se_[t] = eq[k];
     }
     __syncthreads();
-    // phase 2: v = u + P e on the tile plus a one-node halo
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int t = threadIdx.x + k * TL::NT;
-        const int x = x0 - 1 + t % VX, y = y0 - 1 + (t / VX) % VY,
-                  z = DIM == 3 ? z0 - 1 + t / (VX * VY) : 0;
-        if (t >= VX * VY * VZ || x < 0 || x >= F.nx || y < 0 || y >= F.ny ||
-            (DIM == 3 && (z < 0 || z >= F.nz)))
-            continue;
-        const int ax = (x >> 1) - cx0, bxp = ((x + 1) >> 1) - cx0;
-        const int ay = (y >> 1) - cy0, byp = ((y + 1) >> 1) - cy0;
-        const int az = DIM == 3 ? (z >> 1) - cz0 : 0, bzp = DIM == 3 ? ((z + 1) >> 1) - cz0 : 0;
+    // v = u + P e (multilinear prolongation) on the whole box
+    auto put_v = [&](int lx, int ly, int lz, C uv) {
+        const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
+        const int ax = (x >> 1) - CX0, bxp = ((x + 1) >> 1) - CX0;
+        const int ay = (y >> 1) - CY0, byp = ((y + 1) >> 1) - CY0;
+        const int az = DIM == 3 ? (z >> 1) - CZ0 : 0, bzp = DIM == 3 ? ((z + 1) >> 1) - CZ0 : 0;
         const T wx = (x & 1) ? T(0.5) : T(1), wy = (y & 1) ? T(0.5) : T(1),
                 wz = (DIM == 3 && (z & 1)) ? T(0.5) : T(1);
         T px = 0, py = 0;
@@ -314,50 +420,63 @@ k_up(LevelView<T> F, LevelView<T> Cv, T wj, const cplx_t<T> *__restrict__ uin,
             }
         }
         const T wgt = wx * wy * wz;
-        C v = uq[k];
-        v.x += wgt * px;
-        v.y += wgt * py;
-        sv_[t] = v;
+        uv.x = fmaT(wgt, px, uv.x);
+        uv.y = fmaT(wgt, py, uv.y);
+        sv_[(lz * VY + ly) * VX + lx] = uv;
+    };
+#pragma unroll
+    for (int k = 0; k < HP; ++k) {
+        const int hidx = threadIdx.x + k * TL::NT;
+        if (hidx < NH) {
+            int lx, ly, lz;
+            shell_pos<DIM, VX, VY, VZ, 1, 1>(hidx, lx, ly, lz);
+            if (in_f(X0 + lx, Y0 + ly, Z0 + lz)) put_v(lx, ly, lz, uh[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NQL; ++k) {
+        const int q = q0 + k * QP;
+        const int x = 2 * (I0 + tx) + (q & 1), y = 2 * (J0 + ty) + ((q >> 1) & 1),
+                  z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
+        if (in_f(x, y, z)) put_v(x - X0, y - Y0, z - Z0, uq[k]);
     }
     __syncthreads();
-    // phase 3: one damped-Jacobi sweep on the tile
+    // one damped-Jacobi sweep on the own children
 #pragma unroll
-    for (int k = 0; k < NO; ++k) {
-        const int t = threadIdx.x + k * TL::NT;
-        const int lx = t % TL::SX, ly = (t / TL::SX) % TL::SY, lz = DIM == 3 ? t / (TL::SX * TL::SY) : 0;
-        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-        if (t >= TL::SX * TL::SY * TL::SZ || x >= F.nx || y >= F.ny || (DIM == 3 && z >= F.nz)) continue;
-        const int q = ((DIM == 3 ? lz + 1 : 0) * VY + ly + 1) * VX + lx + 1;
+    for (int k = 0; k < NQL; ++k) {
+        const int q = q0 + k * QP;
+        const int x = 2 * (I0 + tx) + (q & 1), y = 2 * (J0 + ty) + ((q >> 1) & 1),
+                  z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
+        if (!in_f(x, y, z)) continue;
+        const int qq = ((z - Z0) * VY + (y - Y0)) * VX + (x - X0);
         T sx = 0, sy = 0;
-        if (x > 0) { const T c = (x == F.nx - 1) ? T(2) : T(1); sx += c * sv_[q - 1].x; sy += c * sv_[q - 1].y; }
-        if (x < F.nx - 1) { const T c = (x == 0) ? T(2) : T(1); sx += c * sv_[q + 1].x; sy += c * sv_[q + 1].y; }
-        if (y > 0) { const T c = (y == F.ny - 1) ? T(2) : T(1); sx += c * sv_[q - VX].x; sy += c * sv_[q - VX].y; }
-        if (y < F.ny - 1) { const T c = (y == 0) ? T(2) : T(1); sx += c * sv_[q + VX].x; sy += c * sv_[q + VX].y; }
+        if (x > 0) { const T c = (x == F.nx - 1) ? T(2) : T(1); sx = fmaT(c, sv_[qq - 1].x, sx); sy = fmaT(c, sv_[qq - 1].y, sy); }
+        if (x < F.nx - 1) { const T c = (x == 0) ? T(2) : T(1); sx = fmaT(c, sv_[qq + 1].x, sx); sy = fmaT(c, sv_[qq + 1].y, sy); }
+        if (y > 0) { const T c = (y == F.ny - 1) ? T(2) : T(1); sx = fmaT(c, sv_[qq - VX].x, sx); sy = fmaT(c, sv_[qq - VX].y, sy); }
+        if (y < F.ny - 1) { const T c = (y == 0) ? T(2) : T(1); sx = fmaT(c, sv_[qq + VX].x, sx); sy = fmaT(c, sv_[qq + VX].y, sy); }
         if (DIM == 3) {
-            if (z > 0) { const T c = (z == F.nz - 1) ? T(2) : T(1); sx += c * sv_[q - VX * VY].x; sy += c * sv_[q - VX * VY].y; }
-            if (z < F.nz - 1) { const T c = (z == 0) ? T(2) : T(1); sx += c * sv_[q + VX * VY].x; sy += c * sv_[q + VX * VY].y; }
+            if (z > 0) { const T c = (z == F.nz - 1) ? T(2) : T(1); sx = fmaT(c, sv_[qq - VX * VY].x, sx); sy = fmaT(c, sv_[qq - VX * VY].y, sy); }
+            if (z < F.nz - 1) { const T c = (z == 0) ? T(2) : T(1); sx = fmaT(c, sv_[qq + VX * VY].x, sx); sy = fmaT(c, sv_[qq + VX * VY].y, sy); }
         }
-        const size_t p = (size_t)z * fxy + (size_t)y * F.nx + x;
-        const C vp = sv_[q];
+        const C vp = sv_[qq];
         const C bp = cvt<C>(bq[k]);
         const C di = dq[k];
-        const T gx = bp.x + F.inv_h2 * sx, gy = bp.y + F.inv_h2 * sy;
+        const T gx = fmaT(F.inv_h2, sx, bp.x), gy = fmaT(F.inv_h2, sy, bp.y);
         const T omw = T(1) - wj;
         C o;
-        o.x = omw * vp.x + wj * (di.x * gx - di.y * gy);
-        o.y = omw * vp.y + wj * (di.x * gy + di.y * gx);
-        uout[p] = o;
+        o.x = fmaT(omw, vp.x, wj * fmaT(di.x, gx, -(di.y * gy)));
+        o.y = fmaT(omw, vp.y, wj * fmaT(di.x, gy, di.y * gx));
+        uout[(size_t)z * fxy + (size_t)y * F.nx + x] = o;
     }
 }
 
 template <int DIM, typename TL> constexpr size_t down_smem(size_t csz) {
     constexpr int UX = 2 * TL::SX + 3, UY = 2 * TL::SY + 3, UZ = DIM == 3 ? 2 * TL::SZ + 3 : 1;
-    constexpr int RX = UX - 2, RY = UY - 2, RZ = DIM == 3 ? UZ - 2 : 1;
-    return csz * (2 * UX * UY * UZ + RX * RY * RZ);
+    return csz * 3 * UX * UY * UZ;
 }
 template <int DIM, typename TL> constexpr size_t up_smem(size_t csz) {
-    constexpr int VX = TL::SX + 2, VY = TL::SY + 2, VZ = DIM == 3 ? TL::SZ + 2 : 1;
-    constexpr int EX = TL::SX / 2 + 2, EY = TL::SY / 2 + 2, EZ = DIM == 3 ? TL::SZ / 2 + 2 : 1;
+    constexpr int VX = 2 * TL::SX + 2, VY = 2 * TL::SY + 2, VZ = DIM == 3 ? 2 * TL::SZ + 2 : 1;
+    constexpr int EX = TL::SX + 2, EY = TL::SY + 2, EZ = DIM == 3 ? TL::SZ + 2 : 1;
     return csz * (VX * VY * VZ + EX * EY * EZ);
 }
 
@@ -366,7 +485,7 @@ void down_impl(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB *b,
                size_t sb, cplx_t<T> *u, size_t su, cplx_t<T> *bc, size_t sbc, int nb,
                const int *active, cudaStream_t st) {
     const size_t sm = down_smem<DIM, TL>(sizeof(cplx_t<T>));
-    const int gz = (Cv.nz + TL::SZ - 1) / TL::SZ;
+    const int gz = DIM == 3 ? (Cv.nz + TL::SZ - 1) / TL::SZ : 1;
     dim3 g((Cv.nx + TL::SX - 1) / TL::SX, (Cv.ny + TL::SY - 1) / TL::SY, gz * nb);
     k_down<T, CB, DIM, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, b, sb, u, su, bc, sbc, active);
 }
@@ -376,8 +495,8 @@ void up_impl(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
              const cplx_t<T> *uin, size_t sin, const cplx_t<T> *ec, size_t sec, const CB *b,
              size_t sb, cplx_t<T> *uout, size_t sout, int nb, const int *active, cudaStream_t st) {
     const size_t sm = up_smem<DIM, TL>(sizeof(cplx_t<T>));
-    const int gz = (F.nz + TL::SZ - 1) / TL::SZ;
-    dim3 g((F.nx + TL::SX - 1) / TL::SX, (F.ny + TL::SY - 1) / TL::SY, gz * nb);
+    const int gz = DIM == 3 ? (Cv.nz + TL::SZ - 1) / TL::SZ : 1;
+    dim3 g((Cv.nx + TL::SX - 1) / TL::SX, (Cv.ny + TL::SY - 1) / TL::SY, gz * nb);
     k_up<T, CB, DIM, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, uin, sin, ec, sec, b, sb, uout, sout, active);
 }
 
@@ -468,7 +587,7 @@ bool tile_shape(int dim, int kernel, int shape, int ext[3], int *threads) {
 int auto_tile_shape(int dim, int kernel, const int fine[3], int nb) {
     const int ns = num_tile_shapes(dim);
     const int cn[3] = {(fine[0] + 1) / 2, (fine[1] + 1) / 2, (fine[2] + 1) / 2};
-    const int *ext_of = kernel == 0 ? cn : fine;   // down tiles cover coarse nodes, up tiles fine
+    const int *ext_of = cn;                        // both kernels tile the coarse nodes
     long long best_blocks = -1;
     int best = 0;
     for (int sh = 0; sh < ns; ++sh) {
