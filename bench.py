@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default="plain", choices=["plain", "batched"],
+                    help="region bracketed by cudaProfilerStart/Stop for ncu --profile-from-start "
+                         "off: the plain timed solves, or one extra (untimed) solve of the "
+                         "64-source batch with the double-single basis")
     return ap.parse_args()
 
 
@@ -295,7 +299,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     l0 = helm.helm_kernel_launches()
-    torch.cuda.cudart().cudaProfilerStart()     # ncu --profile-from-start off: timed region only
+    if args.profile == "plain":
+        torch.cuda.cudart().cudaProfilerStart()     # ncu --profile-from-start off: timed region only
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     its_l, rr_l = [], []
@@ -307,7 +312,8 @@ def main():
         its_l.append(its)
         rr_l.append(rr)
     torch.cuda.synchronize()
-    torch.cuda.cudart().cudaProfilerStop()
+    if args.profile == "plain":
+        torch.cuda.cudart().cudaProfilerStop()
     if world > 1:
         dist.barrier()
     launches = helm.helm_kernel_launches() - l0
@@ -398,12 +404,33 @@ def main():
             torch.cuda.synchronize()
             bt.append(e0.elapsed_time(e1))
         bms = statistics.median(bt)
+        if args.profile == "batched" and form == "mixed_ds":
+            torch.cuda.cudart().cudaProfilerStart()
+            gb.solve_batch(BATCH_SOURCES, Fd, w.tol, Ud)
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
+        bkern = None
+        if form == "mixed_ds":
+            # one more (untimed) solve with the library's per-launch CUDA-event
+            # profiler: algorithmic bytes per kernel over its device time, as a
+            # fraction of the measured copy bandwidth (all levels and steps)
+            helm.helm_profile_start()
+            gb.solve_batch(BATCH_SOURCES, Fd, w.tol, Ud)
+            prof = helm.helm_profile_stop()
+            bkern = {}
+            for name, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:9]:
+                gbs = v["bytes"] / v["ms"] / 1e6 if v["ms"] > 0 else 0.0
+                bkern[name] = {"launches": v["launches"], "ms": round(v["ms"], 3),
+                              "us_per_launch": round(v["ms"] / v["launches"] * 1e3, 2),
+                              "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3)}
         batched_forms[form] = {
             "solves_per_s": world * BATCH_SOURCES / (bms / 1e3), "nrhs": BATCH_SOURCES,
             "ms_per_batch": bms, "iterations_max": int(bits.max()),
             "iterations_mean": float(bits.mean()), "true_rel_residual_max": float(brr.max()),
             "vs_plain": (world * BATCH_SOURCES / (bms / 1e3)) / value,
             "autotune": tune_summary(helm, 2, tune)}
+        if bkern:
+            batched_forms[form]["kernels"] = bkern
         del gb
     batched = dict(batched_forms["mixed_ds"])
     batched["precision"] = ("complex64 V-cycle, double-single Arnoldi basis, complex128 "
