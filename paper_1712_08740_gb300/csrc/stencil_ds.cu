@@ -153,8 +153,9 @@ void launch_apply_H_ds(const LevelView<double> &L, const float4 *hd, const float
     else k_apply_H_ds<3><<<g, kBX, 0, st>>>(L, hd, ihh, ihl, z, sz, w, sw, active);
     count_launch();
     if (prof_on()) {
-        const double n = (double)L.nx * L.ny * L.nz * nb;
-        prof_end("stencil_apply_ds", st, n * (8.0 + 16.0 + 16.0), 0.0);
+        // per right-hand side: z in, w out; the diagonal once per launch
+        const double n1 = (double)L.nx * L.ny * L.nz, n = n1 * nb;
+        prof_end("stencil_apply_ds", st, n * (8.0 + 16.0) + n1 * 16.0, 0.0);
     }
 }
 

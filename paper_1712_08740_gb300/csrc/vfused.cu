@@ -627,10 +627,13 @@ void launch_vdown(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB 
                            bc, sbc, nb, active, st);
     count_launch();
     if (prof_on()) {
-        const double nf = (double)F.nx * F.ny * F.nz * nb, nc = (double)Cv.nx * Cv.ny * Cv.nz * nb;
+        // per right-hand side: b in, u and the coarse right-hand side out;
+        // D^-1 once per launch (shared by the right-hand sides)
+        const double n1 = (double)F.nx * F.ny * F.nz;
+        const double nf = n1 * nb, nc = (double)Cv.nx * Cv.ny * Cv.nz * nb;
         prof_end(sizeof(T) == 8 ? "vdown_f64" : "vdown_f32", st,
-                 nf * (sizeof(CB) + 2.0 * sizeof(cplx_t<T>)) + nc * sizeof(cplx_t<T>),
-                 sizeof(T) == 8 ? nf * 40.0 : 0.0);
+                 nf * (sizeof(CB) + sizeof(cplx_t<T>)) + n1 * sizeof(cplx_t<T>) + nc * sizeof(cplx_t<T>),
+                 sizeof(T) == 8 ? nf * 26.0 : 0.0);
     }
 }
 
@@ -648,10 +651,13 @@ void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
                          sb, uout, sout, nb, active, st);
     count_launch();
     if (prof_on()) {
-        const double nf = (double)F.nx * F.ny * F.nz * nb, nc = (double)Cv.nx * Cv.ny * Cv.nz * nb;
+        // per right-hand side: u and b in, the sweep out, the coarse
+        // correction in; D^-1 once per launch
+        const double n1 = (double)F.nx * F.ny * F.nz;
+        const double nf = n1 * nb, nc = (double)Cv.nx * Cv.ny * Cv.nz * nb;
         prof_end(sizeof(T) == 8 ? "vup_f64" : "vup_f32", st,
-                 nf * (3.0 * sizeof(cplx_t<T>) + sizeof(CB)) + nc * sizeof(cplx_t<T>),
-                 sizeof(T) == 8 ? nf * 44.0 : 0.0);
+                 nf * (2.0 * sizeof(cplx_t<T>) + sizeof(CB)) + n1 * sizeof(cplx_t<T>) + nc * sizeof(cplx_t<T>),
+                 sizeof(T) == 8 ? nf * 24.0 : 0.0);
     }
 }
 
