@@ -329,7 +329,13 @@ void launch_givens_scale(const CycleState &S, int j, const double2 *hb, int hstr
     const size_t qsm = (2 * ld + ld * ld) * sizeof(double2);
     const bool qs = qsm <= 96 * 1024;
     const size_t sm = qs ? qsm : 2 * ld * sizeof(double2);
+    // scaling blocks per right-hand side: one node per thread for a single
+    // right-hand side; for batches about 1216 blocks in all, so each block's
+    // set-up (1/||w|| in FP64) is spread over many nodes
     size_t nbs = (N + kGivensThreads - 1) / kGivensThreads;
+    const size_t cap = (size_t)((1216 + nrhs - 1) / nrhs);
+    if (nrhs > 1 && nbs > cap) nbs = cap;
+    if (nbs < 1) nbs = 1;
     if (nbs > 65535) nbs = 65535;
     prof_begin(st);
     k_givens_scale<SV><<<dim3(1 + (unsigned)nbs, nrhs), kGivensThreads, sm, st>>>(
