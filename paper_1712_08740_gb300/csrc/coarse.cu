@@ -254,7 +254,19 @@ k_coarse_gemm(const cplx_t<T> *__restrict__ At, int n, const cplx_t<T> *__restri
         if (!use[k]) continue;
         const C *pk = part + (size_t)(kt * RT + k) * G * n + i;
         C s = __ldcg(pk);
-        for (int q = 1; q < G; ++q) {
+        int q = 1;
+        // eight group sums in flight at a time, added in group order
+        for (; q + 8 <= G; q += 8) {
+            C v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(pk + (size_t)(q + u) * n);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                s.x += v[u].x;
+                s.y += v[u].y;
+            }
+        }
+        for (; q < G; ++q) {
             const C v = __ldcg(pk + (size_t)q * n);
             s.x += v.x;
             s.y += v.y;

@@ -105,6 +105,46 @@ template <typename T> struct OpShift {
     T q_re, q_im;            // q
 };
 
+// ------------------------------------------------------------ last-block reductions
+// Sum of p[lane], p[lane + 32], p[lane + 64], ... (n values in all, in this
+// order), as one lane's share of a cross-block reduction: four loads are in
+// flight at a time instead of one per dependent add.
+__device__ __forceinline__ void lane_sum(const double2 *p, unsigned n, unsigned lane, double &sx,
+                                         double &sy) {
+    sx = 0.0;
+    sy = 0.0;
+    unsigned b = lane;
+    for (; b + 96 < n; b += 128) {
+        const double2 v0 = p[b], v1 = p[b + 32], v2 = p[b + 64], v3 = p[b + 96];
+        sx += v0.x;
+        sy += v0.y;
+        sx += v1.x;
+        sy += v1.y;
+        sx += v2.x;
+        sy += v2.y;
+        sx += v3.x;
+        sy += v3.y;
+    }
+    for (; b < n; b += 32) {
+        const double2 v = p[b];
+        sx += v.x;
+        sy += v.y;
+    }
+}
+__device__ __forceinline__ double lane_sum(const double *p, unsigned n, unsigned lane) {
+    double s = 0.0;
+    unsigned b = lane;
+    for (; b + 96 < n; b += 128) {
+        const double v0 = p[b], v1 = p[b + 32], v2 = p[b + 64], v3 = p[b + 96];
+        s += v0;
+        s += v1;
+        s += v2;
+        s += v3;
+    }
+    for (; b < n; b += 32) s += p[b];
+    return s;
+}
+
 // ------------------------------------------------------------ launch counter + profiler
 void count_launch(uint64_t k = 1);
 void uncount_launch(uint64_t k);     // kernels that were captured into a graph, not run

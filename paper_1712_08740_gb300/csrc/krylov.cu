@@ -122,12 +122,8 @@ k_multidot(const double2 *__restrict__ V, size_t sV, int nvec, const double2 *__
     if (last_block(counter + r)) {
         const double2 *pr = partial + (size_t)r * nvec_max * gridDim.x;
         for (int i = warp; i < nvec; i += kWarps) {
-            double sx = 0.0, sy = 0.0;
-            for (unsigned b = lane; b < gridDim.x; b += 32) {
-                const double2 v = pr[(size_t)i * gridDim.x + b];
-                sx += v.x;
-                sy += v.y;
-            }
+            double sx, sy;
+            lane_sum(pr + (size_t)i * gridDim.x, gridDim.x, lane, sx, sy);
             sx = warp_sum(sx);
             sy = warp_sum(sy);
             if (lane == 0) out[r * ostride + i] = make_double2(sx, sy);
@@ -150,8 +146,7 @@ __device__ void reduce_norm(double v, double *partial_d, unsigned *counter, doub
     }
     if (last_block(counter + r)) {
         if (warp == 0) {
-            double s = 0.0;
-            for (unsigned b = lane; b < gridDim.x; b += 32) s += partial_d[(size_t)r * gridDim.x + b];
+            double s = lane_sum(partial_d + (size_t)r * gridDim.x, gridDim.x, lane);
             s = warp_sum(s);
             if (lane == 0) {
                 norm2[r] = s;
