@@ -38,6 +38,16 @@ __device__ __forceinline__ void ds_fma(float &h, float &l, float ah, float al, f
     l += err + e;
 }
 
+// (h, l) = a * b for a fresh accumulator: the same bits as ds_fma into (0, 0)
+__device__ __forceinline__ void ds_init(float &h, float &l, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    h = p;
+    l = e;
+}
+
 // (h, l) += (bh, bl), renormalised
 __device__ __forceinline__ void ds_add(float &h, float &l, float bh, float bl) {
     const float s = h + bh;
@@ -106,7 +116,10 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
         for (int q = 0; q < 16; ++q) h[q] = l[q] = 0.f;
         // two of the thread's nodes per round, all their loads issued before
         // use; each accumulator still sums the thread's nodes in index order
-        // (a missing second node adds an exact zero)
+        // (a missing second node adds an exact zero). In the thread's first
+        // round the first product into each accumulator initialises it
+        // (the same bits as adding it to zero, without the two-sum).
+        bool first = true;
         for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N; p += 2 * step) {
             const size_t p2 = p + step;
             const bool two = p2 < N;
@@ -125,9 +138,14 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
                 if (i0 + q < nvec) {
                     // conj(v) x: re = vr xr + vi xi, im = vr xi - vi xr
                     const float4 v = va[q];
-                    ds_fma(h[2 * q], l[2 * q], v.x, v.y, x0.x, x0.y);
+                    if (first) {
+                        ds_init(h[2 * q], l[2 * q], v.x, v.y, x0.x, x0.y);
+                        ds_init(h[2 * q + 1], l[2 * q + 1], v.x, v.y, x0.z, x0.w);
+                    } else {
+                        ds_fma(h[2 * q], l[2 * q], v.x, v.y, x0.x, x0.y);
+                        ds_fma(h[2 * q + 1], l[2 * q + 1], v.x, v.y, x0.z, x0.w);
+                    }
                     ds_fma(h[2 * q], l[2 * q], v.z, v.w, x0.z, x0.w);
-                    ds_fma(h[2 * q + 1], l[2 * q + 1], v.x, v.y, x0.z, x0.w);
                     ds_fma(h[2 * q + 1], l[2 * q + 1], -v.z, -v.w, x0.x, x0.y);
                     const float4 u = vb[q];
                     ds_fma(h[2 * q], l[2 * q], u.x, u.y, x1.x, x1.y);
@@ -136,6 +154,7 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
                     ds_fma(h[2 * q + 1], l[2 * q + 1], -u.z, -u.w, x1.x, x1.y);
                 }
             }
+            first = false;
         }
         float oh, ol;
         warp_reduce16_ds(h, l, oh, ol);
