@@ -348,7 +348,9 @@ helm_status helm_profile_stop(char *json, size_t cap);
 /* Times one kernel of the Arnoldi step j with the data of the grid's last
  * solve: `reps` back-to-back launches are captured in a CUDA graph, replayed
  * once to warm up and once between two CUDA events on the grid's stream.
- * kernel: "multidot", "multiaxpy", "stencil_apply" (H z_j) or "vcycle"
+ * kernel: "multidot", "multiaxpy", "stencil_apply" (H z_j), "multidot_h" (H z_j
+ * fused with the multi-dot, the kernel the complex128-basis forms run),
+ * "vcycle_gemm" (the coarse-level product of one V-cycle) or "vcycle"
  * (M^-1 v_j, all its kernels). Outputs: average microseconds per launch, and
  * the launch's algorithmic bytes and FP64 flops (0 for "vcycle"); bytes and
  * flops64 are nullable. The basis and Hessenberg scratch of the last solve

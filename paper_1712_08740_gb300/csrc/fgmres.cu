@@ -184,10 +184,13 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
     double *nrm = g->nrm.as<double>();
     const int *act = g->act_it.as<int>();
     if (g->opt.precond != HELM_PRECOND_NONE) apply_precond_j(g, j, nrhs, act);
-    apply_H_j(g, j, nrhs, act);
     double2 *w = V + (size_t)(j + 1) * N;
     const int nvec = j + 1;
     const int mode = g->opt.reorth;      // 0: CGS once, 1: CGS twice, 2: twice only when needed
+    // complex128 basis with a plain first Gram-Schmidt pass: H z_j is formed
+    // inside that pass (k_multidot_h); otherwise by its own kernel
+    const bool fuse_h = g->opt.precision != HELM_PREC_MIXED_DS && mode != 2;
+    if (!fuse_h) apply_H_j(g, j, nrhs, act);
     if (g->opt.precision == HELM_PREC_MIXED_DS) {
         float4 *Vd = g->V.as<float4>();
         float4 *wd = Vd + (size_t)(j + 1) * N;
@@ -220,7 +223,16 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
         launch_multidot(V, sV, nvec, w, sV, N, hb + nv, 2 * nv, nrhs, act2, ks, st);
         launch_multiaxpy(V, sV, nvec, hb + nv, 2 * nv, w, sV, N, nrm, nrhs, act2, ks, st);
     } else {
-        launch_multidot(V, sV, nvec, w, sV, N, hb, 2 * nv, nrhs, act, ks, st);
+        const LevelView<double> L0 = level_view<double>(g, 0);
+        if (g->opt.precond == HELM_PRECOND_NONE)
+            launch_multidot_h<double2>(V, sV, nvec, w, sV, N, hb, 2 * nv, nrhs, act, ks, L0, shift_H(g),
+                                       V + (size_t)j * N, sV, st);
+        else if (g->opt.precision == HELM_PREC_F64)
+            launch_multidot_h<double2>(V, sV, nvec, w, sV, N, hb, 2 * nv, nrhs, act, ks, L0, shift_H(g),
+                                       g->Z.as<double2>() + (size_t)j * N, (size_t)m * N, st);
+        else
+            launch_multidot_h<float2>(V, sV, nvec, w, sV, N, hb, 2 * nv, nrhs, act, ks, L0, shift_H(g),
+                                      g->Z.as<float2>() + (size_t)j * N, (size_t)m * N, st);
         launch_multiaxpy(V, sV, nvec, hb, 2 * nv, w, sV, N, mode ? nullptr : nrm, nrhs, act, ks, st);
         if (mode) {
             launch_multidot(V, sV, nvec, w, sV, N, hb + nv, 2 * nv, nrhs, act, ks, st);
@@ -624,6 +636,40 @@ extern "C" helm_status helm_time_kernel(helm_grid *g, const char *kernel, int j,
                                 nullptr, ks, g->st);
             b = (nvec + 2.0) * N * 16.0 * nrhs;
             fl = 4.0 * N * nrhs;
+        } else if (name == "multidot_h" && !dsb) {
+            // H z_j fused with the multi-dot against V_0..V_j (the solve's kernel)
+            const LevelView<double> L0 = level_view<double>(g, 0);
+            double zb = 16.0;
+            if (g->opt.precond == HELM_PRECOND_NONE)
+                launch_multidot_h<double2>(V, sV, nvec, V + (size_t)(j + 1) * N, sV, N, hb, 2 * nv, nrhs,
+                                           nullptr, ks, L0, shift_H(g), V + (size_t)j * N, sV, g->st);
+            else if (g->opt.precision == HELM_PREC_F64)
+                launch_multidot_h<double2>(V, sV, nvec, V + (size_t)(j + 1) * N, sV, N, hb, 2 * nv, nrhs,
+                                           nullptr, ks, L0, shift_H(g), g->Z.as<double2>() + (size_t)j * N,
+                                           (size_t)m * N, g->st);
+            else {
+                launch_multidot_h<float2>(V, sV, nvec, V + (size_t)(j + 1) * N, sV, N, hb, 2 * nv, nrhs,
+                                          nullptr, ks, L0, shift_H(g), g->Z.as<float2>() + (size_t)j * N,
+                                          (size_t)m * N, g->st);
+                zb = 8.0;
+            }
+            b = ((nvec + 1.0) * 16.0 + zb + 8.0) * N * nrhs;
+            fl = (8.0 * nvec + 4.0 * g->dim + 12.0) * N * nrhs;
+        } else if (name == "vcycle_gemm") {
+            // the coarse product of one V-cycle, on the coarsest level's buffers
+            if (g->opt.precond == HELM_PRECOND_NONE || g->nc == 0) return false;
+            const MGLevel &Lc = g->lv.back();
+            if (g->vc_prec == HELM_PREC_F64)
+                launch_dense_gemv<double>((const double2 *)g->Ainv.p, g->nc, Lc.b.as<double2>(), Lc.N,
+                                          Lc.r.as<double2>(), Lc.N, nrhs, nullptr, g->cpart.p,
+                                          g->cticket.as<unsigned>(), g->st);
+            else
+                launch_dense_gemv<float>((const float2 *)g->Ainv.p, g->nc, Lc.b.as<float2>(), Lc.N,
+                                         Lc.r.as<float2>(), Lc.N, nrhs, nullptr, g->cpart.p,
+                                         g->cticket.as<unsigned>(), g->st);
+            const double cs = g->vc_prec == HELM_PREC_F64 ? 16.0 : 8.0;
+            b = ((double)g->nc * g->nc + 2.0 * g->nc * nrhs) * cs;
+            fl = g->vc_prec == HELM_PREC_F64 ? 8.0 * g->nc * (double)g->nc * nrhs : 0.0;
         } else if (name == "multidot") {
             launch_multidot(V, sV, nvec, V + (size_t)(j + 1) * N, sV, N, hb, 2 * nv, nrhs, nullptr, ks, g->st);
             b = (nvec + 1.0) * N * 16.0 * nrhs;

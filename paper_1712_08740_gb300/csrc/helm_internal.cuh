@@ -262,6 +262,12 @@ void launch_multidot(const double2 *V, size_t sV, int nvec, const double2 *w, si
                      size_t N, double2 *out, size_t out_stride, int nrhs, const int *active,
                      KrylovScratch &ks, cudaStream_t st);
 // w[p] -= sum_i V_i[p] c[k * c_stride + i]; if norm2 != null, norm2[k] = ||w_new||^2
+// w = H z (basis slot j+1) fused with the multi-dot of w against V_0..V_{nvec-1}
+template <typename CZ>
+void launch_multidot_h(const double2 *V, size_t sV, int nvec, double2 *w, size_t sw, size_t N,
+                       double2 *out, size_t out_stride, int nrhs, const int *active,
+                       KrylovScratch &ks, const LevelView<double> &L, OpShift<double> sH,
+                       const CZ *z, size_t sz, cudaStream_t st);
 void launch_multiaxpy(const double2 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
                       double2 *w, size_t sw, size_t N, double *norm2, int nrhs,
                       const int *active, KrylovScratch &ks, cudaStream_t st);

@@ -132,6 +132,130 @@ k_multidot(const double2 *__restrict__ V, size_t sV, int nvec, const double2 *__
     }
 }
 
+// (H z)_p of Eq. 2-3 at one node (the same formulas as k_stencil's APPLY
+// mode): d_p z_p - (1/h^2) sum_nbr c z_nbr, c = 2 at a mirrored boundary
+// neighbour, d_p with the absorbing boundary term at boundary nodes.
+template <int DIM, typename CZ>
+__device__ __forceinline__ double2 h_at(const LevelView<double> &L, const OpShift<double> &s,
+                                        const CZ *__restrict__ z, size_t p) {
+    const unsigned nx = (unsigned)L.nx, ny = (unsigned)L.ny, nz = (unsigned)L.nz;
+    const unsigned up = (unsigned)p;
+    const unsigned ix = up % nx, row = up / nx;
+    const unsigned iy = DIM == 3 ? row % ny : row, iz = DIM == 3 ? row / ny : 0;
+    double sre = 0.0, sim = 0.0;
+    int nf = 0;
+    auto axis = [&](unsigned i, unsigned n, size_t stride) {
+        if (i > 0) {
+            const double2 v = cvt<double2>(z[p - stride]);
+            const double c = (i == n - 1) ? 2.0 : 1.0;
+            sre += c * v.x;
+            sim += c * v.y;
+        } else {
+            ++nf;
+        }
+        if (i < n - 1) {
+            const double2 v = cvt<double2>(z[p + stride]);
+            const double c = (i == 0) ? 2.0 : 1.0;
+            sre += c * v.x;
+            sim += c * v.y;
+        } else {
+            ++nf;
+        }
+    };
+    axis(ix, nx, 1);
+    if (DIM >= 2) axis(iy, ny, (size_t)nx);
+    if (DIM == 3) axis(iz, nz, (size_t)nx * ny);
+    const double wp = L.w[p];
+    double dre = 2.0 * DIM * L.inv_h2 - s.s_re * wp;
+    double dim_ = -s.s_im * wp;
+    if (nf) {
+        const double f = nf * L.two_over_h * sqrt(wp);
+        dre -= f * s.q_im;
+        dim_ += f * s.q_re;
+    }
+    const double2 zp = cvt<double2>(z[p]);
+    return make_double2(dre * zp.x - dim_ * zp.y - L.inv_h2 * sre,
+                        dre * zp.y + dim_ * zp.x - L.inv_h2 * sim);
+}
+
+// w = H z_j (written into basis slot j+1) fused with the multi-dot
+// out[i] = sum_p conj(V_i[p]) w[p], i < nvec: the first group of basis vectors
+// forms w at each node from z and stores it, later groups read it back (the
+// thread's own writes). Saves the separate H z launch and one pass over w.
+template <int DIM, typename CZ>
+__global__ void __launch_bounds__(kThreads)
+k_multidot_h(const double2 *__restrict__ V, size_t sV, int nvec, double2 *__restrict__ w,
+             size_t sw, size_t N, double2 *__restrict__ out, size_t ostride,
+             double2 *__restrict__ partial, unsigned *__restrict__ counter, int nvec_max,
+             const int *__restrict__ active, LevelView<double> L, OpShift<double> sH,
+             const CZ *__restrict__ z, size_t sz) {
+    const int r = blockIdx.y;
+    if (active && !active[r]) return;
+    V += r * sV;
+    w += r * sw;
+    z += r * sz;
+    double2 *part = partial + (size_t)r * nvec_max * gridDim.x + blockIdx.x;
+    __shared__ double2 red[kWarps][kMaxVec];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t step = (size_t)gridDim.x * kThreads;
+    for (int i0 = 0; i0 < nvec; i0 += kGroup) {
+        double are[kGroup], aim[kGroup];
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) are[q] = aim[q] = 0.0;
+        for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N; p += step) {
+            double2 x;
+            if (i0 == 0) {
+                x = h_at<DIM>(L, sH, z, p);
+                w[p] = x;
+            } else {
+                x = w[p];
+            }
+#pragma unroll
+            for (int q = 0; q < kGroup; ++q) {
+                if (i0 + q < nvec) {
+                    const double2 v = V[(size_t)(i0 + q) * N + p];
+                    are[q] = fma(v.x, x.x, are[q]);
+                    are[q] = fma(v.y, x.y, are[q]);
+                    aim[q] = fma(v.x, x.y, aim[q]);
+                    aim[q] = fma(-v.y, x.x, aim[q]);
+                }
+            }
+        }
+        double v[16];
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) {
+            v[2 * q] = are[q];
+            v[2 * q + 1] = aim[q];
+        }
+        const double tot = warp_reduce16(v);
+        const int comp = (lane >> 1) & 15;
+        if ((lane & 1) == 0 && i0 + (comp >> 1) < nvec) {
+            double *dst = reinterpret_cast<double *>(&red[warp][i0 + (comp >> 1)]);
+            dst[comp & 1] = tot;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nvec; i += kThreads) {
+        double2 s = red[0][i];
+        for (int q = 1; q < kWarps; ++q) {
+            s.x += red[q][i].x;
+            s.y += red[q][i].y;
+        }
+        part[(size_t)i * gridDim.x] = s;
+    }
+    if (last_block(counter + r)) {
+        const double2 *pr = partial + (size_t)r * nvec_max * gridDim.x;
+        for (int i = warp; i < nvec; i += kWarps) {
+            double sx, sy;
+            lane_sum(pr + (size_t)i * gridDim.x, gridDim.x, lane, sx, sy);
+            sx = warp_sum(sx);
+            sy = warp_sum(sy);
+            if (lane == 0) out[r * ostride + i] = make_double2(sx, sy);
+        }
+        if (threadIdx.x == 0) counter[r] = 0;
+    }
+}
+
 // Block-sum of one double into a partial, then the last block finishes norm2[r].
 __device__ void reduce_norm(double v, double *partial_d, unsigned *counter, double *norm2, int r) {
     __shared__ double red[kWarps];
@@ -335,6 +459,37 @@ void launch_multidot(const double2 *V, size_t sV, int nvec, const double2 *w, si
     if (prof_on())
         prof_end("multidot_f64", st, (nvec + 1.0) * N * 16.0 * nrhs, 8.0 * nvec * N * nrhs);
 }
+
+template <typename CZ>
+void launch_multidot_h(const double2 *V, size_t sV, int nvec, double2 *w, size_t sw, size_t N,
+                       double2 *out, size_t out_stride, int nrhs, const int *active,
+                       KrylovScratch &ks, const LevelView<double> &L, OpShift<double> sH,
+                       const CZ *z, size_t sz, cudaStream_t st) {
+    const int nb = sm_blocks_for(N, 2, ks.max_blocks);
+    prof_begin(st);
+    const dim3 g(nb, nrhs);
+    if (L.dim == 1)
+        k_multidot_h<1, CZ><<<g, kThreads, 0, st>>>(V, sV, nvec, w, sw, N, out, out_stride, ks.partial,
+                                                    ks.counter, ks.nvec_max, active, L, sH, z, sz);
+    else if (L.dim == 2)
+        k_multidot_h<2, CZ><<<g, kThreads, 0, st>>>(V, sV, nvec, w, sw, N, out, out_stride, ks.partial,
+                                                    ks.counter, ks.nvec_max, active, L, sH, z, sz);
+    else
+        k_multidot_h<3, CZ><<<g, kThreads, 0, st>>>(V, sV, nvec, w, sw, N, out, out_stride, ks.partial,
+                                                    ks.counter, ks.nvec_max, active, L, sH, z, sz);
+    count_launch();
+    if (prof_on())
+        prof_end("multidot_h_f64", st, ((nvec + 1.0) * 16.0 + sizeof(CZ) + 8.0) * N * nrhs,
+                 (8.0 * nvec + 4.0 * L.dim + 12.0) * N * nrhs);
+}
+template void launch_multidot_h<double2>(const double2 *, size_t, int, double2 *, size_t, size_t,
+                                         double2 *, size_t, int, const int *, KrylovScratch &,
+                                         const LevelView<double> &, OpShift<double>,
+                                         const double2 *, size_t, cudaStream_t);
+template void launch_multidot_h<float2>(const double2 *, size_t, int, double2 *, size_t, size_t,
+                                        double2 *, size_t, int, const int *, KrylovScratch &,
+                                        const LevelView<double> &, OpShift<double>,
+                                        const float2 *, size_t, cudaStream_t);
 
 void launch_multiaxpy(const double2 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
                       double2 *w, size_t sw, size_t N, double *norm2, int nrhs,
