@@ -193,6 +193,31 @@ def test_solve_2d_smooth_401x201(helm, precision):
     assert its < 200
 
 
+def test_paper_literal_shift_variant(helm):
+    """The paper writes its preconditioner as -Lap + beta k^2 with beta = (1, 1); in the
+    build's convention M = -Lap - (b1 - j b2) w^2 m^2 that is (b1, b2) = (-1, 1). Run as a
+    variant, it is still a valid right preconditioner: the solve converges to the LU answer,
+    but (its spectrum lying off the disc |lambda - 1/2| <= 1/2) it needs more iterations than
+    the build's (1, 0.5)."""
+    w = workload("2d_smooth_small")
+    m = w.slowness()
+    f = w.rhs()
+    out = {}
+    for shift in ((1.0, 0.5), (-1.0, 1.0)):
+        g = helm.Grid(w.n, w.h, restart=30)
+        g.set_model(dev(m), w.omega(), w.alpha)
+        g.set_shift(*shift)
+        fd = dev(f)
+        ud = torch.empty_like(fd)
+        _, its, rr = g.solve(fd, 1e-8, ud)
+        out[shift] = (ud.cpu().numpy(), its, rr)
+        g.close()
+    u_lu = direct.lu_solve(w.n, w.h, m, w.omega(), w.alpha, f).ravel()
+    for shift, (u, its, rr) in out.items():
+        assert rr <= 1e-8 and rel(u, u_lu) <= 1e-6, shift
+    assert out[(-1.0, 1.0)][1] > out[(1.0, 0.5)][1]
+
+
 def test_solve_host_pointers_equal_device(helm):
     w = workload("2d_smooth_small")
     u1, its1, rr1, _, _ = solve_workload(helm, w, "f64")
