@@ -229,16 +229,26 @@ k_multiaxpy_ds(const float4 *__restrict__ V, size_t sV, int nvec, const double2 
     // four instructions per node on it); it is joined into a double once per
     // thread, before the deterministic block and grid reductions.
     float nh = 0.f, nl = 0.f;
-    for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N;
-         p += (size_t)gridDim.x * kThreads) {
-        const float4 x = w[p];
-        float rh = x.x, rl = x.y, ih = x.z, il = x.w;
-        // eight basis loads in flight before they are used
+    const size_t step = (size_t)gridDim.x * kThreads;
+    // two of the thread's nodes per round (p and p + step), all basis loads of
+    // a group of eight vectors issued for both before use; each node's update
+    // and the norm keep the order of a one-node loop
+    for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N; p += 2 * step) {
+        const size_t p2 = p + step;
+        const bool two = p2 < N;
+        const float4 xa = w[p];
+        const float4 xb = two ? w[p2] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float rh = xa.x, rl = xa.y, ih = xa.z, il = xa.w;
+        float sh = xb.x, sl = xb.y, jh = xb.z, jl = xb.w;
         for (int i0 = 0; i0 < nvec; i0 += kGroup) {
-            float4 v[kGroup];
+            float4 v[kGroup], u[kGroup];
 #pragma unroll
-            for (int q = 0; q < kGroup; ++q)
-                if (i0 + q < nvec) v[q] = V[(size_t)(i0 + q) * N + p];
+            for (int q = 0; q < kGroup; ++q) {
+                if (i0 + q < nvec) {
+                    v[q] = V[(size_t)(i0 + q) * N + p];
+                    if (two) u[q] = V[(size_t)(i0 + q) * N + p2];
+                }
+            }
 #pragma unroll
             for (int q = 0; q < kGroup; ++q) {
                 if (i0 + q < nvec) {
@@ -248,21 +258,31 @@ k_multiaxpy_ds(const float4 *__restrict__ V, size_t sV, int nvec, const double2 
                     ds_fma(rh, rl, -v[q].z, -v[q].w, m.z, m.w);
                     ds_fma(ih, il, v[q].x, v[q].y, m.z, m.w);
                     ds_fma(ih, il, v[q].z, v[q].w, m.x, m.y);
+                    if (two) {
+                        ds_fma(sh, sl, u[q].x, u[q].y, m.x, m.y);
+                        ds_fma(sh, sl, -u[q].z, -u[q].w, m.z, m.w);
+                        ds_fma(jh, jl, u[q].x, u[q].y, m.z, m.w);
+                        ds_fma(jh, jl, u[q].z, u[q].w, m.x, m.y);
+                    }
                 }
             }
         }
-        // renormalise (h, l) and store
-        float th = rh + rl;
-        rl = rl - (th - rh);
-        rh = th;
-        th = ih + il;
-        il = il - (th - ih);
-        ih = th;
-        w[p] = make_float4(rh, rl, ih, il);
-        if (norm2) {
-            ds_fma(nh, nl, rh, rl, rh, rl);
-            ds_fma(nh, nl, ih, il, ih, il);
-        }
+        // renormalise (h, l) and store, node p then node p2
+        auto fin = [&](size_t pp, float &ah, float &al, float &bh, float &bl) {
+            float th = ah + al;
+            al = al - (th - ah);
+            ah = th;
+            th = bh + bl;
+            bl = bl - (th - bh);
+            bh = th;
+            w[pp] = make_float4(ah, al, bh, bl);
+            if (norm2) {
+                ds_fma(nh, nl, ah, al, ah, al);
+                ds_fma(nh, nl, bh, bl, bh, bl);
+            }
+        };
+        fin(p, rh, rl, ih, il);
+        if (two) fin(p2, sh, sl, jh, jl);
     }
     if (norm2) reduce_norm(ds_join(nh, nl), partial_d, counter, norm2, r);
 }
@@ -426,7 +446,7 @@ void launch_multidot_ds(const float4 *V, size_t sV, int nvec, const float4 *w, s
 void launch_multiaxpy_ds(const float4 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
                          float4 *w, size_t sw, size_t N, double *norm2, int nrhs, const int *active,
                          KrylovScratch &ks, cudaStream_t st) {
-    const int nb = sm_blocks_for(N, 2, ks.max_blocks);
+    const int nb = sm_blocks_for(N, 4, ks.max_blocks);
     prof_begin(st);
     k_multiaxpy_ds<<<dim3(nb, nrhs), kThreads, 0, st>>>(V, sV, nvec, c, c_stride, w, sw, N, norm2,
                                                         (double *)ks.partial, ks.counter, active);
