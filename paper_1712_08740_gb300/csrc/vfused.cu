@@ -63,6 +63,9 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ int mirror(int i, int n) {
     return i < 0 ? -i : (i > n - 1 ? 2 * (n - 1) - i : i);
 }
+template <bool INT> __device__ __forceinline__ int mirror_if(int i, int n) {
+    return INT ? i : mirror(i, n);
+}
 
 template <typename C> __device__ __forceinline__ C from_d2(double2 a);
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
@@ -157,11 +160,15 @@ __device__ __forceinline__ void shell_pos(int h, int &lx, int &ly, int &lz) {
     lz = zlo + rem / NYI;
 }
 
-template <typename T, typename CB, int DIM, typename TL>
-__global__ void __launch_bounds__(TL::NT)
-k_down(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t sb,
-       cplx_t<T> *__restrict__ u, size_t su, cplx_t<T> *__restrict__ bc, size_t sbc,
-       const int *__restrict__ active) {
+// INT: the block's whole box lies strictly inside the level, so no node of it
+// needs a boundary test, a doubled neighbour or a mirrored restriction point
+// (the same arithmetic as the general body on those nodes).
+template <typename T, typename CB, int DIM, typename TL, bool INT>
+__device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
+                                          const CB *__restrict__ b, size_t sb,
+                                          cplx_t<T> *__restrict__ u, size_t su,
+                                          cplx_t<T> *__restrict__ bc, size_t sbc,
+                                          const int *__restrict__ active) {
     using C = cplx_t<T>;
     constexpr int SX = TL::SX, SY = TL::SY, SZ = DIM == 3 ? TL::SZ : 1;
     // local box of u: fine [2 I0 - 2, 2 I0 + 2 SX] per axis; own children at [2, U - 1)
@@ -190,7 +197,7 @@ k_down(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t s
     C *sb_ = su_ + UX * UY * UZ;
     C *sr_ = sb_ + UX * UY * UZ;
     auto in_f = [&](int x, int y, int z) {
-        return x >= 0 && x < F.nx && y >= 0 && y < F.ny && (DIM != 3 || (z >= 0 && z < F.nz));
+        return INT || (x >= 0 && x < F.nx && y >= 0 && y < F.ny && (DIM != 3 || (z >= 0 && z < F.nz)));
     };
     // loads first: own children, then this thread's share of the halo shell
     CB bq[NQL], bh[HP];
@@ -255,13 +262,13 @@ k_down(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t s
         const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
         const int q = (lz * UY + ly) * UX + lx;
         T sx = 0, sy = 0;
-        if (x > 0) { const T c = (x == F.nx - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - 1].x, sx); sy = fmaT(c, su_[q - 1].y, sy); }
-        if (x < F.nx - 1) { const T c = (x == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + 1].x, sx); sy = fmaT(c, su_[q + 1].y, sy); }
-        if (y > 0) { const T c = (y == F.ny - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - UX].x, sx); sy = fmaT(c, su_[q - UX].y, sy); }
-        if (y < F.ny - 1) { const T c = (y == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + UX].x, sx); sy = fmaT(c, su_[q + UX].y, sy); }
+        if (INT || x > 0) { const T c = (!INT && x == F.nx - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - 1].x, sx); sy = fmaT(c, su_[q - 1].y, sy); }
+        if (INT || x < F.nx - 1) { const T c = (!INT && x == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + 1].x, sx); sy = fmaT(c, su_[q + 1].y, sy); }
+        if (INT || y > 0) { const T c = (!INT && y == F.ny - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - UX].x, sx); sy = fmaT(c, su_[q - UX].y, sy); }
+        if (INT || y < F.ny - 1) { const T c = (!INT && y == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + UX].x, sx); sy = fmaT(c, su_[q + UX].y, sy); }
         if (DIM == 3) {
-            if (z > 0) { const T c = (z == F.nz - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - UX * UY].x, sx); sy = fmaT(c, su_[q - UX * UY].y, sy); }
-            if (z < F.nz - 1) { const T c = (z == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + UX * UY].x, sx); sy = fmaT(c, su_[q + UX * UY].y, sy); }
+            if (INT || z > 0) { const T c = (!INT && z == F.nz - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - UX * UY].x, sx); sy = fmaT(c, su_[q - UX * UY].y, sy); }
+            if (INT || z < F.nz - 1) { const T c = (!INT && z == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + UX * UY].x, sx); sy = fmaT(c, su_[q + UX * UY].y, sy); }
         }
         const C bp = sb_[q];
         const T omw = T(1) - wj;
@@ -295,15 +302,15 @@ k_down(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t s
     T ax = 0, ay = 0;
 #pragma unroll
     for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz) {
-        const int lz = DIM == 3 ? mirror(2 * K + oz, F.nz) - Z0 : 0;
+        const int lz = DIM == 3 ? mirror_if<INT>(2 * K + oz, F.nz) - Z0 : 0;
         const T wz = DIM == 3 ? (oz == 0 ? T(0.5) : T(0.25)) : T(1);
 #pragma unroll
         for (int oy = -1; oy <= 1; ++oy) {
-            const int ly = mirror(2 * J + oy, F.ny) - Y0;
+            const int ly = mirror_if<INT>(2 * J + oy, F.ny) - Y0;
             const T wy = oy == 0 ? T(0.5) : T(0.25);
 #pragma unroll
             for (int ox = -1; ox <= 1; ++ox) {
-                const int lx = mirror(2 * I + ox, F.nx) - X0;
+                const int lx = mirror_if<INT>(2 * I + ox, F.nx) - X0;
                 const T wgt = (ox == 0 ? T(0.5) : T(0.25)) * wy * wz;
                 const C v = sr_[(lz * UY + ly) * UX + lx];
                 ax = fmaT(wgt, v.x, ax);
@@ -317,11 +324,13 @@ k_down(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t s
     bc[(size_t)K * Cv.nx * Cv.ny + (size_t)J * Cv.nx + I] = o;
 }
 
-template <typename T, typename CB, int DIM, typename TL>
-__global__ void __launch_bounds__(TL::NT)
-k_up(LevelView<T> F, LevelView<T> Cv, T wj, const cplx_t<T> *__restrict__ uin,
-     size_t sin, const cplx_t<T> *__restrict__ ec, size_t sec, const CB *__restrict__ b, size_t sb,
-     cplx_t<T> *__restrict__ uout, size_t sout, const int *__restrict__ active) {
+template <typename T, typename CB, int DIM, typename TL, bool INT>
+__device__ __forceinline__ void up_tile(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
+                                        const cplx_t<T> *__restrict__ uin, size_t sin,
+                                        const cplx_t<T> *__restrict__ ec, size_t sec,
+                                        const CB *__restrict__ b, size_t sb,
+                                        cplx_t<T> *__restrict__ uout, size_t sout,
+                                        const int *__restrict__ active) {
     using C = cplx_t<T>;
     constexpr int SX = TL::SX, SY = TL::SY, SZ = DIM == 3 ? TL::SZ : 1;
     // local box of v: fine [2 I0 - 1, 2 I0 + 2 SX] per axis; own children at [1, V - 1)
@@ -351,7 +360,7 @@ k_up(LevelView<T> F, LevelView<T> Cv, T wj, const cplx_t<T> *__restrict__ uin,
     C *sv_ = reinterpret_cast<C *>(smem_raw);
     C *se_ = sv_ + VX * VY * VZ;
     auto in_f = [&](int x, int y, int z) {
-        return x >= 0 && x < F.nx && y >= 0 && y < F.ny && (DIM != 3 || (z >= 0 && z < F.nz));
+        return INT || (x >= 0 && x < F.nx && y >= 0 && y < F.ny && (DIM != 3 || (z >= 0 && z < F.nz)));
     };
     // loads first: coarse correction tile, own children (u, b, D^-1), halo u
     C eq[EP], uq[NQL], dq[NQL], uh[HP];
@@ -450,13 +459,13 @@ k_up(LevelView<T> F, LevelView<T> Cv, T wj, const cplx_t<T> *__restrict__ uin,
         if (!in_f(x, y, z)) continue;
         const int qq = ((z - Z0) * VY + (y - Y0)) * VX + (x - X0);
         T sx = 0, sy = 0;
-        if (x > 0) { const T c = (x == F.nx - 1) ? T(2) : T(1); sx = fmaT(c, sv_[qq - 1].x, sx); sy = fmaT(c, sv_[qq - 1].y, sy); }
-        if (x < F.nx - 1) { const T c = (x == 0) ? T(2) : T(1); sx = fmaT(c, sv_[qq + 1].x, sx); sy = fmaT(c, sv_[qq + 1].y, sy); }
-        if (y > 0) { const T c = (y == F.ny - 1) ? T(2) : T(1); sx = fmaT(c, sv_[qq - VX].x, sx); sy = fmaT(c, sv_[qq - VX].y, sy); }
-        if (y < F.ny - 1) { const T c = (y == 0) ? T(2) : T(1); sx = fmaT(c, sv_[qq + VX].x, sx); sy = fmaT(c, sv_[qq + VX].y, sy); }
+        if (INT || x > 0) { const T c = (!INT && x == F.nx - 1) ? T(2) : T(1); sx = fmaT(c, sv_[qq - 1].x, sx); sy = fmaT(c, sv_[qq - 1].y, sy); }
+        if (INT || x < F.nx - 1) { const T c = (!INT && x == 0) ? T(2) : T(1); sx = fmaT(c, sv_[qq + 1].x, sx); sy = fmaT(c, sv_[qq + 1].y, sy); }
+        if (INT || y > 0) { const T c = (!INT && y == F.ny - 1) ? T(2) : T(1); sx = fmaT(c, sv_[qq - VX].x, sx); sy = fmaT(c, sv_[qq - VX].y, sy); }
+        if (INT || y < F.ny - 1) { const T c = (!INT && y == 0) ? T(2) : T(1); sx = fmaT(c, sv_[qq + VX].x, sx); sy = fmaT(c, sv_[qq + VX].y, sy); }
         if (DIM == 3) {
-            if (z > 0) { const T c = (z == F.nz - 1) ? T(2) : T(1); sx = fmaT(c, sv_[qq - VX * VY].x, sx); sy = fmaT(c, sv_[qq - VX * VY].y, sy); }
-            if (z < F.nz - 1) { const T c = (z == 0) ? T(2) : T(1); sx = fmaT(c, sv_[qq + VX * VY].x, sx); sy = fmaT(c, sv_[qq + VX * VY].y, sy); }
+            if (INT || z > 0) { const T c = (!INT && z == F.nz - 1) ? T(2) : T(1); sx = fmaT(c, sv_[qq - VX * VY].x, sx); sy = fmaT(c, sv_[qq - VX * VY].y, sy); }
+            if (INT || z < F.nz - 1) { const T c = (!INT && z == 0) ? T(2) : T(1); sx = fmaT(c, sv_[qq + VX * VY].x, sx); sy = fmaT(c, sv_[qq + VX * VY].y, sy); }
         }
         const C vp = sv_[qq];
         const C bp = cvt<C>(bq[k]);
@@ -468,6 +477,40 @@ k_up(LevelView<T> F, LevelView<T> Cv, T wj, const cplx_t<T> *__restrict__ uin,
         o.y = fmaT(omw, vp.y, wj * fmaT(di.x, gy, di.y * gx));
         uout[(size_t)z * fxy + (size_t)y * F.nx + x] = o;
     }
+}
+
+template <typename T, typename CB, int DIM, typename TL>
+__global__ void __launch_bounds__(TL::NT)
+k_down(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t sb,
+       cplx_t<T> *__restrict__ u, size_t su, cplx_t<T> *__restrict__ bc, size_t sbc,
+       const int *__restrict__ active) {
+    // the box of u spans fine [2 I0 - 2, 2 I0 + 2 S] per axis
+    const int gz = DIM == 3 ? (Cv.nz + TL::SZ - 1) / TL::SZ : 1;
+    const int bz = blockIdx.z % gz;
+    const int x0 = 2 * (int)blockIdx.x * TL::SX - 2, y0 = 2 * (int)blockIdx.y * TL::SY - 2,
+              z0 = 2 * bz * TL::SZ - 2;
+    const bool inside = x0 >= 0 && x0 + 2 * TL::SX + 2 <= F.nx - 1 && y0 >= 0 &&
+                        y0 + 2 * TL::SY + 2 <= F.ny - 1 &&
+                        (DIM != 3 || (z0 >= 0 && z0 + 2 * TL::SZ + 2 <= F.nz - 1));
+    if (inside) down_tile<T, CB, DIM, TL, true>(F, Cv, wj, b, sb, u, su, bc, sbc, active);
+    else down_tile<T, CB, DIM, TL, false>(F, Cv, wj, b, sb, u, su, bc, sbc, active);
+}
+
+template <typename T, typename CB, int DIM, typename TL>
+__global__ void __launch_bounds__(TL::NT)
+k_up(LevelView<T> F, LevelView<T> Cv, T wj, const cplx_t<T> *__restrict__ uin,
+     size_t sin, const cplx_t<T> *__restrict__ ec, size_t sec, const CB *__restrict__ b, size_t sb,
+     cplx_t<T> *__restrict__ uout, size_t sout, const int *__restrict__ active) {
+    // the box of v spans fine [2 I0 - 1, 2 I0 + 2 S] per axis (coarse [I0 - 1, I0 + S])
+    const int gz = DIM == 3 ? (Cv.nz + TL::SZ - 1) / TL::SZ : 1;
+    const int bz = blockIdx.z % gz;
+    const int x0 = 2 * (int)blockIdx.x * TL::SX - 1, y0 = 2 * (int)blockIdx.y * TL::SY - 1,
+              z0 = 2 * bz * TL::SZ - 1;
+    const bool inside = x0 >= 0 && x0 + 2 * TL::SX + 1 <= F.nx - 1 && y0 >= 0 &&
+                        y0 + 2 * TL::SY + 1 <= F.ny - 1 &&
+                        (DIM != 3 || (z0 >= 0 && z0 + 2 * TL::SZ + 1 <= F.nz - 1));
+    if (inside) up_tile<T, CB, DIM, TL, true>(F, Cv, wj, uin, sin, ec, sec, b, sb, uout, sout, active);
+    else up_tile<T, CB, DIM, TL, false>(F, Cv, wj, uin, sin, ec, sec, b, sb, uout, sout, active);
 }
 
 template <int DIM, typename TL> constexpr size_t down_smem(size_t csz) {
