@@ -15,6 +15,7 @@
 // decision are no-ops for them. The host runs at most kLookahead steps ahead
 // of the device, polling a host-mapped "any right-hand side still stepping"
 // flag written by the Givens kernel, and synchronises once per cycle.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -52,8 +53,9 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
     if ((s = g->hbuf.ensure(R * 2 * nv * sizeof(double2)))) return s;
     if ((s = g->nrm.ensure(R * sizeof(double)))) return s;
     if ((s = g->yv.ensure(R * m * sizeof(double2)))) return s;
-    const int max_blocks = kMaxBlocks;
-    if ((s = g->partial.ensure(R * max_blocks * nv * sizeof(double2)))) return s;
+    size_t per_rhs = (size_t)kMaxBlocks * nv;
+    if (prec == HELM_PREC_MIXED_DS) per_rhs = std::max(per_rhs, ds_partial_per_rhs(N, nv));
+    if ((s = g->partial.ensure(R * per_rhs * sizeof(double2)))) return s;
     if ((s = g->counter.ensure(R * sizeof(unsigned)))) return s;
     cudaMemsetAsync(g->counter.p, 0, R * sizeof(unsigned), g->st);
     if ((s = g->act_it.ensure(R * sizeof(int))) || (s = g->act_cy.ensure(R * sizeof(int))) ||

@@ -294,6 +294,9 @@ void launch_reorth_flags(const int *act, const double2 *h1, double2 *h2, int hst
 // ---- double-single basis (precision HELM_PREC_MIXED_DS): the same operations on
 // a basis stored as float4 (re_hi, re_lo, im_hi, im_lo), computed with FP32
 // error-free products and two-sums; results and coefficients stay complex128.
+// double2 elements of KrylovScratch::partial that the double-single multi-dot
+// and multi-axpy need per right-hand side (nvec_max = restart + 1)
+size_t ds_partial_per_rhs(size_t N, int nvec_max);
 void launch_multidot_ds(const float4 *V, size_t sV, int nvec, const float4 *w, size_t sw, size_t N,
                         double2 *out, size_t out_stride, int nrhs, const int *active,
                         KrylovScratch &ks, cudaStream_t st);

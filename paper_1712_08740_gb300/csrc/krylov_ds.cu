@@ -15,13 +15,13 @@
 // into doubles before the block and grid reductions, which are the same
 // deterministic two-level reductions as in krylov.cu.
 #include "helm_internal.cuh"
+#include "pipe.cuh"
 
 namespace helm {
 
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
 constexpr int kMaxVec = 257;
 constexpr int kGroup = 8;
 
@@ -84,207 +84,329 @@ __device__ __forceinline__ void warp_reduce16_ds(float h[16], float l[16], float
     ds_add(oh, ol, __shfl_xor_sync(0xffffffffu, h[0], 1), __shfl_xor_sync(0xffffffffu, l[0], 1));
 }
 
-__device__ bool last_block(unsigned *counter) {
-    __shared__ bool is_last;
-    __threadfence();
-    __syncthreads();
+
+// ---------------------------------------------------------------- streamed Arnoldi kernels
+// The multi-dot and multi-axpy read every basis vector V_0..V_{n-1} of every
+// right-hand side once per call: about 1.3 GB for a 64-source batch of the
+// 401 x 201 grid at n = 16. Both run as persistent blocks of 8 consumer warps
+// and one producer warp. One lane of the producer streams tiles of the
+// vectors through a ring of shared-memory stages with cp.async.bulk, each
+// stage completing on its "full" mbarrier; the consumer warps release a stage
+// with one arrive each on its "empty" mbarrier. The consumer warps never
+// synchronise with one another: every warp writes its own partial results,
+// and a small finalize kernel adds them in a fixed order. All sums thus have
+// an order fixed by N alone (the same for a batch as for one right-hand side).
+constexpr int kCons = 256;                  // consumer threads (8 warps)
+constexpr int kConsWarps = kCons / 32;
+constexpr int kPipeThreads = kCons + 32;    // + the producer warp
+
+// multi-dot: a stage is one tile of kDotTile nodes of w and of up to kGroup
+// vectors (9 x 4 KB); the accumulators of a group run over a chunk of
+// kDotTpi consecutive tiles (4 nodes per thread) before the warp reduction.
+constexpr int kDotTile = 256;
+constexpr int kDotStages = 3;
+constexpr int kDotTpi = 4;
+constexpr int kDotBlocksPerSM = 2;
+
+struct DotSmem {
+    float4 slot[kDotStages][kGroup + 1][kDotTile];
+    uint64_t full[kDotStages], empty[kDotStages];
+    int abort;
+};
+
+// multi-axpy: a stage is one tile of kAxpyTile nodes (16 KB) of w or of one
+// vector; 4 nodes per consumer thread.
+constexpr int kAxpyTile = 1024;
+constexpr int kAxpyStages = 6;
+constexpr int kAxpyBlocksPerSM = 2;
+
+struct alignas(16) AxpySmem {
+    float4 slot[kAxpyStages][kAxpyTile];
+    uint64_t full[kAxpyStages], empty[kAxpyStages];
+    int abort;
+    // followed by float4 cs[kConsWarps][nvec]: each warp's copy of -c split
+};
+
+__host__ __device__ constexpr int ceil_div(size_t a, size_t b) { return (int)((a + b - 1) / b); }
+
+template <int S> __device__ __forceinline__ void ring_init(uint64_t (&full)[S], uint64_t (&empty)[S], int &abort) {
     if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(counter, 1u);
-        is_last = (t == gridDim.x - 1);
+        for (int s = 0; s < S; ++s) {
+            pipe::mbar_init(&full[s], 1);
+            pipe::mbar_init(&empty[s], kConsWarps);
+        }
+        abort = 0;
+        pipe::mbar_init_fence();
     }
     __syncthreads();
-    if (is_last) __threadfence();
-    return is_last;
 }
 
-__global__ void __launch_bounds__(kThreads)
+// Producer teardown: wait (bounded) for the copies of the last stages issued
+// (the stages issued always form a prefix 0 .. issued - 1).
+template <int S> __device__ __forceinline__ void ring_drain(uint64_t (&full)[S], unsigned issued) {
+    const unsigned k0 = issued > (unsigned)S ? issued - S : 0u;
+    for (unsigned k = k0; k < issued; ++k)
+        if (!pipe::mbar_wait_drain(&full[k % S], (k / S) & 1u)) return;
+}
+
+__device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ll); }
+
+// partial[((r * nvec_max + i) * nch + c) * 8 + warp] = warp's part of
+// sum_p conj(V_i[p]) w[p] over chunk c of right-hand side r
+__global__ void __launch_bounds__(kPipeThreads, kDotBlocksPerSM)
 k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *__restrict__ w,
-              size_t sw, size_t N, double2 *__restrict__ out, size_t ostride,
-              double2 *__restrict__ partial, unsigned *__restrict__ counter, int nvec_max,
+              size_t sw, size_t N, double2 *__restrict__ partial, int nvec_max, int nrhs,
               const int *__restrict__ active) {
-    const int r = blockIdx.y;
-    if (active && !active[r]) return;
-    V += r * sV;
-    w += r * sw;
-    double2 *part = partial + (size_t)r * nvec_max * gridDim.x + blockIdx.x;
-    __shared__ double2 red[kWarps][kMaxVec];
+    extern __shared__ __align__(128) unsigned char pipe_raw[];
+    DotSmem &S = *reinterpret_cast<DotSmem *>(pipe_raw);
+    ring_init(S.full, S.empty, S.abort);
+    const int ntiles = ceil_div(N, kDotTile), nch = ceil_div(ntiles, kDotTpi);
+    const int items = nrhs * nch;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t step = (size_t)gridDim.x * kThreads;
-    for (int i0 = 0; i0 < nvec; i0 += kGroup) {
-        float h[16], l[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) h[q] = l[q] = 0.f;
-        // two of the thread's nodes per round, all their loads issued before
-        // use; each accumulator still sums the thread's nodes in index order
-        // (a missing second node adds an exact zero). In the thread's first
-        // round the first product into each accumulator initialises it
-        // (the same bits as adding it to zero, without the two-sum).
-        bool first = true;
-        for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N; p += 2 * step) {
-            const size_t p2 = p + step;
-            const bool two = p2 < N;
-            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 x0 = w[p], x1 = two ? w[p2] : zero;
-            float4 va[kGroup], vb[kGroup];
-#pragma unroll
-            for (int q = 0; q < kGroup; ++q) {
-                if (i0 + q < nvec) {
-                    va[q] = V[(size_t)(i0 + q) * N + p];
-                    vb[q] = two ? V[(size_t)(i0 + q) * N + p2] : zero;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kGroup; ++q) {
-                if (i0 + q < nvec) {
-                    // conj(v) x: re = vr xr + vi xi, im = vr xi - vi xr
-                    const float4 v = va[q];
-                    if (first) {
-                        ds_init(h[2 * q], l[2 * q], v.x, v.y, x0.x, x0.y);
-                        ds_init(h[2 * q + 1], l[2 * q + 1], v.x, v.y, x0.z, x0.w);
-                    } else {
-                        ds_fma(h[2 * q], l[2 * q], v.x, v.y, x0.x, x0.y);
-                        ds_fma(h[2 * q + 1], l[2 * q + 1], v.x, v.y, x0.z, x0.w);
+    unsigned k = 0;
+    if (warp == kConsWarps) {
+        // producer: per item (r, c), per group, per tile: one stage
+        if (lane == 0) {
+            unsigned issued = 0;
+            for (int it = blockIdx.x; it < items; it += gridDim.x) {
+                const int r = it / nch, c = it % nch;
+                if (active && !active[r]) continue;
+                const int t0 = c * kDotTpi, t1 = min(t0 + kDotTpi, ntiles);
+                const float4 *Vr = V + r * sV, *wr = w + r * sw;
+                for (int i0 = 0; i0 < nvec; i0 += kGroup) {
+                    const int nq = min(kGroup, nvec - i0);
+                    for (int tl = t0; tl < t1; ++tl, ++k) {
+                        const size_t p0 = (size_t)tl * kDotTile;
+                        const unsigned bytes = (unsigned)min((size_t)kDotTile, N - p0) * 16u;
+                        const int s = (int)(k % kDotStages);
+                        if (!pipe::mbar_wait(&S.empty[s], ((k / kDotStages) & 1u) ^ 1u, &S.abort)) continue;
+                        pipe::mbar_arrive_expect_tx(&S.full[s], bytes * (nq + 1));
+                        pipe::bulk_load(&S.slot[s][0][0], wr + p0, bytes, &S.full[s]);
+                        for (int q = 0; q < nq; ++q)
+                            pipe::bulk_load(&S.slot[s][1 + q][0], Vr + (size_t)(i0 + q) * N + p0, bytes, &S.full[s]);
+                        issued = k + 1;
                     }
-                    ds_fma(h[2 * q], l[2 * q], v.z, v.w, x0.z, x0.w);
-                    ds_fma(h[2 * q + 1], l[2 * q + 1], -v.z, -v.w, x0.x, x0.y);
-                    const float4 u = vb[q];
-                    ds_fma(h[2 * q], l[2 * q], u.x, u.y, x1.x, x1.y);
-                    ds_fma(h[2 * q], l[2 * q], u.z, u.w, x1.z, x1.w);
-                    ds_fma(h[2 * q + 1], l[2 * q + 1], u.x, u.y, x1.z, x1.w);
-                    ds_fma(h[2 * q + 1], l[2 * q + 1], -u.z, -u.w, x1.x, x1.y);
                 }
             }
-            first = false;
+            ring_drain(S.full, issued);
         }
-        float oh, ol;
-        warp_reduce16_ds(h, l, oh, ol);
-        const int comp = (lane >> 1) & 15;
-        if ((lane & 1) == 0 && i0 + (comp >> 1) < nvec) {
-            double *dst = reinterpret_cast<double *>(&red[warp][i0 + (comp >> 1)]);
-            dst[comp & 1] = ds_join(oh, ol);
+        __syncwarp();
+        __syncthreads();
+        return;
+    }
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int t = threadIdx.x;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int r = it / nch, c = it % nch;
+        if (active && !active[r]) continue;
+        const int t0 = c * kDotTpi, t1 = min(t0 + kDotTpi, ntiles);
+        for (int i0 = 0; i0 < nvec; i0 += kGroup) {
+            const int nq = min(kGroup, nvec - i0);
+            float h[16], l[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) h[q] = l[q] = 0.f;
+            // each accumulator sums the thread's nodes of the chunk in index
+            // order; the first product into it initialises it (the same bits
+            // as adding it to zero, without the two-sum)
+            bool first = true;
+            for (int tl = t0; tl < t1; ++tl, ++k) {
+                const int nodes = (int)min((size_t)kDotTile, N - (size_t)tl * kDotTile);
+                const int s = (int)(k % kDotStages);
+                const bool ok = pipe::mbar_wait(&S.full[s], (k / kDotStages) & 1u, &S.abort);
+                const bool in = ok && t < nodes;
+                const float4 x = in ? S.slot[s][0][t] : zero;
+                float4 v[kGroup];
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) v[q] = (in && q < nq) ? S.slot[s][1 + q][t] : zero;
+                __syncwarp();
+                if (lane == 0) pipe::mbar_arrive(&S.empty[s]);
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) {
+                    if (q < nq) {
+                        // conj(v) x: re = vr xr + vi xi, im = vr xi - vi xr
+                        if (first) {
+                            ds_init(h[2 * q], l[2 * q], v[q].x, v[q].y, x.x, x.y);
+                            ds_init(h[2 * q + 1], l[2 * q + 1], v[q].x, v[q].y, x.z, x.w);
+                        } else {
+                            ds_fma(h[2 * q], l[2 * q], v[q].x, v[q].y, x.x, x.y);
+                            ds_fma(h[2 * q + 1], l[2 * q + 1], v[q].x, v[q].y, x.z, x.w);
+                        }
+                        ds_fma(h[2 * q], l[2 * q], v[q].z, v[q].w, x.z, x.w);
+                        ds_fma(h[2 * q + 1], l[2 * q + 1], -v[q].z, -v[q].w, x.x, x.y);
+                    }
+                }
+                first = false;
+            }
+            float oh, ol;
+            warp_reduce16_ds(h, l, oh, ol);
+            const int comp = (lane >> 1) & 15;
+            if ((lane & 1) == 0 && (comp >> 1) < nq) {
+                double *dst = reinterpret_cast<double *>(
+                    partial + (((size_t)r * nvec_max + i0 + (comp >> 1)) * nch + c) * kConsWarps + warp);
+                dst[comp & 1] = S.abort ? qnan() : ds_join(oh, ol);
+            }
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nvec; i += kThreads) {
-        double2 s = red[0][i];
-        for (int q = 1; q < kWarps; ++q) {
-            s.x += red[q][i].x;
-            s.y += red[q][i].y;
-        }
-        part[(size_t)i * gridDim.x] = s;
-    }
-    if (last_block(counter + r)) {
-        const double2 *pr = partial + (size_t)r * nvec_max * gridDim.x;
-        for (int i = warp; i < nvec; i += kWarps) {
-            double sx, sy;
-            lane_sum(pr + (size_t)i * gridDim.x, gridDim.x, lane, sx, sy);
-            sx = warp_sum(sx);
-            sy = warp_sum(sy);
-            if (lane == 0) out[r * ostride + i] = make_double2(sx, sy);
-        }
-        if (threadIdx.x == 0) counter[r] = 0;
-    }
 }
 
-__device__ void reduce_norm(double v, double *partial_d, unsigned *counter, double *norm2, int r) {
-    __shared__ double red[kWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    v = warp_sum(v);
-    if (lane == 0) red[warp] = v;
+// out[r * ostride + i] = sum of the n partials of (r, i), in index order per
+// thread, then warps and threads in a fixed tree
+__global__ void __launch_bounds__(256)
+k_dot_finalize(const double2 *__restrict__ partial, int nvec_max, int n, double2 *__restrict__ out,
+               size_t ostride, const int *__restrict__ active) {
+    const int i = blockIdx.x, r = blockIdx.y;
+    if (active && !active[r]) return;
+    const double2 *p = partial + ((size_t)r * nvec_max + i) * n;
+    __shared__ double2 red[8];
+    double sx = 0.0, sy = 0.0;
+    for (int t = threadIdx.x; t < n; t += 256) {
+        const double2 v = p[t];
+        sx += v.x;
+        sy += v.y;
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(sx, sy);
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < kWarps; ++q) s += red[q];
-        partial_d[(size_t)r * gridDim.x + blockIdx.x] = s;
-    }
-    if (last_block(counter + r)) {
-        if (warp == 0) {
-            double s = lane_sum(partial_d + (size_t)r * gridDim.x, gridDim.x, lane);
-            s = warp_sum(s);
-            if (lane == 0) {
-                norm2[r] = s;
-                counter[r] = 0;
-            }
+        double2 s = red[0];
+        for (int q = 1; q < 8; ++q) {
+            s.x += red[q].x;
+            s.y += red[q].y;
         }
+        out[r * ostride + i] = s;
     }
 }
 
-// w -= sum_i V_i c_i (c complex128, split once per block), optional ||w||^2
-__global__ void __launch_bounds__(kThreads)
+// w -= sum_i V_i c_i (c complex128, split into double-single by each warp per
+// item); partial_d[(r * ntiles + tile) * 8 + warp] = warp's part of ||w||^2.
+// Stages of item (r, tile): w, then V_0..V_{n-1}; the updated tile of w is
+// stored from registers.
+__global__ void __launch_bounds__(kPipeThreads, kAxpyBlocksPerSM)
 k_multiaxpy_ds(const float4 *__restrict__ V, size_t sV, int nvec, const double2 *__restrict__ c,
-               size_t cstride, float4 *__restrict__ w, size_t sw, size_t N, double *__restrict__ norm2,
-               double *__restrict__ partial_d, unsigned *__restrict__ counter,
-               const int *__restrict__ active) {
-    const int r = blockIdx.y;
-    if (active && !active[r]) return;
-    V += r * sV;
-    w += r * sw;
-    __shared__ float4 cs[kMaxVec];   // (re_hi, re_lo, im_hi, im_lo) of -c_i
-    for (int i = threadIdx.x; i < nvec; i += kThreads) {
-        const double2 ci = c[r * cstride + i];
-        cs[i] = cvt<float4>(make_double2(-ci.x, -ci.y));
-    }
-    __syncthreads();
-    // ||w||^2 accumulates in double-single as well (the FP64 pipe would spend
-    // four instructions per node on it); it is joined into a double once per
-    // thread, before the deterministic block and grid reductions.
-    float nh = 0.f, nl = 0.f;
-    const size_t step = (size_t)gridDim.x * kThreads;
-    // two of the thread's nodes per round (p and p + step), all basis loads of
-    // a group of eight vectors issued for both before use; each node's update
-    // and the norm keep the order of a one-node loop
-    for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N; p += 2 * step) {
-        const size_t p2 = p + step;
-        const bool two = p2 < N;
-        const float4 xa = w[p];
-        const float4 xb = two ? w[p2] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float rh = xa.x, rl = xa.y, ih = xa.z, il = xa.w;
-        float sh = xb.x, sl = xb.y, jh = xb.z, jl = xb.w;
-        for (int i0 = 0; i0 < nvec; i0 += kGroup) {
-            float4 v[kGroup], u[kGroup];
-#pragma unroll
-            for (int q = 0; q < kGroup; ++q) {
-                if (i0 + q < nvec) {
-                    v[q] = V[(size_t)(i0 + q) * N + p];
-                    if (two) u[q] = V[(size_t)(i0 + q) * N + p2];
+               size_t cstride, float4 *__restrict__ w, size_t sw, size_t N, double *__restrict__ partial_d,
+               int nrhs, const int *__restrict__ active) {
+    constexpr int NPT = kAxpyTile / kCons;
+    extern __shared__ __align__(128) unsigned char pipe_raw[];
+    AxpySmem &S = *reinterpret_cast<AxpySmem *>(pipe_raw);
+    float4 *cs = reinterpret_cast<float4 *>(pipe_raw + sizeof(AxpySmem)) + (threadIdx.x >> 5) * nvec;
+    ring_init(S.full, S.empty, S.abort);
+    const int ntiles = ceil_div(N, kAxpyTile);
+    const int items = nrhs * ntiles;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned k = 0;
+    if (warp == kConsWarps) {
+        if (lane == 0) {
+            unsigned issued = 0;
+            for (int it = blockIdx.x; it < items; it += gridDim.x) {
+                const int r = it / ntiles, tl = it % ntiles;
+                if (active && !active[r]) continue;
+                const size_t p0 = (size_t)tl * kAxpyTile;
+                const unsigned bytes = (unsigned)min((size_t)kAxpyTile, N - p0) * 16u;
+                const float4 *Vr = V + r * sV, *wr = w + r * sw;
+                for (int i = -1; i < nvec; ++i, ++k) {
+                    const int s = (int)(k % kAxpyStages);
+                    if (!pipe::mbar_wait(&S.empty[s], ((k / kAxpyStages) & 1u) ^ 1u, &S.abort)) continue;
+                    pipe::mbar_arrive_expect_tx(&S.full[s], bytes);
+                    pipe::bulk_load(&S.slot[s][0], i < 0 ? wr + p0 : Vr + (size_t)i * N + p0, bytes, &S.full[s]);
+                    issued = k + 1;
                 }
             }
+            ring_drain(S.full, issued);
+        }
+        __syncwarp();
+        __syncthreads();
+        return;
+    }
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int t = threadIdx.x;
+    auto take = [&](int nodes, float4 (&a)[NPT]) {
+        const int s = (int)(k % kAxpyStages);
+        const bool ok = pipe::mbar_wait(&S.full[s], (k / kAxpyStages) & 1u, &S.abort);
 #pragma unroll
-            for (int q = 0; q < kGroup; ++q) {
-                if (i0 + q < nvec) {
-                    const float4 m = cs[i0 + q];   // -c_i
-                    // w += v * (-c): re = vr mr - vi mi, im = vr mi + vi mr
-                    ds_fma(rh, rl, v[q].x, v[q].y, m.x, m.y);
-                    ds_fma(rh, rl, -v[q].z, -v[q].w, m.z, m.w);
-                    ds_fma(ih, il, v[q].x, v[q].y, m.z, m.w);
-                    ds_fma(ih, il, v[q].z, v[q].w, m.x, m.y);
-                    if (two) {
-                        ds_fma(sh, sl, u[q].x, u[q].y, m.x, m.y);
-                        ds_fma(sh, sl, -u[q].z, -u[q].w, m.z, m.w);
-                        ds_fma(jh, jl, u[q].x, u[q].y, m.z, m.w);
-                        ds_fma(jh, jl, u[q].z, u[q].w, m.x, m.y);
-                    }
-                }
+        for (int m = 0; m < NPT; ++m) a[m] = (ok && t + m * kCons < nodes) ? S.slot[s][t + m * kCons] : zero;
+        __syncwarp();
+        if (lane == 0) pipe::mbar_arrive(&S.empty[s]);
+        ++k;
+    };
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int r = it / ntiles, tl = it % ntiles;
+        if (active && !active[r]) continue;
+        const size_t p0 = (size_t)tl * kAxpyTile;
+        const int nodes = (int)min((size_t)kAxpyTile, N - p0);
+        float4 *wr = w + r * sw;
+        for (int i = lane; i < nvec; i += 32) {
+            const double2 ci = c[r * cstride + i];
+            cs[i] = cvt<float4>(make_double2(-ci.x, -ci.y));   // (re_hi, re_lo, im_hi, im_lo) of -c_i
+        }
+        __syncwarp();
+        float4 xa[NPT];
+        take(nodes, xa);
+        float rh[NPT], rl[NPT], ih[NPT], il[NPT];
+#pragma unroll
+        for (int m = 0; m < NPT; ++m) {
+            rh[m] = xa[m].x;
+            rl[m] = xa[m].y;
+            ih[m] = xa[m].z;
+            il[m] = xa[m].w;
+        }
+        for (int i = 0; i < nvec; ++i) {
+            float4 v[NPT];
+            take(nodes, v);
+            const float4 mc = cs[i];   // -c_i
+#pragma unroll
+            for (int m = 0; m < NPT; ++m) {
+                // w += v * (-c): re = vr mr - vi mi, im = vr mi + vi mr
+                ds_fma(rh[m], rl[m], v[m].x, v[m].y, mc.x, mc.y);
+                ds_fma(rh[m], rl[m], -v[m].z, -v[m].w, mc.z, mc.w);
+                ds_fma(ih[m], il[m], v[m].x, v[m].y, mc.z, mc.w);
+                ds_fma(ih[m], il[m], v[m].z, v[m].w, mc.x, mc.y);
             }
         }
-        // renormalise (h, l) and store, node p then node p2
-        auto fin = [&](size_t pp, float &ah, float &al, float &bh, float &bl) {
-            float th = ah + al;
-            al = al - (th - ah);
-            ah = th;
-            th = bh + bl;
-            bl = bl - (th - bh);
-            bh = th;
-            w[pp] = make_float4(ah, al, bh, bl);
-            if (norm2) {
-                ds_fma(nh, nl, ah, al, ah, al);
-                ds_fma(nh, nl, bh, bl, bh, bl);
+        // renormalise (h, l), store, and add to the thread's norm, node by node
+        float nh = 0.f, nl = 0.f;
+#pragma unroll
+        for (int m = 0; m < NPT; ++m) {
+            float th = rh[m] + rl[m];
+            rl[m] = rl[m] - (th - rh[m]);
+            rh[m] = th;
+            th = ih[m] + il[m];
+            il[m] = il[m] - (th - ih[m]);
+            ih[m] = th;
+            if (t + m * kCons < nodes) {
+                wr[p0 + t + m * kCons] = make_float4(rh[m], rl[m], ih[m], il[m]);
+                ds_fma(nh, nl, rh[m], rl[m], rh[m], rl[m]);
+                ds_fma(nh, nl, ih[m], il[m], ih[m], il[m]);
             }
-        };
-        fin(p, rh, rl, ih, il);
-        if (two) fin(p2, sh, sl, jh, jl);
+        }
+        if (partial_d) {
+            const double v = warp_sum(ds_join(nh, nl));
+            if (lane == 0) partial_d[((size_t)r * ntiles + tl) * kConsWarps + warp] = S.abort ? qnan() : v;
+        }
+        __syncwarp();   // this warp's cs is rewritten by the next item
     }
-    if (norm2) reduce_norm(ds_join(nh, nl), partial_d, counter, norm2, r);
+    __syncthreads();
+}
+
+// norm2[r] = sum of the n partials of r (fixed order, as k_dot_finalize)
+__global__ void __launch_bounds__(256)
+k_norm_finalize(const double *__restrict__ partial_d, int n, double *__restrict__ norm2,
+                const int *__restrict__ active) {
+    const int r = blockIdx.x;
+    if (active && !active[r]) return;
+    const double *p = partial_d + (size_t)r * n;
+    __shared__ double red[8];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < n; t += 256) s += p[t];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = red[0];
+        for (int q = 1; q < 8; ++q) a += red[q];
+        norm2[r] = a;
+    }
 }
 
 template <typename CIn> __device__ __forceinline__ float4 ds_scaled(CIn x, float sh, float sl, double s);
@@ -416,12 +538,6 @@ k_update_zds(const float2 *__restrict__ Z, size_t sZ, int nvec, const double2 *_
     }
 }
 
-inline int sm_blocks_for(size_t N, int per_thread, int cap) {
-    const size_t per_wave = (size_t)152 * kThreads * per_thread;
-    int k = 1;
-    while (k < 8 && (size_t)k * per_wave < N && 152 * 2 * k <= cap) k *= 2;
-    return 152 * k <= cap ? 152 * k : cap;
-}
 
 inline int blocks_for(size_t N, int cap) {
     size_t b = (N + kThreads - 1) / kThreads;
@@ -431,14 +547,40 @@ inline int blocks_for(size_t N, int cap) {
 
 }  // namespace
 
+namespace {
+void set_pipe_attrs() {
+    static const int once = [] {
+        cudaFuncSetAttribute(k_multidot_ds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DotSmem));
+        cudaFuncSetAttribute(k_multiaxpy_ds, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(AxpySmem) + kConsWarps * kMaxVec * sizeof(float4)));
+        return 1;
+    }();
+    (void)once;
+}
+int pipe_grid(int items, int per_sm) {
+    const int cap = 152 * per_sm;
+    return items < cap ? (items > 0 ? items : 1) : cap;
+}
+}  // namespace
+
+size_t ds_partial_per_rhs(size_t N, int nvec_max) {
+    const size_t dot = (size_t)nvec_max * ceil_div(ceil_div(N, kDotTile), kDotTpi) * kConsWarps;
+    const size_t axpy = ((size_t)ceil_div(N, kAxpyTile) * kConsWarps + 1) / 2;   // doubles, in double2 units
+    return dot > axpy ? dot : axpy;
+}
+
 void launch_multidot_ds(const float4 *V, size_t sV, int nvec, const float4 *w, size_t sw, size_t N,
                         double2 *out, size_t out_stride, int nrhs, const int *active,
                         KrylovScratch &ks, cudaStream_t st) {
-    const int nb = sm_blocks_for(N, 4, ks.max_blocks);
+    set_pipe_attrs();
+    const int nch = ceil_div(ceil_div(N, kDotTile), kDotTpi);
+    const int nb = pipe_grid(nrhs * nch, kDotBlocksPerSM);
     prof_begin(st);
-    k_multidot_ds<<<dim3(nb, nrhs), kThreads, 0, st>>>(V, sV, nvec, w, sw, N, out, out_stride,
-                                                       ks.partial, ks.counter, ks.nvec_max, active);
-    count_launch();
+    k_multidot_ds<<<nb, kPipeThreads, sizeof(DotSmem), st>>>(V, sV, nvec, w, sw, N, ks.partial,
+                                                             ks.nvec_max, nrhs, active);
+    k_dot_finalize<<<dim3(nvec, nrhs), 256, 0, st>>>(ks.partial, ks.nvec_max, nch * kConsWarps, out,
+                                                     out_stride, active);
+    count_launch(2);
     if (prof_on())
         prof_end("multidot_ds", st, (nvec + 1.0) * N * 16.0 * nrhs, 0.0);
 }
@@ -446,11 +588,18 @@ void launch_multidot_ds(const float4 *V, size_t sV, int nvec, const float4 *w, s
 void launch_multiaxpy_ds(const float4 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
                          float4 *w, size_t sw, size_t N, double *norm2, int nrhs, const int *active,
                          KrylovScratch &ks, cudaStream_t st) {
-    const int nb = sm_blocks_for(N, 4, ks.max_blocks);
+    set_pipe_attrs();
+    const int ntiles = ceil_div(N, kAxpyTile);
+    const int nb = pipe_grid(nrhs * ntiles, kAxpyBlocksPerSM);
+    double *pd = norm2 ? (double *)ks.partial : nullptr;
     prof_begin(st);
-    k_multiaxpy_ds<<<dim3(nb, nrhs), kThreads, 0, st>>>(V, sV, nvec, c, c_stride, w, sw, N, norm2,
-                                                        (double *)ks.partial, ks.counter, active);
+    k_multiaxpy_ds<<<nb, kPipeThreads, sizeof(AxpySmem) + kConsWarps * nvec * sizeof(float4), st>>>(
+        V, sV, nvec, c, c_stride, w, sw, N, pd, nrhs, active);
     count_launch();
+    if (norm2) {
+        k_norm_finalize<<<nrhs, 256, 0, st>>>(pd, ntiles * kConsWarps, norm2, active);
+        count_launch();
+    }
     if (prof_on())
         prof_end("multiaxpy_ds", st, (nvec + 2.0) * N * 16.0 * nrhs, norm2 ? 4.0 * N * nrhs : 0.0);
 }

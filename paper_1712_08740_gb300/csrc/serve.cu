@@ -16,6 +16,7 @@
 // together by the batched solver.
 #include <atomic>
 #include <chrono>
+#include <algorithm>
 #include <cmath>
 #include <condition_variable>
 #include <deque>
@@ -101,7 +102,12 @@ size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o)
     b += 2.0 * nrhs * N * 16.0;                          // staging of host f and u
     if (o.precision == HELM_PREC_MIXED_DS) b += nrhs * N * 16.0;   // complex128 residuals
     b += (double)nrhs * (m + 1.0) * (m + 1.0) * 16.0 * 3.0;   // Hessenberg, rotations
-    b += (double)nrhs * (m + 1.0) * kMaxBlocks * 16.0;   // reduction partials
+    {
+        double per_rhs = (m + 1.0) * kMaxBlocks;         // reduction partials
+        if (o.precision == HELM_PREC_MIXED_DS)
+            per_rhs = std::max(per_rhs, (double)ds_partial_per_rhs((size_t)N, m + 1));
+        b += (double)nrhs * per_rhs * 16.0;
+    }
     b += 1 << 20;                                        // small buffers
     return (size_t)b;
 }
