@@ -153,6 +153,13 @@ helm_status helm_solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double 
  * not overlapping). Errors: HELM_ERR_STATE, HELM_ERR_ARG, HELM_ERR_CUDA. */
 helm_status helm_apply_H(helm_grid *g, const helm_c128 *x, helm_c128 *y);
 
+/* Eq. 3 in the arithmetic of the double-single Arnoldi step: x is rounded
+ * (truncated) to complex64, as the preconditioned vectors of that step are,
+ * and y = H x is formed with FP32 error-free products and two-sums (about 48
+ * significant bits) and returned as complex128. x, y: N complex values, host
+ * or device, not overlapping. Errors as helm_apply_H, plus HELM_ERR_NOMEM. */
+helm_status helm_apply_H_ds(helm_grid *g, const helm_c128 *x, helm_c128 *y);
+
 /* Eq. 6: y = M x on multigrid level `level` (0 = fine grid), in the grid's
  * preconditioner arithmetic. x, y: the level's node count of complex values.
  * Errors: HELM_ERR_STATE, HELM_ERR_ARG, HELM_ERR_CUDA. */

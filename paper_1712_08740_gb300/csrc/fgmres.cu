@@ -516,6 +516,33 @@ helm_status helm_apply_H(helm_grid *g, const helm_c128 *x, helm_c128 *y) {
     return sync_stream(g, "helm_apply_H");
 }
 
+helm_status helm_apply_H_ds(helm_grid *g, const helm_c128 *x, helm_c128 *y) {
+    clear_error();
+    if (!g || !x || !y) return fail(HELM_ERR_ARG, "null argument");
+    if (!g->has_model) return fail(HELM_ERR_STATE, "helm_set_model has not been called");
+    const size_t N = g->N;
+    const size_t bytes = N * sizeof(double2);
+    const void *xd;
+    void *yd;
+    helm_status s;
+    if ((s = stage_in(g, x, bytes, g->fst, &xd)) || (s = out_buf(g, y, bytes, g->ust, &yd))) return s;
+    if ((s = g->hdiag.ensure(N * sizeof(float4))) || (s = g->xst.ensure(N * sizeof(float2))) ||
+        (s = g->yst.ensure(N * sizeof(float4))))
+        return s;
+    if (!g->hdiag_ok) {
+        launch_make_hdiag_ds(level_view<double>(g, 0), shift_H(g), g->hdiag.as<float4>(), g->st);
+        g->hdiag_ok = true;
+    }
+    float2 *xf = g->xst.as<float2>();
+    float4 *wd = g->yst.as<float4>();
+    launch_convert<double2, float2>((const double2 *)xd, 0, xf, 0, N, 1, g->st);
+    launch_apply_H_ds(level_view<double>(g, 0), g->hdiag.as<float4>(), xf, 0, wd, 0, 1, nullptr, g->st);
+    launch_convert<float4, double2>(wd, 0, (double2 *)yd, 0, N, 1, g->st);
+    if ((s = check_cuda("helm_apply_H_ds"))) return s;
+    if ((s = copy_out(g, y, yd, bytes))) return s;
+    return sync_stream(g, "helm_apply_H_ds");
+}
+
 helm_status helm_apply_M(helm_grid *g, int level, const helm_c128 *x, helm_c128 *y) {
     clear_error();
     if (!g || !x || !y) return fail(HELM_ERR_ARG, "null argument");

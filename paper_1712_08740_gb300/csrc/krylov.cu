@@ -578,6 +578,8 @@ template void launch_convert<float2, double2>(const float2 *, size_t, double2 *,
                                               int, cudaStream_t);
 template void launch_convert<double2, double2>(const double2 *, size_t, double2 *, size_t,
                                                size_t, int, cudaStream_t);
+template void launch_convert<float4, double2>(const float4 *, size_t, double2 *, size_t, size_t, int,
+                                               cudaStream_t);
 template void launch_convert<float4, float2>(const float4 *, size_t, float2 *, size_t, size_t, int,
                                              cudaStream_t);
 

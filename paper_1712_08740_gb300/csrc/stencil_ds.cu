@@ -16,18 +16,10 @@ namespace helm {
 
 namespace {
 
-constexpr int kBX = 128;
-
 struct dsf {
     float h, l;
 };
 
-__device__ __forceinline__ dsf ds_add_f(dsf a, float b) {      // unnormalised
-    const float s = a.h + b;
-    const float bb = s - a.h;
-    const float e = (a.h - (s - bb)) + (b - bb);
-    return {s, a.l + e};
-}
 __device__ __forceinline__ dsf ds_norm(dsf a) {
     const float s = a.h + a.l;
     return {s, a.l - (s - a.h)};
@@ -77,25 +69,32 @@ __global__ void k_make_hdiag_ds(LevelView<double> L, OpShift<double> s, float4 *
     }
 }
 
-template <int DIM, typename CIn>
-__device__ __forceinline__ void nbr_terms(const CIn *__restrict__ z, size_t p, int i, int n,
-                                          size_t stride, dsf &sr, dsf &si) {
-    if (i > 0) {
-        const float2 v = cvt<float2>(z[p - stride]);
-        const float c = (i == n - 1) ? 2.f : 1.f;
-        sr = ds_add_f(sr, c * v.x);
-        si = ds_add_f(si, c * v.y);
-    }
-    if (i < n - 1) {
-        const float2 v = cvt<float2>(z[p + stride]);
-        const float c = (i == 0) ? 2.f : 1.f;
-        sr = ds_add_f(sr, c * v.x);
-        si = ds_add_f(si, c * v.y);
-    }
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ dsf two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+// (s.h, s.l) + (t.h, t.l) for two exact pair sums; renormalised
+__device__ __forceinline__ dsf add_pairs(dsf s, dsf t) {
+    const dsf u = two_sum(s.h, t.h);
+    return ds_norm({u.h, (s.l + t.l) + u.l});
 }
 
+// Neighbour of node p along one axis, scaled by the boundary factor: the
+// mirrored ghost of the absorbing boundary doubles the inner neighbour at
+// the first and last node, and the missing outer neighbour contributes 0.
+__device__ __forceinline__ float2 nbr(const float2 *__restrict__ z, size_t q, bool exists, bool twice) {
+    if (!exists) return make_float2(0.f, 0.f);
+    const float2 v = z[q];
+    return twice ? make_float2(2.f * v.x, 2.f * v.y) : v;
+}
+
+// One block covers (part of) a row of the grid with one node per thread; the
+// grid's y dimension strides over rows (y, z), its z dimension over
+// right-hand sides.
 template <int DIM>
-__global__ void __launch_bounds__(kBX)
+__global__ void __launch_bounds__(512)
 k_apply_H_ds(LevelView<double> L, const float4 *__restrict__ hd, float ihh, float ihl,
              const float2 *__restrict__ z, size_t sz, float4 *__restrict__ w, size_t sw,
              const int *__restrict__ active) {
@@ -103,21 +102,41 @@ k_apply_H_ds(LevelView<double> L, const float4 *__restrict__ hd, float ihh, floa
     if (active && !active[r]) return;
     z += r * sz;
     w += r * sw;
-    const int nx = L.nx;
+    const int nx = L.nx, ny = L.ny;
     const int rows = L.ny * L.nz;
-    const int ix = blockIdx.x * kBX + threadIdx.x;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     if (ix >= nx) return;
     const dsf ih = {ihh, ihl};
+    const bool xw = ix > 0, xe = ix < nx - 1;
     for (int row = blockIdx.y; row < rows; row += gridDim.y) {
         const size_t p = (size_t)row * nx + ix;
-        dsf sr = {0.f, 0.f}, si = {0.f, 0.f};
-        nbr_terms<DIM>(z, p, ix, nx, 1, sr, si);
-        if (DIM >= 2) nbr_terms<DIM>(z, p, (DIM == 3) ? row % L.ny : row, L.ny, (size_t)nx, sr, si);
-        if (DIM == 3) nbr_terms<DIM>(z, p, row / L.ny, L.nz, (size_t)nx * L.ny, sr, si);
-        sr = ds_norm(sr);
-        si = ds_norm(si);
-        const float4 d = hd[p];
         const float2 zp = z[p];
+        // neighbour sums, exact as unevaluated pairs: x pair + y pair (+ z pair)
+        dsf sr, si;
+        {
+            const float2 a = nbr(z, p - 1, xw, !xe), b = nbr(z, p + 1, xe, !xw);
+            sr = two_sum(a.x, b.x);
+            si = two_sum(a.y, b.y);
+        }
+        if (DIM >= 2) {
+            const int iy = DIM == 3 ? row % ny : row;
+            const bool ys = iy > 0, yn = iy < ny - 1;
+            const float2 a = nbr(z, p - nx, ys, !yn), b = nbr(z, p + nx, yn, !ys);
+            sr = add_pairs(sr, two_sum(a.x, b.x));
+            si = add_pairs(si, two_sum(a.y, b.y));
+        } else {
+            sr = ds_norm(sr);
+            si = ds_norm(si);
+        }
+        if (DIM == 3) {
+            const int iz = row / ny;
+            const size_t sl = (size_t)nx * ny;
+            const bool zb = iz > 0, zf = iz < L.nz - 1;
+            const float2 a = nbr(z, p - sl, zb, !zf), b = nbr(z, p + sl, zf, !zb);
+            sr = add_pairs(sr, ds_norm(two_sum(a.x, b.x)));
+            si = add_pairs(si, ds_norm(two_sum(a.y, b.y)));
+        }
+        const float4 d = hd[p];
         const dsf dre = {d.x, d.y}, dim_ = {d.z, d.w};
         // d z
         const dsf ar = ds_add(ds_mul_f(dre, zp.x), ds_mul_f(dim_, -zp.y));
@@ -146,11 +165,14 @@ void launch_apply_H_ds(const LevelView<double> &L, const float4 *hd, const float
     const float ihh = (float)ih;                    // nearest float; ih - ihh is exact in FP64
     const float ihl = (float)(ih - (double)ihh);
     const int rows = L.ny * L.nz;
-    const dim3 g((L.nx + kBX - 1) / kBX, rows < 65535 ? rows : 65535, nb);
+    // blocks of whole warps spanning a row: 401 nodes -> 416 threads
+    const int wpr = (L.nx + 31) / 32, bpr = (wpr + 15) / 16;
+    const int bx = 32 * ((wpr + bpr - 1) / bpr);
+    const dim3 g(bpr, rows < 65535 ? rows : 65535, nb);
     prof_begin(st);
-    if (L.dim == 1) k_apply_H_ds<1><<<g, kBX, 0, st>>>(L, hd, ihh, ihl, z, sz, w, sw, active);
-    else if (L.dim == 2) k_apply_H_ds<2><<<g, kBX, 0, st>>>(L, hd, ihh, ihl, z, sz, w, sw, active);
-    else k_apply_H_ds<3><<<g, kBX, 0, st>>>(L, hd, ihh, ihl, z, sz, w, sw, active);
+    if (L.dim == 1) k_apply_H_ds<1><<<g, bx, 0, st>>>(L, hd, ihh, ihl, z, sz, w, sw, active);
+    else if (L.dim == 2) k_apply_H_ds<2><<<g, bx, 0, st>>>(L, hd, ihh, ihl, z, sz, w, sw, active);
+    else k_apply_H_ds<3><<<g, bx, 0, st>>>(L, hd, ihh, ihl, z, sz, w, sw, active);
     count_launch();
     if (prof_on()) {
         // per right-hand side: z in, w out; the diagonal once per launch

@@ -28,7 +28,7 @@ PRECISION = {"f64": 0, "mixed": 1, "mixed_ds": 2}
 
 EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "helm_set_stream",
             "helm_set_options", "helm_get_options", "helm_set_model", "helm_set_shift",
-            "helm_solve", "helm_solve_batch", "helm_apply_H", "helm_apply_M",
+            "helm_solve", "helm_solve_batch", "helm_apply_H", "helm_apply_H_ds", "helm_apply_M",
             "helm_apply_precond", "helm_true_residual", "helm_num_levels", "helm_level_info",
             "helm_last_error", "helm_kernel_launches", "helm_profile_start", "helm_profile_stop",
             "helm_time_kernel", "helm_true_residual_noalloc", "helm_solve_footprint",
@@ -106,6 +106,7 @@ def _load():
         "helm_solve": (I, [P, P, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "helm_solve_batch": (I, [P, I, P, D, P, P, P]),
         "helm_apply_H": (I, [P, P, P]),
+        "helm_apply_H_ds": (I, [P, P, P]),
         "helm_apply_M": (I, [P, I, P, P]),
         "helm_apply_precond": (I, [P, P, P]),
         "helm_true_residual": (I, [P, P, P, ctypes.POINTER(D)]),
@@ -245,6 +246,10 @@ def helm_solve_batch(g, nrhs, f, tol, u, check=True):
 
 def helm_apply_H(g, x, y):
     _check(_lib.helm_apply_H(g, _ptr(x, np.complex128), _ptr(y, np.complex128)))
+
+
+def helm_apply_H_ds(g, x, y):
+    _check(_lib.helm_apply_H_ds(g, _ptr(x, np.complex128), _ptr(y, np.complex128)))
 
 
 def helm_apply_M(g, level, x, y):
@@ -397,6 +402,9 @@ class Grid:
 
     def apply_H(self, x, y):
         helm_apply_H(self._g, x, y)
+
+    def apply_H_ds(self, x, y):
+        helm_apply_H_ds(self._g, x, y)
 
     def apply_M(self, level, x, y):
         helm_apply_M(self._g, level, x, y)

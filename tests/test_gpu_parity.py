@@ -66,6 +66,24 @@ def test_apply_H_matches_oracle(helm, n):
     assert rel(y.cpu().numpy(), ref) < 1e-13
 
 
+@pytest.mark.parametrize("n", SHAPES + [(401, 201)])
+def test_apply_H_double_single_matches_oracle(helm, n):
+    """H z of the double-single Arnoldi step on complex64 input: the oracle's
+    complex128 product of the same complex64 values, to the ~48 bits of the
+    double-single result (element by element, relative to the largest)."""
+    h, om, al = 10.0, 2 * np.pi * 10.0, 0.01
+    m = rand_model(n, 5)
+    g = helm.Grid(n, h)
+    g.set_model(dev(m), om, al)
+    x = rand_c(int(np.prod(n)), 6).astype(np.complex64).astype(np.complex128)
+    y = torch.empty(len(x), dtype=torch.complex128, device=DEV)
+    g.apply_H_ds(dev(x), y)
+    ref = op.assemble_H(n, h, m, om, al) @ x
+    y = y.cpu().numpy()
+    assert np.abs(y - ref).max() <= 2e-13 * np.abs(ref).max()
+    assert rel(y, ref) < 1e-13
+
+
 def test_unit_vectors_give_dense_H_columns(helm):
     n, h, om, al = (8, 8), 12.0, 2 * np.pi * 9.0, 0.02
     m = rand_model(n, 3)
