@@ -155,6 +155,8 @@ helm_status build_hierarchy(helm_grid *g) {
             launch_assemble_dense<float>(v, shift_M<float>(g), g->Ainv.as<float2>(), g->st);
             launch_gauss_jordan<float>(g->Ainv.as<float2>(), g->colbuf.as<float2>(), nc, g->st);
             launch_transpose_square<float>(g->Ainv.as<float2>(), nc, g->st);
+            if ((s = g->Atc.ensure(coarse_tc_tile_floats(nc) * sizeof(float)))) return s;
+            launch_coarse_tc_tiles(g->Ainv.as<float2>(), nc, g->Atc.as<float>(), g->st);
         }
         g->nc = nc;
     }
@@ -185,7 +187,10 @@ helm_status ensure_level_work(helm_grid *g, int nrhs) {
         if (l == 0 && ((s = L.u.ensure(b)) || (s = L.b.ensure(b)))) return s;
     }
     if (g->nc > 0 && g->cpart_rhs < nrhs) {
-        if ((s = g->cpart.ensure(coarse_part_elems(g->nc, nrhs) * esz)) ||
+        size_t pb = coarse_part_elems(g->nc, nrhs) * esz;
+        if (g->vc_prec != HELM_PREC_F64)
+            pb = std::max(pb, coarse_tc_part_floats(g->nc, nrhs) * sizeof(float));
+        if ((s = g->cpart.ensure(pb)) ||
             (s = g->cticket.ensure(coarse_tickets(g->nc, nrhs) * sizeof(unsigned))))
             return s;
         cudaMemsetAsync(g->cticket.p, 0, coarse_tickets(g->nc, nrhs) * sizeof(unsigned), g->st);

@@ -1,0 +1,294 @@
+// Coarsest-level product of the complex64 V-cycle on the tensor cores:
+// Z = Ainv R, Ainv the dense inverse of the coarsest shifted Laplacian (Eq. 6;
+// n x n complex, about 1300 x 1300 on the 401 x 201 grid) and R the coarse
+// right-hand sides of up to 64 sources at once.
+//
+// The complex product is split into real ones, Zr = Ar Rr - Ai Ri and
+// Zi = Ai Rr + Ar Ri, each formed with tcgen05.mma kind::tf32 (M = 128 rows,
+// N = 64 right-hand sides, K = 8 per instruction; the minus sign is the
+// instruction's negate-B bit). TF32 keeps 10 mantissa bits, so every FP32
+// operand x is split into x_hi = x with its low 13 bits cleared (exact in
+// TF32) and x_lo = x - x_hi, and a b = a_hi b_hi + a_hi b_lo + a_lo b_hi
+// (the dropped a_lo b_lo is ~2^-22 relative): the product keeps FP32
+// accuracy, as the rest of the complex64 V-cycle.
+//
+// Ainv is split and laid out once per model (launch_coarse_tc_tiles) in
+// blocks of 128 rows x 32 columns, four planes (re_hi, re_lo, im_hi, im_lo)
+// in the K-major core-matrix order the MMA reads, so one cp.async.bulk copy
+// stages a CTA's 64 KB of Ainv. CTA (kc, rt, jt) takes rows 128 rt.., columns
+// 32 kc.. and sources 64 jt..; it splits its slice of R into shared memory,
+// issues 48 MMAs into two TMEM accumulators (real, imaginary: 128 lanes x 64
+// columns each), and writes its partial product. k_coarse_tc_sum adds the
+// n/32 partials in chunk order. Each output element's arithmetic depends on
+// n only (one source's column never mixes with another's), so batched and
+// single solves agree bitwise.
+#include "helm_internal.cuh"
+#include "pipe.cuh"
+
+namespace helm {
+
+namespace {
+
+constexpr int kM = 128;               // rows of Ainv per CTA (MMA M)
+constexpr int kN = 64;                // right-hand sides per CTA (MMA N)
+constexpr int kK = 32;                // columns of Ainv per CTA
+constexpr int kThreads = 256;
+constexpr int kAPlane = kM * kK;      // floats per plane of an Ainv block
+constexpr int kBPlane = kN * kK;
+constexpr unsigned kTmemCols = 128;   // two accumulators of kN columns
+
+// element (row, k) of a block with kK columns, K-major core-matrix order:
+// core matrices of 8 rows x 4 floats (128 contiguous bytes), kK / 4 of them
+// along K for each group of 8 rows
+__host__ __device__ constexpr int cm_off(int row, int k) {
+    return ((row >> 3) * (kK / 4) + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+    return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+}
+
+struct alignas(1024) TcSmem {
+    float a[4][kAPlane];    // re_hi, re_lo, im_hi, im_lo of the Ainv block
+    float b[4][kBPlane];    // re_hi, re_lo, im_hi, im_lo of the R slice (row = source)
+    uint64_t abar, mbar;    // Ainv block landed; MMAs complete
+    uint32_t tmem;          // TMEM base address
+    int abort;
+};
+
+// Shared-memory matrix descriptor: K-major, no swizzle; lbo = byte distance
+// of core matrices adjacent along K, sbo = along M/N (sm_100 descriptor,
+// version field 1).
+__device__ __forceinline__ uint64_t smem_desc(const void *p, unsigned lbo, unsigned sbo) {
+    const unsigned addr = pipe::smem_addr(p);
+    return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 64 columns of TMEM (this warp's lane quarter) into registers
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+          "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+          "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]),
+          "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]),
+          "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]),
+          "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+          "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]),
+          "=r"(v[63])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcGeom {
+    int n, nrt, nkc, Mp, nsb;   // order, row blocks, column chunks, padded rows, source blocks
+};
+
+inline TcGeom tc_geom(int n, int nb) {
+    TcGeom g;
+    g.n = n;
+    g.nrt = (n + kM - 1) / kM;
+    g.nkc = (n + kK - 1) / kK;
+    g.Mp = g.nrt * kM;
+    g.nsb = (nb + kN - 1) / kN;
+    return g;
+}
+
+// tiles[((rt * nkc + kc) * 4 + plane) * kAPlane + cm_off(m % kM, k % kK)],
+// m = row, k = column of Ainv (At is Ainv column-major); zero padding
+__global__ void k_coarse_tc_tiles(const float2 *__restrict__ At, TcGeom G, float *__restrict__ tiles) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (m >= G.Mp) return;
+    float2 v = make_float2(0.f, 0.f);
+    if (m < G.n && k < G.n) v = At[(size_t)k * G.n + m];
+    float *blk = tiles + (size_t)((m / kM) * G.nkc + k / kK) * 4 * kAPlane;
+    const int o = cm_off(m % kM, k % kK);
+    const float rh = tf32_hi(v.x), ih = tf32_hi(v.y);
+    blk[o] = rh;
+    blk[kAPlane + o] = v.x - rh;
+    blk[2 * kAPlane + o] = ih;
+    blk[3 * kAPlane + o] = v.y - ih;
+}
+
+// part[((kc * 2 + plane) * nb + source) * Mp + row]: chunk kc's share of Z
+__global__ void __launch_bounds__(kThreads, 2)
+k_coarse_tc(const float *__restrict__ tiles, TcGeom G, const float2 *__restrict__ R, size_t sr,
+            float *__restrict__ part, int nb, const int *__restrict__ active) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    TcSmem &S = *reinterpret_cast<TcSmem *>(tc_raw);
+    const int kc = blockIdx.x, rt = blockIdx.y, jt = blockIdx.z;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (t == 0) {
+        pipe::mbar_init(&S.abar, 1);
+        pipe::mbar_init(&S.mbar, 1);
+        S.abort = 0;
+        pipe::mbar_init_fence();
+        const unsigned bytes = 4u * kAPlane * sizeof(float);
+        pipe::mbar_arrive_expect_tx(&S.abar, bytes);
+        pipe::bulk_load(&S.a[0][0], tiles + (size_t)(rt * G.nkc + kc) * 4 * kAPlane, bytes, &S.abar);
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         pipe::smem_addr(&S.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // this CTA's slice of R, split into TF32 hi and lo planes
+    for (int idx = t; idx < kN * kK; idx += kThreads) {
+        const int j = idx / kK, k = idx % kK;
+        const int src = jt * kN + j, col = kc * kK + k;
+        float2 v = make_float2(0.f, 0.f);
+        if (src < nb && col < G.n && (!active || active[src])) v = R[(size_t)src * sr + col];
+        const int o = cm_off(j, k);
+        const float rh = tf32_hi(v.x), ih = tf32_hi(v.y);
+        S.b[0][o] = rh;
+        S.b[1][o] = v.x - rh;
+        S.b[2][o] = ih;
+        S.b[3][o] = v.y - ih;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> MMA reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    if (t == 0) {
+        if (pipe::mbar_wait(&S.abar, 0, &S.abort)) {
+            // D f32, A and B tf32, both K-major, N = 64, M = 128; bit 14 negates B
+            const uint32_t idp = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                                 ((uint32_t)(kM >> 4) << 24);
+            const uint32_t idn = idp | (1u << 14);
+            const uint32_t dr = tmem, di = tmem + kN;
+            constexpr unsigned lbo = 128, sbo = (kK / 4) * 128;
+#pragma unroll
+            for (int s = 0; s < kK / 8; ++s) {
+                uint64_t a[4], b[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = smem_desc(&S.a[q][s * 64], lbo, sbo);
+                    b[q] = smem_desc(&S.b[q][s * 64], lbo, sbo);
+                }
+                const uint32_t acc = s > 0;
+                // Zr += Ar Rr - Ai Ri
+                mma_tf32(dr, a[0], b[0], idp, acc);
+                mma_tf32(dr, a[0], b[1], idp, 1);
+                mma_tf32(dr, a[1], b[0], idp, 1);
+                mma_tf32(dr, a[2], b[2], idn, 1);
+                mma_tf32(dr, a[2], b[3], idn, 1);
+                mma_tf32(dr, a[3], b[2], idn, 1);
+                // Zi += Ai Rr + Ar Ri
+                mma_tf32(di, a[2], b[0], idp, acc);
+                mma_tf32(di, a[2], b[1], idp, 1);
+                mma_tf32(di, a[3], b[0], idp, 1);
+                mma_tf32(di, a[0], b[2], idp, 1);
+                mma_tf32(di, a[0], b[3], idp, 1);
+                mma_tf32(di, a[1], b[2], idp, 1);
+            }
+        }
+        // arrives once the MMAs issued above (if any) have completed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         pipe::smem_addr(&S.mbar))
+                     : "memory");
+    }
+    __syncwarp();
+    if (!pipe::mbar_wait_drain(&S.mbar, 0)) S.abort = 1;
+    __syncthreads();   // every thread sees the same abort word
+    tc_fence_after();
+    // warps 0-3 read the real accumulator, 4-7 the imaginary one; warp w sees
+    // TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 = rows of the block
+    const int qtr = warp & 3, plane = warp >> 2;
+    uint32_t v[64];
+    tmem_ld64(tmem + ((uint32_t)(32 * qtr) << 16) + (uint32_t)(plane * kN), v);
+    const int row = rt * kM + 32 * qtr + lane;
+    const bool bad = S.abort != 0;
+    float *dst = part + ((size_t)(kc * 2 + plane) * nb + (size_t)jt * kN) * G.Mp + row;
+    const int nc = min(kN, nb - jt * kN);   // padding columns are not stored
+#pragma unroll
+    for (int c = 0; c < kN; ++c)
+        if (c < nc) dst[(size_t)c * G.Mp] = bad ? __int_as_float(0x7fc00000) : __uint_as_float(v[c]);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+    // after an abort, wait (bounded) for the Ainv copy before the CTA exits
+    if (t == 0 && bad) pipe::mbar_wait_drain(&S.abar, 0);
+}
+
+// Z[source][row] = sum over chunks kc, in chunk order, of the partials
+__global__ void __launch_bounds__(256)
+k_coarse_tc_sum(const float *__restrict__ part, TcGeom G, float2 *__restrict__ Z, size_t sz, int nb,
+                const int *__restrict__ active) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x, src = blockIdx.y;
+    if (row >= G.n || src >= nb || (active && !active[src])) return;
+    const size_t plane = (size_t)nb * G.Mp;
+    const float *p = part + (size_t)src * G.Mp + row;
+    float re = 0.f, im = 0.f;
+#pragma unroll 8
+    for (int kc = 0; kc < G.nkc; ++kc) {
+        re += p[(size_t)(2 * kc) * plane];
+        im += p[(size_t)(2 * kc + 1) * plane];
+    }
+    Z[(size_t)src * sz + row] = make_float2(re, im);
+}
+
+}  // namespace
+
+size_t coarse_tc_tile_floats(int n) {
+    const TcGeom g = tc_geom(n, 1);
+    return (size_t)g.nrt * g.nkc * 4 * kAPlane;
+}
+
+size_t coarse_tc_part_floats(int n, int nb) {
+    const TcGeom g = tc_geom(n, nb);
+    return (size_t)g.nkc * 2 * nb * g.Mp;
+}
+
+void launch_coarse_tc_tiles(const float2 *At, int n, float *tiles, cudaStream_t st) {
+    const TcGeom g = tc_geom(n, 1);
+    k_coarse_tc_tiles<<<dim3((g.Mp + 255) / 256, g.nkc * kK), 256, 0, st>>>(At, g, tiles);
+    count_launch();
+}
+
+void launch_coarse_tc(const float *tiles, int n, const float2 *r, size_t sr, float2 *z, size_t sz,
+                      int nb, const int *active, float *part, cudaStream_t st) {
+    static const int once = [] {
+        cudaFuncSetAttribute(k_coarse_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+        return 1;
+    }();
+    (void)once;
+    const TcGeom g = tc_geom(n, nb);
+    prof_begin(st);
+    k_coarse_tc<<<dim3(g.nkc, g.nrt, g.nsb), kThreads, sizeof(TcSmem), st>>>(tiles, g, r, sr, part,
+                                                                                   nb, active);
+    k_coarse_tc_sum<<<dim3((n + 255) / 256, nb), 256, 0, st>>>(part, g, z, sz, nb, active);
+    count_launch(2);
+    if (prof_on()) {
+        // Ainv planes once per source block, R and Z once
+        const double ab = (double)g.nrt * g.nkc * 4 * kAPlane * 4.0 * g.nsb;
+        prof_end("coarse_tc", st, ab + 16.0 * n * (double)nb, 0.0);
+    }
+}
+
+}  // namespace helm

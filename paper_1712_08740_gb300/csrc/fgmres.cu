@@ -256,7 +256,7 @@ long long graph_key_of(const helm_grid *g, int nrhs, double tol) {
     mixp(g->act_it.p); mixp(g->act_cy.p); mixp(g->act2.p); mixp(g->Ainv.p); mixp(g->hflag);
     mixp(g->cpart.p); mixp(g->cticket.p);
     mixp(g->cR.p); mixp(g->cg.p); mixp(g->ccs.p); mixp(g->csn.p); mixp(g->cQ.p); mixp(g->cfn.p);
-    mixp(g->ck.p); mixp(g->cits.p); mixp(g->cstat.p); mixp(g->cany.p); mixp(g->hdiag.p); mixp(g->rbuf.p);
+    mixp(g->ck.p); mixp(g->cits.p); mixp(g->cstat.p); mixp(g->cany.p); mixp(g->hdiag.p); mixp(g->Atc.p); mixp(g->rbuf.p);
     for (const auto &L : g->lv) {
         mixp(L.w64.p); mixp(L.w32.p); mixp(L.dinv.p); mixp(L.u.p); mixp(L.t.p); mixp(L.b.p); mixp(L.r.p);
         mixu((unsigned long long)L.N);
@@ -693,11 +693,14 @@ extern "C" helm_status helm_time_kernel(helm_grid *g, const char *kernel, int j,
                                           Lc.r.as<double2>(), Lc.N, nrhs, nullptr, g->cpart.p,
                                           g->cticket.as<unsigned>(), g->st);
             else
-                launch_dense_gemv<float>((const float2 *)g->Ainv.p, g->nc, Lc.b.as<float2>(), Lc.N,
-                                         Lc.r.as<float2>(), Lc.N, nrhs, nullptr, g->cpart.p,
-                                         g->cticket.as<unsigned>(), g->st);
+                coarse_product<float>(g, Lc.b.as<float2>(), Lc.N, Lc.r.as<float2>(), Lc.N, nrhs, nullptr,
+                                      g->st);
             const double cs = g->vc_prec == HELM_PREC_F64 ? 16.0 : 8.0;
-            b = ((double)g->nc * g->nc + 2.0 * g->nc * nrhs) * cs;
+            // complex128: Ainv once; complex64: its TF32 hi/lo planes once per block of 64 sources
+            const double ab = g->vc_prec == HELM_PREC_F64
+                                  ? (double)g->nc * g->nc * cs
+                                  : (double)coarse_tc_tile_floats(g->nc) * 4.0 * ((nrhs + 63) / 64);
+            b = ab + 2.0 * g->nc * nrhs * cs;
             fl = g->vc_prec == HELM_PREC_F64 ? 8.0 * g->nc * (double)g->nc * nrhs : 0.0;
         } else if (name == "multidot") {
             launch_multidot(V, sV, nvec, V + (size_t)(j + 1) * N, sV, N, hb, 2 * nv, nrhs, nullptr, ks, g->st);

@@ -56,6 +56,7 @@ struct helm_grid {
     int vc_prec = -1;                   // precision the hierarchy was built for
     int nc = 0;                         // coarse inverse order
     helm::DevBuf Ainv, colbuf;          // coarse inverse (transposed) and Gauss-Jordan column
+    helm::DevBuf Atc;                   // complex64 inverse as TF32 hi/lo tensor-core tiles
     helm::DevBuf cpart, cticket;        // coarse product scratch: group sums, tickets
     int cpart_rhs = 0;                  // right-hand sides cpart/cticket are sized for
 

@@ -239,6 +239,16 @@ void launch_dense_gemv(const cplx_t<T> *At, int n, const cplx_t<T> *r, size_t sr
 // the inverse is stored transposed (column-major) for launch_dense_gemv
 template <typename T>
 void launch_transpose_square(cplx_t<T> *A, int n, cudaStream_t st);
+// complex64 coarse product on the tensor cores (tcgen05 kind::tf32, FP32
+// operands split into TF32 hi + lo): Ainv (given column-major, as stored for
+// launch_dense_gemv) is laid out once into coarse_tc_tile_floats(n) floats;
+// z = Ainv r for nb right-hand sides uses coarse_tc_part_floats(n, nb) floats
+// of scratch
+size_t coarse_tc_tile_floats(int n);
+size_t coarse_tc_part_floats(int n, int nb);
+void launch_coarse_tc_tiles(const float2 *At, int n, float *tiles, cudaStream_t st);
+void launch_coarse_tc(const float *tiles, int n, const float2 *r, size_t sr, float2 *z, size_t sz,
+                      int nb, const int *active, float *part, cudaStream_t st);
 // scratch of launch_dense_gemv for nb right-hand sides: group sums (complex
 // elements of the V-cycle type) and tickets (unsigned, zero at rest)
 size_t coarse_part_elems(int n, int nb);

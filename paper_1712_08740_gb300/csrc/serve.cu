@@ -97,7 +97,13 @@ size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o)
     b += levels_sum * (8.0 + 8.0 + 4.0 + csz);           // slowness, coefficients, 1/diag(M)
     if (o.precond != HELM_PRECOND_NONE) {
         b += nc * nc * csz + nc * csz;                   // coarse inverse
-        b += (double)coarse_part_elems((int)nc, nrhs) * csz + coarse_tickets((int)nc, nrhs) * 4.0;
+        double part = (double)coarse_part_elems((int)nc, nrhs) * csz;
+        if (csz == 8.0) {
+            // complex64: TF32 tensor-core tiles of the inverse and their partial products
+            b += (double)coarse_tc_tile_floats((int)nc) * 4.0;
+            part = std::max(part, (double)coarse_tc_part_floats((int)nc, nrhs) * 4.0);
+        }
+        b += part + coarse_tickets((int)nc, nrhs) * 4.0;
     }
     b += 2.0 * nrhs * N * 16.0;                          // staging of host f and u
     if (o.precision == HELM_PREC_MIXED_DS) b += nrhs * N * 16.0;   // complex128 residuals

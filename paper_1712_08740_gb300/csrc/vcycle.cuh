@@ -79,6 +79,18 @@ inline OpShift<double> shift_H(const helm_grid *g) {
 // u0 = V-cycle(b0) for nb right-hand sides; b0/u0 with per-rhs strides sb0/su0.
 // CB0 is the type of b0: complex128 basis vectors feed a complex64 V-cycle
 // directly in the mixed form (the fused kernels convert on load).
+// Coarsest-level product z = Ainv r (Eq. 6's coarse solve): complex128 on the
+// CUDA cores, complex64 on the tensor cores.
+template <typename T>
+inline void coarse_product(helm_grid *g, const cplx_t<T> *r, size_t sr, cplx_t<T> *z, size_t sz, int nb,
+                           const int *act, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value)
+        launch_coarse_tc(g->Atc.as<float>(), g->nc, r, sr, z, sz, nb, act, g->cpart.as<float>(), st);
+    else
+        launch_dense_gemv<T>((const cplx_t<T> *)g->Ainv.p, g->nc, r, sr, z, sz, nb, act, g->cpart.p,
+                             g->cticket.template as<unsigned>(), st);
+}
+
 template <typename T, typename CB0>
 void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, int nb,
             const int *act) {
@@ -103,9 +115,8 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
                                    act, st, tile_down(g, l, nb));
         }
         C *uc = (L - 1 == 0) ? u0 : g->lv[L - 1].u.template as<C>();
-        launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, g->lv[L - 1].b.template as<C>(),
-                             g->lv[L - 1].N, uc, g->lv[L - 1].N, nb, act, g->cpart.p,
-                             g->cticket.template as<unsigned>(), st);
+        coarse_product<T>(g, g->lv[L - 1].b.template as<C>(), g->lv[L - 1].N, uc, g->lv[L - 1].N, nb,
+                          act, st);
         // up: u_l = Jacobi(u_pre + P e_{l+1})
         for (int l = L - 2; l >= 0; --l) {
             const LevelView<T> F = level_view<T>(g, l), Cv = level_view<T>(g, l + 1);
@@ -132,8 +143,7 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
         sb0c = g->lv[0].N;
     }
     if (L == 1) {
-        launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, b0c, sb0c, u0, su0, nb, act, g->cpart.p,
-                             g->cticket.template as<unsigned>(), st);
+        coarse_product<T>(g, b0c, sb0c, u0, su0, nb, act, st);
         return;
     }
     std::vector<const C *> B(L);
@@ -179,8 +189,7 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
         launch_restrict<T>(Lv, level_view<T>(g, l + 1), res, N, g->lv[l + 1].b.template as<C>(),
                            g->lv[l + 1].N, nb, act, st);
     }
-    launch_dense_gemv<T>((const C *)g->Ainv.p, g->nc, B[L - 1], SB[L - 1], U[L - 1], SU[L - 1], nb,
-                         act, g->cpart.p, g->cticket.template as<unsigned>(), st);
+    coarse_product<T>(g, B[L - 1], SB[L - 1], U[L - 1], SU[L - 1], nb, act, st);
     for (int l = L - 2; l >= 0; --l) {
         const LevelView<T> Lv = level_view<T>(g, l);
         const LevelView<T> Cv = level_view<T>(g, l + 1);

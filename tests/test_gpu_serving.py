@@ -69,11 +69,14 @@ def test_results_same_alone_and_in_the_mix(helm, precision):
 
 
 def test_admission_by_memory_budget(helm):
-    reqs = make_requests(4, seed=3)[:3]
+    # three requests on one grid size: their footprints differ by little, so a
+    # budget of 1.2 x the largest holds one of them but never two
+    reqs = [r for r in make_requests(12, seed=3) if r["n"] == (97, 49)][:3]
     o = helm.helm_default_options()
     o.precision = 1
     fp = [helm.helm_solve_footprint(len(r["n"]), r["n"], r["F"].shape[0], o) for r in reqs]
     # a budget that admits only one request at a time
+    assert max(fp) * 1.2 < 2 * min(fp)
     srv = helm.Server(workers=3, memory_budget=int(max(fp) * 1.2), precision="mixed")
     ids = [srv.submit(r["n"], r["h"], r["m"], r["omega"], r["alpha"], r["F"], 1e-8) for r in reqs]
     res = [srv.wait(i)[1] for i in ids]
