@@ -126,8 +126,17 @@ k_givens_scale(CycleState S, int j, const double2 *__restrict__ hb, int hstride,
         const double s = s_sh;
         const float2 sd = s_ds;
         SV *wr = w + (size_t)r * sw;
-        for (size_t p = (size_t)bx * kGivensThreads + tid; p < N; p += (size_t)nbs * kGivensThreads)
-            wr[p] = ScaleOp<SV>::apply(wr[p], s, sd.x, sd.y);
+        // four nodes per round, all loads issued first
+        const size_t stride = (size_t)nbs * kGivensThreads;
+        size_t p = (size_t)bx * kGivensThreads + tid;
+        for (; p + 3 * stride < N; p += 4 * stride) {
+            const SV a0 = wr[p], a1 = wr[p + stride], a2 = wr[p + 2 * stride], a3 = wr[p + 3 * stride];
+            wr[p] = ScaleOp<SV>::apply(a0, s, sd.x, sd.y);
+            wr[p + stride] = ScaleOp<SV>::apply(a1, s, sd.x, sd.y);
+            wr[p + 2 * stride] = ScaleOp<SV>::apply(a2, s, sd.x, sd.y);
+            wr[p + 3 * stride] = ScaleOp<SV>::apply(a3, s, sd.x, sd.y);
+        }
+        for (; p < N; p += stride) wr[p] = ScaleOp<SV>::apply(wr[p], s, sd.x, sd.y);
         return;
     }
     const int r = (int)lin;
