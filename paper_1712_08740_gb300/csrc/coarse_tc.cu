@@ -15,11 +15,12 @@
 // Ainv is split and laid out once per model (launch_coarse_tc_tiles) in
 // blocks of 128 rows x 32 columns, four planes (re_hi, re_lo, im_hi, im_lo)
 // in the K-major core-matrix order the MMA reads, so one cp.async.bulk copy
-// stages a CTA's 64 KB of Ainv. CTA (kc, rt, jt) takes rows 128 rt.., columns
+// stages 64 KB of Ainv. For chunk kc a CTA takes rows 128 rt.., columns
 // 32 kc.. and sources 64 jt..; it splits its slice of R into shared memory,
 // issues 48 MMAs into two TMEM accumulators (real, imaginary: 128 lanes x 64
-// columns each), and writes its partial product. k_coarse_tc_sum adds the
-// n/32 partials in chunk order. Each output element's arithmetic depends on
+// columns each). A CTA walks a group of consecutive chunks (about one CTA per
+// SM), accumulating in TMEM, and writes its partial product;
+// k_coarse_tc_sum adds the partials in group order. Each output element's arithmetic depends on
 // n only (one source's column never mixes with another's), so batched and
 // single solves agree bitwise.
 #include "helm_internal.cuh"
@@ -48,11 +49,12 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
 }
 
+// two stages: the Ainv copy of the next chunk lands while this chunk's MMAs run
 struct alignas(1024) TcSmem {
-    float a[4][kAPlane];    // re_hi, re_lo, im_hi, im_lo of the Ainv block
-    float b[4][kBPlane];    // re_hi, re_lo, im_hi, im_lo of the R slice (row = source)
-    uint64_t abar, mbar;    // Ainv block landed; MMAs complete
-    uint32_t tmem;          // TMEM base address
+    float a[2][4][kAPlane];    // re_hi, re_lo, im_hi, im_lo of an Ainv block, per stage
+    float b[2][4][kBPlane];    // re_hi, re_lo, im_hi, im_lo of an R slice (row = source), per stage
+    uint64_t abar[2], mbar[2]; // per stage: Ainv block landed; the stage's MMAs complete
+    uint32_t tmem;             // TMEM base address
     int abort;
 };
 
@@ -100,6 +102,7 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
 
 struct TcGeom {
     int n, nrt, nkc, Mp, nsb;   // order, row blocks, column chunks, padded rows, source blocks
+    int kch, nkg;               // chunks per CTA (accumulated in TMEM), CTA column groups
 };
 
 inline TcGeom tc_geom(int n, int nb) {
@@ -109,6 +112,10 @@ inline TcGeom tc_geom(int n, int nb) {
     g.nkc = (n + kK - 1) / kK;
     g.Mp = g.nrt * kM;
     g.nsb = (nb + kN - 1) / kN;
+    // about one CTA per SM per block of sources; depends on n only, so the
+    // order of every sum is fixed by n
+    g.kch = (g.nrt * g.nkc + 151) / 152;
+    g.nkg = (g.nkc + g.kch - 1) / g.kch;
     return g;
 }
 
@@ -129,22 +136,40 @@ __global__ void k_coarse_tc_tiles(const float2 *__restrict__ At, TcGeom G, float
     blk[3 * kAPlane + o] = v.y - ih;
 }
 
-// part[((kc * 2 + plane) * nb + source) * Mp + row]: chunk kc's share of Z
-__global__ void __launch_bounds__(kThreads, 2)
+// part[((kg * 2 + plane) * nb + source) * Mp + row]: the share of Z of
+// column group kg (chunks kg * kch .. kg * kch + kch - 1, accumulated in TMEM).
+//
+// Chunk i of the group uses stage i % 2. Each stage has its own "landed" and
+// "MMAs done" barriers, completing once per use of the stage (phase i / 2),
+// and each phase is waited for before the next use of that stage is issued,
+// so no wait can find its barrier two phases ahead.
+__global__ void __launch_bounds__(kThreads, 1)
 k_coarse_tc(const float *__restrict__ tiles, TcGeom G, const float2 *__restrict__ R, size_t sr,
             float *__restrict__ part, int nb, const int *__restrict__ active) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(tc_raw);
-    const int kc = blockIdx.x, rt = blockIdx.y, jt = blockIdx.z;
+    const int kg = blockIdx.x, rt = blockIdx.y, jt = blockIdx.z;
+    const int c0 = kg * G.kch, c1 = min(c0 + G.kch, G.nkc);
+    const int nch = c1 - c0;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const unsigned abytes = 4u * kAPlane * sizeof(float);
+    unsigned issued[2] = {0u, 0u};   // Ainv copies issued per stage (thread 0)
+    auto copy_a = [&](int i) {       // thread 0: Ainv block of chunk c0 + i into stage i % 2
+        const int st = i & 1;
+        pipe::mbar_arrive_expect_tx(&S.abar[st], abytes);
+        pipe::bulk_load(&S.a[st][0][0], tiles + (size_t)(rt * G.nkc + c0 + i) * 4 * kAPlane, abytes,
+                        &S.abar[st]);
+        ++issued[st];
+    };
     if (t == 0) {
-        pipe::mbar_init(&S.abar, 1);
-        pipe::mbar_init(&S.mbar, 1);
+        for (int st = 0; st < 2; ++st) {
+            pipe::mbar_init(&S.abar[st], 1);
+            pipe::mbar_init(&S.mbar[st], 1);
+        }
         S.abort = 0;
         pipe::mbar_init_fence();
-        const unsigned bytes = 4u * kAPlane * sizeof(float);
-        pipe::mbar_arrive_expect_tx(&S.abar, bytes);
-        pipe::bulk_load(&S.a[0][0], tiles + (size_t)(rt * G.nkc + kc) * 4 * kAPlane, bytes, &S.abar);
+        copy_a(0);
+        if (nch > 1) copy_a(1);
     }
     __syncwarp();
     if (warp == 0) {
@@ -154,64 +179,93 @@ k_coarse_tc(const float *__restrict__ tiles, TcGeom G, const float2 *__restrict_
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // this CTA's slice of R, split into TF32 hi and lo planes
-    for (int idx = t; idx < kN * kK; idx += kThreads) {
-        const int j = idx / kK, k = idx % kK;
-        const int src = jt * kN + j, col = kc * kK + k;
-        float2 v = make_float2(0.f, 0.f);
-        if (src < nb && col < G.n && (!active || active[src])) v = R[(size_t)src * sr + col];
-        const int o = cm_off(j, k);
-        const float rh = tf32_hi(v.x), ih = tf32_hi(v.y);
-        S.b[0][o] = rh;
-        S.b[1][o] = v.x - rh;
-        S.b[2][o] = ih;
-        S.b[3][o] = v.y - ih;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> MMA reads
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = S.tmem;
-    if (t == 0) {
-        if (pipe::mbar_wait(&S.abar, 0, &S.abort)) {
-            // D f32, A and B tf32, both K-major, N = 64, M = 128; bit 14 negates B
-            const uint32_t idp = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                                 ((uint32_t)(kM >> 4) << 24);
-            const uint32_t idn = idp | (1u << 14);
-            const uint32_t dr = tmem, di = tmem + kN;
-            constexpr unsigned lbo = 128, sbo = (kK / 4) * 128;
+    static_assert(kN == 8 * (kThreads / 32) && kK == 32, "one source per four lanes, eight groups of four columns");
+    const int src_j = jt * kN + 8 * warp + (lane >> 2);
+    const bool use_j = src_j < nb && (!active || active[src_j]);
+    for (int i = 0; i < nch; ++i) {
+        const int st = i & 1, kc = c0 + i;
+        const unsigned ph = (unsigned)(i >> 1) & 1u;
+        // stage st was last read by the MMAs of chunk i - 2
+        if (i >= 2 && !pipe::mbar_wait_drain(&S.mbar[st], ph ^ 1u)) S.abort = 1;
+        tc_fence_after();
+        // this chunk's slice of R, split into TF32 hi and lo planes. Thread
+        // (warp w, lane l) owns source j = 8 w + l / 4 and columns 4 g + l % 4,
+        // g = 0..7: all eight loads are issued first, and each warp's stores
+        // cover 32 consecutive floats of a plane (one core-matrix row group)
+        {
+            float2 v[kK / 4];
+            const size_t base = (size_t)src_j * sr + (size_t)kc * kK + (lane & 3);
 #pragma unroll
-            for (int s = 0; s < kK / 8; ++s) {
-                uint64_t a[4], b[4];
+            for (int g = 0; g < kK / 4; ++g) {
+                v[g] = make_float2(0.f, 0.f);
+                if (use_j && kc * kK + 4 * g + (lane & 3) < G.n) v[g] = R[base + 4 * g];
+            }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    a[q] = smem_desc(&S.a[q][s * 64], lbo, sbo);
-                    b[q] = smem_desc(&S.b[q][s * 64], lbo, sbo);
-                }
-                const uint32_t acc = s > 0;
-                // Zr += Ar Rr - Ai Ri
-                mma_tf32(dr, a[0], b[0], idp, acc);
-                mma_tf32(dr, a[0], b[1], idp, 1);
-                mma_tf32(dr, a[1], b[0], idp, 1);
-                mma_tf32(dr, a[2], b[2], idn, 1);
-                mma_tf32(dr, a[2], b[3], idn, 1);
-                mma_tf32(dr, a[3], b[2], idn, 1);
-                // Zi += Ai Rr + Ar Ri
-                mma_tf32(di, a[2], b[0], idp, acc);
-                mma_tf32(di, a[2], b[1], idp, 1);
-                mma_tf32(di, a[3], b[0], idp, 1);
-                mma_tf32(di, a[0], b[2], idp, 1);
-                mma_tf32(di, a[0], b[3], idp, 1);
-                mma_tf32(di, a[1], b[2], idp, 1);
+            for (int g = 0; g < kK / 4; ++g) {
+                const int o = (warp * (kK / 4) + g) * 32 + lane;   // = cm_off(8 w + l / 4, 4 g + l % 4)
+                const float rh = tf32_hi(v[g].x), ih = tf32_hi(v[g].y);
+                S.b[st][0][o] = rh;
+                S.b[st][1][o] = v[g].x - rh;
+                S.b[st][2][o] = ih;
+                S.b[st][3][o] = v[g].y - ih;
             }
         }
-        // arrives once the MMAs issued above (if any) have completed
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         pipe::smem_addr(&S.mbar))
-                     : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> MMA reads
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0) {
+            const uint32_t tmem = S.tmem;
+            if (pipe::mbar_wait(&S.abar[st], ph, &S.abort)) {
+                // D f32, A and B tf32, both K-major, N = 64, M = 128; bit 14 negates B
+                const uint32_t idp = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                                     ((uint32_t)(kM >> 4) << 24);
+                const uint32_t idn = idp | (1u << 14);
+                const uint32_t dr = tmem, di = tmem + kN;
+                constexpr unsigned lbo = 128, sbo = (kK / 4) * 128;
+#pragma unroll
+                for (int s = 0; s < kK / 8; ++s) {
+                    uint64_t a[4], b[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        a[q] = smem_desc(&S.a[st][q][s * 64], lbo, sbo);
+                        b[q] = smem_desc(&S.b[st][q][s * 64], lbo, sbo);
+                    }
+                    const uint32_t acc = (i > 0 || s > 0) ? 1u : 0u;
+                    // Zr += Ar Rr - Ai Ri
+                    mma_tf32(dr, a[0], b[0], idp, acc);
+                    mma_tf32(dr, a[0], b[1], idp, 1);
+                    mma_tf32(dr, a[1], b[0], idp, 1);
+                    mma_tf32(dr, a[2], b[2], idn, 1);
+                    mma_tf32(dr, a[2], b[3], idn, 1);
+                    mma_tf32(dr, a[3], b[2], idn, 1);
+                    // Zi += Ai Rr + Ar Ri
+                    mma_tf32(di, a[2], b[0], idp, acc);
+                    mma_tf32(di, a[2], b[1], idp, 1);
+                    mma_tf32(di, a[3], b[0], idp, 1);
+                    mma_tf32(di, a[0], b[2], idp, 1);
+                    mma_tf32(di, a[0], b[3], idp, 1);
+                    mma_tf32(di, a[1], b[2], idp, 1);
+                }
+            }
+            // arrives once the MMAs issued so far (if any) have completed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             pipe::smem_addr(&S.mbar[st]))
+                         : "memory");
+            // refill the other stage with chunk i + 1 once chunk i - 1's MMAs
+            // have read it (chunk 1 was issued up front)
+            if (i >= 1 && i + 1 < nch) {
+                const int so = st ^ 1;
+                if (pipe::mbar_wait(&S.mbar[so], (unsigned)((i - 1) >> 1) & 1u, &S.abort)) copy_a(i + 1);
+            }
+        }
+        __syncwarp();
     }
-    __syncwarp();
-    if (!pipe::mbar_wait_drain(&S.mbar, 0)) S.abort = 1;
+    const uint32_t tmem = S.tmem;
+    {
+        const int il = nch - 1;
+        if (!pipe::mbar_wait_drain(&S.mbar[il & 1], (unsigned)(il >> 1) & 1u)) S.abort = 1;
+    }
     __syncthreads();   // every thread sees the same abort word
     tc_fence_after();
     // warps 0-3 read the real accumulator, 4-7 the imaginary one; warp w sees
@@ -221,22 +275,25 @@ k_coarse_tc(const float *__restrict__ tiles, TcGeom G, const float2 *__restrict_
     tmem_ld64(tmem + ((uint32_t)(32 * qtr) << 16) + (uint32_t)(plane * kN), v);
     const int row = rt * kM + 32 * qtr + lane;
     const bool bad = S.abort != 0;
-    float *dst = part + ((size_t)(kc * 2 + plane) * nb + (size_t)jt * kN) * G.Mp + row;
-    const int nc = min(kN, nb - jt * kN);   // padding columns are not stored
+    float *dst = part + ((size_t)(kg * 2 + plane) * nb + (size_t)jt * kN) * G.Mp + row;
+    const int ncol = min(kN, nb - jt * kN);   // padding columns are not stored
 #pragma unroll
     for (int c = 0; c < kN; ++c)
-        if (c < nc) dst[(size_t)c * G.Mp] = bad ? __int_as_float(0x7fc00000) : __uint_as_float(v[c]);
+        if (c < ncol) dst[(size_t)c * G.Mp] = bad ? __int_as_float(0x7fc00000) : __uint_as_float(v[c]);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                      : "memory");
-    // after an abort, wait (bounded) for the Ainv copy before the CTA exits
-    if (t == 0 && bad) pipe::mbar_wait_drain(&S.abar, 0);
+    // after an abort, wait (bounded) for the last Ainv copy of each stage before the CTA exits
+    if (t == 0 && bad)
+        for (int st = 0; st < 2; ++st)
+            if (issued[st]) pipe::mbar_wait_drain(&S.abar[st], (issued[st] - 1) & 1u);
 }
 
-// Z[source][row] = sum over chunks kc, in chunk order, of the partials
+// Z[source][row] = sum over column groups kg, in group order, of the partials
+// (eight groups' loads in flight at a time)
 __global__ void __launch_bounds__(256)
 k_coarse_tc_sum(const float *__restrict__ part, TcGeom G, float2 *__restrict__ Z, size_t sz, int nb,
                 const int *__restrict__ active) {
@@ -245,10 +302,23 @@ k_coarse_tc_sum(const float *__restrict__ part, TcGeom G, float2 *__restrict__ Z
     const size_t plane = (size_t)nb * G.Mp;
     const float *p = part + (size_t)src * G.Mp + row;
     float re = 0.f, im = 0.f;
-#pragma unroll 8
-    for (int kc = 0; kc < G.nkc; ++kc) {
-        re += p[(size_t)(2 * kc) * plane];
-        im += p[(size_t)(2 * kc + 1) * plane];
+    int kg = 0;
+    for (; kg + 8 <= G.nkg; kg += 8) {
+        float a[8], b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            a[u] = p[(size_t)(2 * (kg + u)) * plane];
+            b[u] = p[(size_t)(2 * (kg + u) + 1) * plane];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            re += a[u];
+            im += b[u];
+        }
+    }
+    for (; kg < G.nkg; ++kg) {
+        re += p[(size_t)(2 * kg) * plane];
+        im += p[(size_t)(2 * kg + 1) * plane];
     }
     Z[(size_t)src * sz + row] = make_float2(re, im);
 }
@@ -262,7 +332,7 @@ size_t coarse_tc_tile_floats(int n) {
 
 size_t coarse_tc_part_floats(int n, int nb) {
     const TcGeom g = tc_geom(n, nb);
-    return (size_t)g.nkc * 2 * nb * g.Mp;
+    return (size_t)g.nkg * 2 * nb * g.Mp;
 }
 
 void launch_coarse_tc_tiles(const float2 *At, int n, float *tiles, cudaStream_t st) {
@@ -280,7 +350,7 @@ void launch_coarse_tc(const float *tiles, int n, const float2 *r, size_t sr, flo
     (void)once;
     const TcGeom g = tc_geom(n, nb);
     prof_begin(st);
-    k_coarse_tc<<<dim3(g.nkc, g.nrt, g.nsb), kThreads, sizeof(TcSmem), st>>>(tiles, g, r, sr, part,
+    k_coarse_tc<<<dim3(g.nkg, g.nrt, g.nsb), kThreads, sizeof(TcSmem), st>>>(tiles, g, r, sr, part,
                                                                                    nb, active);
     k_coarse_tc_sum<<<dim3((n + 255) / 256, nb), 256, 0, st>>>(part, g, z, sz, nb, active);
     count_launch(2);
