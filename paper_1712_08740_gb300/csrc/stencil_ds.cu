@@ -81,18 +81,47 @@ __device__ __forceinline__ dsf add_pairs(dsf s, dsf t) {
     return ds_norm({u.h, (s.l + t.l) + u.l});
 }
 
-// Neighbour of node p along one axis, scaled by the boundary factor: the
-// mirrored ghost of the absorbing boundary doubles the inner neighbour at
-// the first and last node, and the missing outer neighbour contributes 0.
-__device__ __forceinline__ float2 nbr(const float2 *__restrict__ z, size_t q, bool exists, bool twice) {
+// Scaled neighbour values: the mirrored ghost of the absorbing boundary
+// doubles the inner neighbour at the first and last node of an axis, and the
+// missing outer neighbour contributes 0.
+__device__ __forceinline__ float2 scaled(float2 v, bool exists, bool twice) {
     if (!exists) return make_float2(0.f, 0.f);
-    const float2 v = z[q];
     return twice ? make_float2(2.f * v.x, 2.f * v.y) : v;
 }
 
-// One block covers (part of) a row of the grid with one node per thread; the
-// grid's y dimension strides over rows (y, z), its z dimension over
-// right-hand sides.
+// w_p = d_p z_p - (1/h^2) sum_nbr, double-single; the neighbour sums are exact
+// as unevaluated pairs: x pair + y pair (+ z pair)
+template <int DIM>
+__device__ __forceinline__ float4 node_out(float2 zp, float2 xa, float2 xb, float2 ya, float2 yb, float2 za,
+                                           float2 zb, float4 d, dsf ih) {
+    dsf sr = two_sum(xa.x, xb.x), si = two_sum(xa.y, xb.y);
+    if (DIM >= 2) {
+        sr = add_pairs(sr, two_sum(ya.x, yb.x));
+        si = add_pairs(si, two_sum(ya.y, yb.y));
+    } else {
+        sr = ds_norm(sr);
+        si = ds_norm(si);
+    }
+    if (DIM == 3) {
+        sr = add_pairs(sr, ds_norm(two_sum(za.x, zb.x)));
+        si = add_pairs(si, ds_norm(two_sum(za.y, zb.y)));
+    }
+    const dsf dre = {d.x, d.y}, dim_ = {d.z, d.w};
+    // d z
+    const dsf ar = ds_add(ds_mul_f(dre, zp.x), ds_mul_f(dim_, -zp.y));
+    const dsf ai = ds_add(ds_mul_f(dre, zp.y), ds_mul_f(dim_, zp.x));
+    // (1/h^2) sum
+    const dsf br = ds_mul(ih, sr), bi = ds_mul(ih, si);
+    const dsf wr = ds_add(ar, {-br.h, -br.l});
+    const dsf wi = ds_add(ai, {-bi.h, -bi.l});
+    return make_float4(wr.h, wr.l, wi.h, wi.l);
+}
+
+// One thread per pair of x-adjacent nodes (ix0, ix0 + 1) of a row: the pair
+// shares its x-neighbour loads (four for two nodes) and index arithmetic.
+// Blocks of whole warps span a row's pairs; the grid's y dimension strides
+// over rows (y, z), its z dimension over right-hand sides. Indices are 32-bit
+// (a right-hand side has fewer than 2^31 nodes).
 template <int DIM>
 __global__ void __launch_bounds__(512)
 k_apply_H_ds(LevelView<double> L, const float4 *__restrict__ hd, float ihh, float ihl,
@@ -104,48 +133,63 @@ k_apply_H_ds(LevelView<double> L, const float4 *__restrict__ hd, float ihh, floa
     w += r * sw;
     const int nx = L.nx, ny = L.ny;
     const int rows = L.ny * L.nz;
-    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ix >= nx) return;
+    const int ix0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (ix0 >= nx) return;
+    const int ix1 = ix0 + 1;
+    const bool two = ix1 < nx;
     const dsf ih = {ihh, ihl};
-    const bool xw = ix > 0, xe = ix < nx - 1;
+    const float2 zero = make_float2(0.f, 0.f);
     for (int row = blockIdx.y; row < rows; row += gridDim.y) {
-        const size_t p = (size_t)row * nx + ix;
-        const float2 zp = z[p];
-        // neighbour sums, exact as unevaluated pairs: x pair + y pair (+ z pair)
-        dsf sr, si;
-        {
-            const float2 a = nbr(z, p - 1, xw, !xe), b = nbr(z, p + 1, xe, !xw);
-            sr = two_sum(a.x, b.x);
-            si = two_sum(a.y, b.y);
-        }
+        const unsigned p = (unsigned)row * (unsigned)nx + (unsigned)ix0;
+        // x: z[p-1], z[p], z[p+1], z[p+2]
+        const float2 zl = ix0 > 0 ? z[p - 1] : zero;
+        const float2 za_ = z[p];
+        const float2 zb_ = two ? z[p + 1] : zero;
+        const float2 zr = ix1 + 1 < nx ? z[p + 2] : zero;
+        float2 ya0 = zero, yb0 = zero, ya1 = zero, yb1 = zero;
         if (DIM >= 2) {
             const int iy = DIM == 3 ? row % ny : row;
             const bool ys = iy > 0, yn = iy < ny - 1;
-            const float2 a = nbr(z, p - nx, ys, !yn), b = nbr(z, p + nx, yn, !ys);
-            sr = add_pairs(sr, two_sum(a.x, b.x));
-            si = add_pairs(si, two_sum(a.y, b.y));
-        } else {
-            sr = ds_norm(sr);
-            si = ds_norm(si);
+            if (ys) {
+                ya0 = z[p - nx];
+                if (two) ya1 = z[p + 1 - nx];
+            }
+            if (yn) {
+                yb0 = z[p + nx];
+                if (two) yb1 = z[p + 1 + nx];
+            }
+            ya0 = scaled(ya0, ys, !yn);
+            yb0 = scaled(yb0, yn, !ys);
+            ya1 = scaled(ya1, ys, !yn);
+            yb1 = scaled(yb1, yn, !ys);
         }
+        float2 za0 = zero, zb0 = zero, za1 = zero, zb1 = zero;
         if (DIM == 3) {
             const int iz = row / ny;
-            const size_t sl = (size_t)nx * ny;
-            const bool zb = iz > 0, zf = iz < L.nz - 1;
-            const float2 a = nbr(z, p - sl, zb, !zf), b = nbr(z, p + sl, zf, !zb);
-            sr = add_pairs(sr, ds_norm(two_sum(a.x, b.x)));
-            si = add_pairs(si, ds_norm(two_sum(a.y, b.y)));
+            const unsigned sl = (unsigned)nx * (unsigned)ny;
+            const bool zbk = iz > 0, zfw = iz < L.nz - 1;
+            if (zbk) {
+                za0 = z[p - sl];
+                if (two) za1 = z[p + 1 - sl];
+            }
+            if (zfw) {
+                zb0 = z[p + sl];
+                if (two) zb1 = z[p + 1 + sl];
+            }
+            za0 = scaled(za0, zbk, !zfw);
+            zb0 = scaled(zb0, zfw, !zbk);
+            za1 = scaled(za1, zbk, !zfw);
+            zb1 = scaled(zb1, zfw, !zbk);
         }
-        const float4 d = hd[p];
-        const dsf dre = {d.x, d.y}, dim_ = {d.z, d.w};
-        // d z
-        const dsf ar = ds_add(ds_mul_f(dre, zp.x), ds_mul_f(dim_, -zp.y));
-        const dsf ai = ds_add(ds_mul_f(dre, zp.y), ds_mul_f(dim_, zp.x));
-        // (1/h^2) sum
-        const dsf br = ds_mul(ih, sr), bi = ds_mul(ih, si);
-        const dsf wr = ds_add(ar, {-br.h, -br.l});
-        const dsf wi = ds_add(ai, {-bi.h, -bi.l});
-        w[p] = make_float4(wr.h, wr.l, wi.h, wi.l);
+        const float4 d0 = hd[p];
+        const float4 d1 = two ? hd[p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // node ix0: left z[p-1], right z[p+1]
+        w[p] = node_out<DIM>(za_, scaled(zl, ix0 > 0, ix0 == nx - 1), scaled(zb_, two, ix0 == 0), ya0, yb0,
+                             za0, zb0, d0, ih);
+        // node ix1: left z[p], right z[p+2]
+        if (two)
+            w[p + 1] = node_out<DIM>(zb_, scaled(za_, true, ix1 == nx - 1), scaled(zr, ix1 + 1 < nx, false),
+                                     ya1, yb1, za1, zb1, d1, ih);
     }
 }
 
@@ -165,8 +209,8 @@ void launch_apply_H_ds(const LevelView<double> &L, const float4 *hd, const float
     const float ihh = (float)ih;                    // nearest float; ih - ihh is exact in FP64
     const float ihl = (float)(ih - (double)ihh);
     const int rows = L.ny * L.nz;
-    // blocks of whole warps spanning a row: 401 nodes -> 416 threads
-    const int wpr = (L.nx + 31) / 32, bpr = (wpr + 15) / 16;
+    // blocks of whole warps spanning a row's node pairs: 401 nodes -> 201 pairs -> 224 threads
+    const int wpr = ((L.nx + 1) / 2 + 31) / 32, bpr = (wpr + 15) / 16;
     const int bx = 32 * ((wpr + bpr - 1) / bpr);
     const dim3 g(bpr, rows < 65535 ? rows : 65535, nb);
     prof_begin(st);
