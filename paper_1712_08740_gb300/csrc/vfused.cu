@@ -227,14 +227,15 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
             }
         }
     }
-    // u = wj D^-1 b (first Jacobi sweep from zero) on the whole box
-    auto put_u = [&](int t, CB braw, C di) {
+    // u = wj D^-1 b (first Jacobi sweep from zero) on the whole box; b goes to
+    // shared memory only for the halo (own children keep it in registers)
+    auto put_u = [&](int t, CB braw, C di, bool keep_b) {
         const C bp = cvt<C>(braw);
         C up;
         up.x = wj * fmaT(di.x, bp.x, -(di.y * bp.y));
         up.y = wj * fmaT(di.x, bp.y, di.y * bp.x);
         su_[t] = up;
-        sb_[t] = bp;
+        if (keep_b) sb_[t] = bp;
         return up;
     };
 #pragma unroll
@@ -243,7 +244,7 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
         if (hidx < NH) {
             int lx, ly, lz;
             shell_pos<DIM, UX, UY, UZ, 2, 1>(hidx, lx, ly, lz);
-            if (in_f(X0 + lx, Y0 + ly, Z0 + lz)) put_u((lz * UY + ly) * UX + lx, bh[k], dh[k]);
+            if (in_f(X0 + lx, Y0 + ly, Z0 + lz)) put_u((lz * UY + ly) * UX + lx, bh[k], dh[k], true);
         }
     }
 #pragma unroll
@@ -253,12 +254,12 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
                   z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
         if (in_f(x, y, z)) {
             const int t = ((z - Z0) * UY + (y - Y0)) * UX + (x - X0);
-            u[(size_t)z * fxy + (size_t)y * F.nx + x] = put_u(t, bq[k], dq[k]);
+            u[(size_t)z * fxy + (size_t)y * F.nx + x] = put_u(t, bq[k], dq[k], false);
         }
     }
     __syncthreads();
     // r = (1 - wj) b + (1/h^2) sum_nbr c u_nbr on the r box
-    auto put_r = [&](int lx, int ly, int lz) {
+    auto put_r = [&](int lx, int ly, int lz, C bp) {
         const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
         const int q = (lz * UY + ly) * UX + lx;
         T sx = 0, sy = 0;
@@ -270,12 +271,12 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
             if (INT || z > 0) { const T c = (!INT && z == F.nz - 1) ? T(2) : T(1); sx = fmaT(c, su_[q - UX * UY].x, sx); sy = fmaT(c, su_[q - UX * UY].y, sy); }
             if (INT || z < F.nz - 1) { const T c = (!INT && z == 0) ? T(2) : T(1); sx = fmaT(c, su_[q + UX * UY].x, sx); sy = fmaT(c, su_[q + UX * UY].y, sy); }
         }
-        const C bp = sb_[q];
         const T omw = T(1) - wj;
         C o;
         o.x = fmaT(F.inv_h2, sx, omw * bp.x);
         o.y = fmaT(F.inv_h2, sy, omw * bp.y);
         sr_[q] = o;
+        return o;
     };
     for (int hidx = threadIdx.x; hidx < NR; hidx += TL::NT) {
         int lx, ly, lz;
@@ -283,14 +284,21 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
         ++lx;
         ++ly;
         if (DIM == 3) ++lz;
-        if (in_f(X0 + lx, Y0 + ly, Z0 + lz)) put_r(lx, ly, lz);
+        if (in_f(X0 + lx, Y0 + ly, Z0 + lz)) put_r(lx, ly, lz, sb_[(lz * UY + ly) * UX + lx]);
     }
+    // in interior 2D blocks with one thread per coarse node, the thread's own
+    // four children are four of its nine restriction taps: keep their r
+    constexpr bool RREG = DIM == 2 && QP == 1 && INT;
+    C ro[RREG ? NQL : 1];
 #pragma unroll
     for (int k = 0; k < NQL; ++k) {
         const int q = q0 + k * QP;
         const int x = 2 * (I0 + tx) + (q & 1), y = 2 * (J0 + ty) + ((q >> 1) & 1),
                   z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
-        if (in_f(x, y, z)) put_r(x - X0, y - Y0, z - Z0);
+        if (in_f(x, y, z)) {
+            const C o = put_r(x - X0, y - Y0, z - Z0, cvt<C>(bq[k]));
+            if constexpr (RREG) ro[k] = o;
+        }
     }
     __syncthreads();
     // full weighting, one coarse node per thread: threads 0 .. SX SY SZ - 1
@@ -312,7 +320,13 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
             for (int ox = -1; ox <= 1; ++ox) {
                 const int lx = mirror_if<INT>(2 * I + ox, F.nx) - X0;
                 const T wgt = (ox == 0 ? T(0.5) : T(0.25)) * wy * wz;
-                const C v = sr_[(lz * UY + ly) * UX + lx];
+                C v;
+                if constexpr (RREG) {
+                    if (ox >= 0 && oy >= 0) v = ro[ox + 2 * oy];   // own child (2I + ox, 2J + oy)
+                    else v = sr_[(lz * UY + ly) * UX + lx];
+                } else {
+                    v = sr_[(lz * UY + ly) * UX + lx];
+                }
                 ax = fmaT(wgt, v.x, ax);
                 ay = fmaT(wgt, v.y, ay);
             }
