@@ -247,6 +247,11 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
             if (in_f(X0 + lx, Y0 + ly, Z0 + lz)) put_u((lz * UY + ly) * UX + lx, bh[k], dh[k], true);
         }
     }
+    // in interior 2D blocks with one thread per coarse node the thread keeps
+    // its four children's u and r in registers: two of each child's four u
+    // neighbours and four of the coarse node's nine restriction taps
+    constexpr bool RREG = DIM == 2 && QP == 1 && INT;
+    C uo[RREG ? NQL : 1];
 #pragma unroll
     for (int k = 0; k < NQL; ++k) {
         const int q = q0 + k * QP;
@@ -254,7 +259,9 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
                   z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
         if (in_f(x, y, z)) {
             const int t = ((z - Z0) * UY + (y - Y0)) * UX + (x - X0);
-            u[(size_t)z * fxy + (size_t)y * F.nx + x] = put_u(t, bq[k], dq[k], false);
+            const C up = put_u(t, bq[k], dq[k], false);
+            u[(size_t)z * fxy + (size_t)y * F.nx + x] = up;
+            if constexpr (RREG) uo[k] = up;
         }
     }
     __syncthreads();
@@ -286,18 +293,35 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
         if (DIM == 3) ++lz;
         if (in_f(X0 + lx, Y0 + ly, Z0 + lz)) put_r(lx, ly, lz, sb_[(lz * UY + ly) * UX + lx]);
     }
-    // in interior 2D blocks with one thread per coarse node, the thread's own
-    // four children are four of its nine restriction taps: keep their r
-    constexpr bool RREG = DIM == 2 && QP == 1 && INT;
     C ro[RREG ? NQL : 1];
 #pragma unroll
     for (int k = 0; k < NQL; ++k) {
         const int q = q0 + k * QP;
         const int x = 2 * (I0 + tx) + (q & 1), y = 2 * (J0 + ty) + ((q >> 1) & 1),
                   z = DIM == 3 ? 2 * (K0 + tz) + (q >> 2) : 0;
-        if (in_f(x, y, z)) {
-            const C o = put_r(x - X0, y - Y0, z - Z0, cvt<C>(bq[k]));
-            if constexpr (RREG) ro[k] = o;
+        if constexpr (RREG) {
+            // child (cx, cy) = (k & 1, k >> 1); the same multiply-adds in the
+            // same order as put_r (interior: every factor 1)
+            const int cx = k & 1, cy = k >> 1;
+            const int t = (y - Y0) * UX + (x - X0);
+            const C wv = cx ? uo[k - 1] : su_[t - 1];
+            const C ev = cx ? su_[t + 1] : uo[k + 1];
+            const C sv = cy ? uo[k - 2] : su_[t - UX];
+            const C nv = cy ? su_[t + UX] : uo[k + 2];
+            T sx = 0, sy = 0;
+            sx = fmaT(T(1), wv.x, sx); sy = fmaT(T(1), wv.y, sy);
+            sx = fmaT(T(1), ev.x, sx); sy = fmaT(T(1), ev.y, sy);
+            sx = fmaT(T(1), sv.x, sx); sy = fmaT(T(1), sv.y, sy);
+            sx = fmaT(T(1), nv.x, sx); sy = fmaT(T(1), nv.y, sy);
+            const C bp = cvt<C>(bq[k]);
+            const T omw = T(1) - wj;
+            C o;
+            o.x = fmaT(F.inv_h2, sx, omw * bp.x);
+            o.y = fmaT(F.inv_h2, sy, omw * bp.y);
+            sr_[t] = o;
+            ro[k] = o;
+        } else if (in_f(x, y, z)) {
+            put_r(x - X0, y - Y0, z - Z0, cvt<C>(bq[k]));
         }
     }
     __syncthreads();
