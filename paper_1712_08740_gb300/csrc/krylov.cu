@@ -451,7 +451,7 @@ inline int blocks_for(size_t N, int per_block, int cap) {
 void launch_multidot(const double2 *V, size_t sV, int nvec, const double2 *w, size_t sw,
                      size_t N, double2 *out, size_t out_stride, int nrhs, const int *active,
                      KrylovScratch &ks, cudaStream_t st) {
-    const int nb = sm_blocks_for(N, 2, ks.max_blocks);
+    const int nb = sm_blocks_for(N, 4, ks.max_blocks);
     prof_begin(st);
     k_multidot<<<dim3(nb, nrhs), kThreads, 0, st>>>(V, sV, nvec, w, sw, N, out, out_stride,
                                                     ks.partial, ks.counter, ks.nvec_max, active);
@@ -465,7 +465,7 @@ void launch_multidot_h(const double2 *V, size_t sV, int nvec, double2 *w, size_t
                        double2 *out, size_t out_stride, int nrhs, const int *active,
                        KrylovScratch &ks, const LevelView<double> &L, OpShift<double> sH,
                        const CZ *z, size_t sz, cudaStream_t st) {
-    const int nb = sm_blocks_for(N, 2, ks.max_blocks);
+    const int nb = sm_blocks_for(N, 4, ks.max_blocks);
     prof_begin(st);
     const dim3 g(nb, nrhs);
     if (L.dim == 1)
@@ -494,7 +494,7 @@ template void launch_multidot_h<float2>(const double2 *, size_t, int, double2 *,
 void launch_multiaxpy(const double2 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
                       double2 *w, size_t sw, size_t N, double *norm2, int nrhs,
                       const int *active, KrylovScratch &ks, cudaStream_t st) {
-    const int nb = sm_blocks_for(N, 2, ks.max_blocks);
+    const int nb = sm_blocks_for(N, 4, ks.max_blocks);
     prof_begin(st);
     k_multiaxpy<<<dim3(nb, nrhs), kThreads, 0, st>>>(V, sV, nvec, c, c_stride, w, sw, N, norm2,
                                                      (double *)ks.partial, ks.counter, active);
