@@ -147,14 +147,16 @@ def cpu_baseline(w, budget_s=12.0):
     times = []
     while True:
         t = time.perf_counter()
-        direct.lu_solve(w.n, w.h, m, om, w.alpha, f)
+        u_lu = direct.lu_solve(w.n, w.h, m, om, w.alpha, f)
         times.append(time.perf_counter() - t)
         if time.perf_counter() - t0 > budget_s or len(times) >= 20:
             break
     mean = sum(times) / len(times)
+    # "_u": the oracle's solution, for the GPU solution's error (not printed)
     return {"value": 1.0 / mean, "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(times)} full sparse-LU solves (SuperLU factor + solve, complex128, "
-                      f"single-threaded) of the same 401x201 system; mean {mean * 1e3:.1f} ms"}
+                      f"single-threaded) of the same 401x201 system; mean {mean * 1e3:.1f} ms",
+            "_u": np.asarray(u_lu).ravel()}
 
 
 def tune_summary(helm, dim, rep):
@@ -507,8 +509,13 @@ def main():
         del gx, Fx, Ux
 
     cpu = None
+    rel_err_lu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
+        # the last timed plain solve against the oracle's sparse-LU solution
+        u_lu = cpu.pop("_u")
+        u_gpu = ud.cpu().numpy().ravel()
+        rel_err_lu = float(np.linalg.norm(u_gpu - u_lu) / np.linalg.norm(u_lu))
 
     if rank == 0:
         line = {
@@ -522,6 +529,8 @@ def main():
                        "setup_ms": setup_ms, "tiles": tune_summary(helm, 2, tune_plain)},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "iterations": int(np.median(its_l)), "true_rel_residual_max": float(max(rr_l)),
+            "rel_err_vs_oracle_lu": rel_err_lu,
+            "unknown_iterations_per_s": float(N * np.median(its_l) * value),
             "clocks": clk,
             "e2e": {"value": e2e_v, "unit": "solves/s", "h2d_bytes_per_step": int(fh.numel() * 16),
                     "d2h_bytes_per_step": int(uh.numel() * 16),
@@ -530,7 +539,7 @@ def main():
             "roofline": roof,
             "kernels": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv)
                             for kk, vv in v.items()} for k, v in kern.items()},
-            "launches_per_solve": {k: v["launches"] for k, v in prof.items()},
+            "launches_per_batched_solve": {k: v["launches"] for k, v in prof.items()},
             "batched": batched,
             "batched_801x401_4freq": batched_multi,
             "serving": serving,
