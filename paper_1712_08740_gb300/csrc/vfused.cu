@@ -111,7 +111,8 @@ template <> struct Shapes<2> {
 };
 template <> struct Shapes<3> {
     using Down = std::tuple<Shape<8, 4, 4, 128, 1>, Shape<8, 8, 2, 128, 1>, Shape<4, 4, 4, 64, 1>,
-                            Shape<4, 4, 2, 256, 8>, Shape<8, 4, 4, 256, 2>, Shape<8, 8, 2, 256, 2>>;
+                            Shape<4, 4, 2, 256, 8>, Shape<8, 4, 4, 256, 2>, Shape<8, 8, 2, 256, 2>,
+                            Shape<8, 4, 4, 512, 4>, Shape<8, 8, 4, 512, 2>>;
     using Up = Down;
 };
 
