@@ -252,9 +252,9 @@ def run_reference(args, rank):
 
 def main():
     args = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1712_08740_gb300.replicas import max_over_ranks, rank_env, whole_job_rate
+    env = rank_env()
+    world, rank, local = env.world, env.rank, env.local
     if args.impl == "reference":
         run_reference(args, rank)
         return
@@ -322,11 +322,8 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(tot_ms, dist, dev)
+    value = whole_job_rate(args.steps, world, tot_ms)
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     fh = torch.from_numpy(f.ravel().copy()).pin_memory()
