@@ -417,7 +417,7 @@ def main():
             gb.solve_batch(BATCH_SOURCES, Fd, w.tol, Ud)
             prof = helm.helm_profile_stop()
             bkern = {}
-            for name, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:9]:
+            for name, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]:
                 gbs = v["bytes"] / v["ms"] / 1e6 if v["ms"] > 0 else 0.0
                 bkern[name] = {"launches": v["launches"], "ms": round(v["ms"], 3),
                               "us_per_launch": round(v["ms"] / v["launches"] * 1e3, 2),

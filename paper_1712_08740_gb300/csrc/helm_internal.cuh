@@ -197,15 +197,17 @@ void launch_make_dinv(const LevelView<double> &L, OpShift<double> s, C *dinv, cu
 
 // Fused V(1,1) level kernels for 2D/3D (vfused.cu). CB: type of the level's
 // right-hand side (complex128 basis vector at level 0 of the mixed form).
+// `finest` only names the launch for the profiler (level 0 is reported apart
+// from the coarser levels).
 template <typename T, typename CB>
 void launch_vdown(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB *b,
                   size_t sb, cplx_t<T> *u, size_t su, cplx_t<T> *bc, size_t sbc, int nb,
-                  const int *active, cudaStream_t st, int shape);
+                  const int *active, cudaStream_t st, int shape, bool finest = false);
 template <typename T, typename CB>
 void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
                 const cplx_t<T> *uin, size_t sin, const cplx_t<T> *ec, size_t sec, const CB *b,
                 size_t sb, cplx_t<T> *uout, size_t sout, int nb, const int *active,
-                cudaStream_t st, int shape);
+                cudaStream_t st, int shape, bool finest = false);
 // tile shapes of the fused kernels: count per dimension (down and up lists
 // have equal length) and the extents/threads of one (kernel 0 down, 1 up)
 int num_tile_shapes(int dim);

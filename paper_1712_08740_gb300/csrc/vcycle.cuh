@@ -108,7 +108,7 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
             C *bc = g->lv[l + 1].b.template as<C>();
             if (l == 0)
                 launch_vdown<T, CB0>(F, Cv, wj, b0, sb0, g->lv[0].t.template as<C>(), g->lv[0].N,
-                                     bc, g->lv[1].N, nb, act, st, tile_down(g, 0, nb));
+                                     bc, g->lv[1].N, nb, act, st, tile_down(g, 0, nb), true);
             else
                 launch_vdown<T, C>(F, Cv, wj, g->lv[l].b.template as<C>(), g->lv[l].N,
                                    g->lv[l].t.template as<C>(), g->lv[l].N, bc, g->lv[l + 1].N, nb,
@@ -123,7 +123,7 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
             const C *ec = g->lv[l + 1].u.template as<C>();
             if (l == 0)
                 launch_vup<T, CB0>(F, Cv, wj, g->lv[0].t.template as<C>(), g->lv[0].N, ec,
-                                   g->lv[1].N, b0, sb0, u0, su0, nb, act, st, tile_up(g, 0, nb));
+                                   g->lv[1].N, b0, sb0, u0, su0, nb, act, st, tile_up(g, 0, nb), true);
             else
                 launch_vup<T, C>(F, Cv, wj, g->lv[l].t.template as<C>(), g->lv[l].N, ec,
                                  g->lv[l + 1].N, g->lv[l].b.template as<C>(), g->lv[l].N,

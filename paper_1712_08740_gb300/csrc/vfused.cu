@@ -699,7 +699,7 @@ void prepare_vfused() {
 template <typename T, typename CB>
 void launch_vdown(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB *b,
                   size_t sb, cplx_t<T> *u, size_t su, cplx_t<T> *bc, size_t sbc, int nb,
-                  const int *active, cudaStream_t st, int shape) {
+                  const int *active, cudaStream_t st, int shape, bool finest) {
     prof_begin(st);
     if (F.dim == 2)
         down_sel<T, CB, 2>(shape, std::make_index_sequence<n_down<2>()>{}, F, Cv, wj, b, sb, u, su,
@@ -713,7 +713,7 @@ void launch_vdown(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB 
         // D^-1 once per launch (shared by the right-hand sides)
         const double n1 = (double)F.nx * F.ny * F.nz;
         const double nf = n1 * nb, nc = (double)Cv.nx * Cv.ny * Cv.nz * nb;
-        prof_end(sizeof(T) == 8 ? "vdown_f64" : "vdown_f32", st,
+        prof_end(sizeof(T) == 8 ? (finest ? "vdown_l0_f64" : "vdown_f64") : (finest ? "vdown_l0_f32" : "vdown_f32"), st,
                  nf * (sizeof(CB) + sizeof(cplx_t<T>)) + n1 * sizeof(cplx_t<T>) + nc * sizeof(cplx_t<T>),
                  sizeof(T) == 8 ? nf * 26.0 : 0.0);
     }
@@ -723,7 +723,7 @@ template <typename T, typename CB>
 void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
                 const cplx_t<T> *uin, size_t sin, const cplx_t<T> *ec, size_t sec, const CB *b,
                 size_t sb, cplx_t<T> *uout, size_t sout, int nb, const int *active,
-                cudaStream_t st, int shape) {
+                cudaStream_t st, int shape, bool finest) {
     prof_begin(st);
     if (F.dim == 2)
         up_sel<T, CB, 2>(shape, std::make_index_sequence<n_up<2>()>{}, F, Cv, wj, uin, sin, ec, sec, b,
@@ -737,7 +737,7 @@ void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
         // correction in; D^-1 once per launch
         const double n1 = (double)F.nx * F.ny * F.nz;
         const double nf = n1 * nb, nc = (double)Cv.nx * Cv.ny * Cv.nz * nb;
-        prof_end(sizeof(T) == 8 ? "vup_f64" : "vup_f32", st,
+        prof_end(sizeof(T) == 8 ? (finest ? "vup_l0_f64" : "vup_f64") : (finest ? "vup_l0_f32" : "vup_f32"), st,
                  nf * (2.0 * sizeof(cplx_t<T>) + sizeof(CB)) + n1 * sizeof(cplx_t<T>) + nc * sizeof(cplx_t<T>),
                  sizeof(T) == 8 ? nf * 24.0 : 0.0);
     }
@@ -746,11 +746,11 @@ void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
 #define HELM_INST_V(T, CB)                                                                      \
     template void launch_vdown<T, CB>(const LevelView<T> &, const LevelView<T> &, T,             \
                                       const CB *, size_t, cplx_t<T> *, size_t, cplx_t<T> *,     \
-                                      size_t, int, const int *, cudaStream_t, int);             \
+                                      size_t, int, const int *, cudaStream_t, int, bool);       \
     template void launch_vup<T, CB>(const LevelView<T> &, const LevelView<T> &, T,               \
                                     const cplx_t<T> *, size_t, const cplx_t<T> *, size_t,       \
                                     const CB *, size_t, cplx_t<T> *, size_t, int, const int *,  \
-                                    cudaStream_t, int);
+                                    cudaStream_t, int, bool);
 HELM_INST_V(double, double2)
 HELM_INST_V(float, float2)
 HELM_INST_V(float, double2)
