@@ -407,6 +407,53 @@ def test_double_single_batch_equals_single(helm):
         assert its == its_b[k] and np.array_equal(Ub[k], uk.cpu().numpy())
 
 
+def test_more_than_64_sources_batch_equals_single(helm):
+    """70 sources: the tensor-core coarse product takes them in two blocks of
+    64 (the second partly filled); every source still equals its single solve."""
+    w = workload("2d_smooth_small")
+    from workloads import point_sources
+    ns = 70
+    xs = [1 + (k * 97) // (ns - 1) for k in range(ns)]
+    F = np.stack([point_sources(w.n, w.h, [(x, 2 + (k % 5))]).ravel() for k, x in enumerate(xs)])
+    g = helm.Grid(w.n, w.h, restart=30, precision="mixed_ds")
+    g.set_model(dev(w.slowness()), w.omega(), w.alpha)
+    g.set_shift(*w.beta)
+    Fd = dev(F)
+    Ud = torch.empty_like(Fd)
+    _, its_b, rr_b = g.solve_batch(ns, Fd, 1e-8, Ud)
+    assert (rr_b <= 1e-8).all()
+    Ub = Ud.cpu().numpy().reshape(ns, -1)
+    for k in (0, 63, 64, 69):
+        fk = dev(F[k])
+        uk = torch.empty_like(fk)
+        _, its, rr = g.solve(fk, 1e-8, uk)
+        assert its == its_b[k] and np.array_equal(Ub[k], uk.cpu().numpy())
+
+
+def test_double_single_basis_on_a_large_grid(helm):
+    """513 x 321 nodes: the double-single multi-dot keeps more per-warp partials
+    per vector than the other reductions (161 chunks x 8 warps); the solve
+    agrees with the complex128-basis solve and meets the residual bound."""
+    from workloads import point_sources, smooth_random
+    n, h = (513, 321), 10.0
+    c = smooth_random(n, h, seed=4)
+    m = (1.0 / c).ravel()
+    f = point_sources(n, h, [(256, 2)]).ravel()
+    out = {}
+    for prec in ("mixed", "mixed_ds"):
+        g = helm.Grid(n, h, restart=30, precision=prec)
+        g.set_model(dev(m), 2 * np.pi * 10.0, 0.01)
+        g.set_shift(1.0, 0.5)
+        fd = dev(f)
+        ud = torch.empty_like(fd)
+        _, its, rr = g.solve(fd, 1e-8, ud)
+        assert rr <= 1e-8
+        out[prec] = (ud.cpu().numpy(), its)
+        g.close()
+    assert abs(out["mixed"][1] - out["mixed_ds"][1]) <= 2
+    assert rel(out["mixed_ds"][0], out["mixed"][0]) < 1e-9
+
+
 @pytest.mark.parametrize("precision", ["f64", "mixed", "mixed_ds"])
 def test_partial_cycle_update_ignores_unfilled_columns(helm, precision):
     """A cycle that ends before `restart` steps (iteration cap or convergence)
