@@ -101,7 +101,15 @@ __global__ void k_make_dinv(LevelView<double> L, OpShift<double> s, C *__restric
 // latency rather than issue rate bounds the kernel).
 template <int X, int Y, int Z, int NT_, int QP_> struct Shape {
     static constexpr int SX = X, SY = Y, SZ = Z, NT = NT_, QP = QP_;
+    static constexpr bool MARCH = false;
     static_assert(X * Y * Z * QP_ == NT_, "QP threads per coarse node");
+};
+// 3D down kernel that marches along z: a block takes X x Y coarse nodes in x, y
+// and KC consecutive coarse planes, one thread per coarse (x, y) node, and
+// walks the fine planes in order with rings of planes in shared memory.
+template <int X, int Y, int KC> struct ZShape {
+    static constexpr int SX = X, SY = Y, SZ = KC, NT = X * Y, QP = 1;
+    static constexpr bool MARCH = true;
 };
 template <int DIM> struct Shapes;
 template <> struct Shapes<2> {
@@ -112,8 +120,10 @@ template <> struct Shapes<2> {
 template <> struct Shapes<3> {
     using Down = std::tuple<Shape<8, 4, 4, 128, 1>, Shape<8, 8, 2, 128, 1>, Shape<4, 4, 4, 64, 1>,
                             Shape<4, 4, 2, 256, 8>, Shape<8, 4, 4, 256, 2>, Shape<8, 8, 2, 256, 2>,
-                            Shape<8, 4, 4, 512, 4>, Shape<8, 8, 4, 512, 2>>;
-    using Up = Down;
+                            Shape<8, 4, 4, 512, 4>, Shape<8, 8, 4, 512, 2>, ZShape<16, 8, 16>>;
+    using Up = std::tuple<Shape<8, 4, 4, 128, 1>, Shape<8, 8, 2, 128, 1>, Shape<4, 4, 4, 64, 1>,
+                          Shape<4, 4, 2, 256, 8>, Shape<8, 4, 4, 256, 2>, Shape<8, 8, 2, 256, 2>,
+                          Shape<8, 4, 4, 512, 4>, Shape<8, 8, 4, 512, 2>, Shape<4, 4, 4, 128, 2>>;
 };
 
 // Halo shells. A block's local box has U = (UX, UY, UZ) nodes per axis; its
@@ -552,9 +562,209 @@ k_up(LevelView<T> F, LevelView<T> Cv, T wj, const cplx_t<T> *__restrict__ uin,
     else up_tile<T, CB, DIM, TL, false>(F, Cv, wj, uin, sin, ec, sec, b, sb, uout, sout, active);
 }
 
+// ---------------------------------------------------------------- 3D down, marching along z
+// The same arithmetic as the 3D k_down (u = wj D^-1 b, r with the neighbours
+// in the order x-, x+, y-, y+, z-, z+, full weighting with the 27 taps in the
+// order z, y, x), so its results equal every other 3D shape's bit for bit.
+// The block keeps three planes of u, two of b and three of r (its x, y box of
+// (2 SX + 3) x (2 SY + 3) fine nodes) in shared memory and walks the fine
+// planes 2 K0 - 2 .. 2 K1 in order: u of plane z, then r of plane z - 1, then
+// the restriction of coarse plane K once r of 2K - 1, 2K and 2K + 1 exist.
+// The loads of the next plane are issued before the current plane is used.
+template <typename T, typename CB, typename TL, bool INT>
+__device__ __forceinline__ void down_zm_tile(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
+                                             const CB *__restrict__ b, size_t sb,
+                                             cplx_t<T> *__restrict__ u, size_t su,
+                                             cplx_t<T> *__restrict__ bc, size_t sbc) {
+    using C = cplx_t<T>;
+    constexpr int SX = TL::SX, SY = TL::SY, KC = TL::SZ, NT = TL::NT;
+    constexpr int UX = 2 * SX + 3, UY = 2 * SY + 3, UP = UX * UY;
+    constexpr int NH = shell_count<2, UX, UY, 1, 2, 1>();
+    constexpr int HP = (NH + NT - 1) / NT;
+    constexpr int RX = UX - 2, RY = UY - 2;
+    constexpr int NR = shell_count<2, RX, RY, 1, 1, 0>();
+    const int gz = (Cv.nz + KC - 1) / KC;
+    const int bz = blockIdx.z % gz;
+    const int I0 = blockIdx.x * SX, J0 = blockIdx.y * SY, K0 = bz * KC, K1 = min(K0 + KC, Cv.nz);
+    const int X0 = 2 * I0 - 2, Y0 = 2 * J0 - 2;
+    const int tx = threadIdx.x % SX, ty = threadIdx.x / SX;
+    const int nz = F.nz;
+    const size_t fxy = (size_t)F.nx * F.ny;
+    extern __shared__ unsigned char smem_raw[];
+    C *su_ = reinterpret_cast<C *>(smem_raw);   // u, planes z mod 3
+    C *sb_ = su_ + 3 * UP;                        // b, planes z mod 2
+    C *sr_ = sb_ + 2 * UP;                        // r, planes z mod 3
+    auto in_xy = [&](int x, int y) { return INT || (x >= 0 && x < F.nx && y >= 0 && y < F.ny); };
+    const int zs = max(0, 2 * K0 - 2), ze = min(nz - 1, 2 * K1);
+    const int zr_lo = max(0, 2 * K0 - 1), zr_hi = min(nz - 1, 2 * K1 - 1);
+    CB bq[4], bh[HP], bq2[4], bh2[HP];
+    C dq[4], dh[HP], dq2[4], dh2[HP];
+    auto load_plane = [&](int z, CB (&pb)[4], C (&pd)[4], CB (&hb)[HP], C (&hd)[HP]) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int x = 2 * (I0 + tx) + (k & 1), y = 2 * (J0 + ty) + (k >> 1);
+            if (in_xy(x, y)) {
+                const size_t p = (size_t)z * fxy + (size_t)y * F.nx + x;
+                pb[k] = b[p];
+                pd[k] = F.dinv[p];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < HP; ++k) {
+            const int hidx = threadIdx.x + k * NT;
+            if (hidx < NH) {
+                int lx, ly, lz;
+                shell_pos<2, UX, UY, 1, 2, 1>(hidx, lx, ly, lz);
+                const int x = X0 + lx, y = Y0 + ly;
+                if (in_xy(x, y)) {
+                    const size_t p = (size_t)z * fxy + (size_t)y * F.nx + x;
+                    hb[k] = b[p];
+                    hd[k] = F.dinv[p];
+                }
+            }
+        }
+    };
+    auto put_u = [&](C *sup, C *sbp, int t, CB braw, C di) {
+        const C bp = cvt<C>(braw);
+        C up;
+        up.x = wj * fmaT(di.x, bp.x, -(di.y * bp.y));
+        up.y = wj * fmaT(di.x, bp.y, di.y * bp.x);
+        sup[t] = up;
+        sbp[t] = bp;
+        return up;
+    };
+    auto put_r = [&](int lx, int ly, int zr, const C *um, const C *uc, const C *upl, const C *sbp, C *srp) {
+        const int x = X0 + lx, y = Y0 + ly;
+        const int q = ly * UX + lx;
+        T sx = 0, sy = 0;
+        if (INT || x > 0) { const T c = (!INT && x == F.nx - 1) ? T(2) : T(1); sx = fmaT(c, uc[q - 1].x, sx); sy = fmaT(c, uc[q - 1].y, sy); }
+        if (INT || x < F.nx - 1) { const T c = (!INT && x == 0) ? T(2) : T(1); sx = fmaT(c, uc[q + 1].x, sx); sy = fmaT(c, uc[q + 1].y, sy); }
+        if (INT || y > 0) { const T c = (!INT && y == F.ny - 1) ? T(2) : T(1); sx = fmaT(c, uc[q - UX].x, sx); sy = fmaT(c, uc[q - UX].y, sy); }
+        if (INT || y < F.ny - 1) { const T c = (!INT && y == 0) ? T(2) : T(1); sx = fmaT(c, uc[q + UX].x, sx); sy = fmaT(c, uc[q + UX].y, sy); }
+        if (zr > 0) { const T c = (zr == nz - 1) ? T(2) : T(1); sx = fmaT(c, um[q].x, sx); sy = fmaT(c, um[q].y, sy); }
+        if (zr < nz - 1) { const T c = (zr == 0) ? T(2) : T(1); sx = fmaT(c, upl[q].x, sx); sy = fmaT(c, upl[q].y, sy); }
+        const C bp = sbp[q];
+        const T omw = T(1) - wj;
+        C o;
+        o.x = fmaT(F.inv_h2, sx, omw * bp.x);
+        o.y = fmaT(F.inv_h2, sy, omw * bp.y);
+        srp[q] = o;
+    };
+    load_plane(zs, bq, dq, bh, dh);
+    for (int zu = zs; zu <= ze + 1; ++zu) {
+        // the next plane's loads go out before this plane is used
+        const bool more = zu + 1 <= ze;
+        if (more) load_plane(zu + 1, bq2, dq2, bh2, dh2);
+        if (zu <= ze) {
+            C *sup = su_ + (zu % 3) * UP, *sbp = sb_ + (zu & 1) * UP;
+#pragma unroll
+            for (int k = 0; k < HP; ++k) {
+                const int hidx = threadIdx.x + k * NT;
+                if (hidx < NH) {
+                    int lx, ly, lz;
+                    shell_pos<2, UX, UY, 1, 2, 1>(hidx, lx, ly, lz);
+                    if (in_xy(X0 + lx, Y0 + ly)) put_u(sup, sbp, ly * UX + lx, bh[k], dh[k]);
+                }
+            }
+            const bool own = zu >= 2 * K0 && zu < 2 * K1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = 2 * (I0 + tx) + (k & 1), y = 2 * (J0 + ty) + (k >> 1);
+                if (in_xy(x, y)) {
+                    const C up = put_u(sup, sbp, (y - Y0) * UX + (x - X0), bq[k], dq[k]);
+                    if (own) u[(size_t)zu * fxy + (size_t)y * F.nx + x] = up;
+                }
+            }
+        }
+        __syncthreads();
+        const int zr = zu - 1;
+        if (zr >= zr_lo && zr <= zr_hi) {
+            const C *um = su_ + ((zr + 2) % 3) * UP, *uc = su_ + (zr % 3) * UP, *upl = su_ + ((zr + 1) % 3) * UP;
+            const C *sbp = sb_ + (zr & 1) * UP;
+            C *srp = sr_ + (zr % 3) * UP;
+            for (int hidx = threadIdx.x; hidx < NR; hidx += NT) {
+                int lx, ly, lz;
+                shell_pos<2, RX, RY, 1, 1, 0>(hidx, lx, ly, lz);
+                ++lx;
+                ++ly;
+                if (in_xy(X0 + lx, Y0 + ly)) put_r(lx, ly, zr, um, uc, upl, sbp, srp);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = 2 * (I0 + tx) + (k & 1), y = 2 * (J0 + ty) + (k >> 1);
+                if (in_xy(x, y)) put_r(x - X0, y - Y0, zr, um, uc, upl, sbp, srp);
+            }
+        }
+        __syncthreads();
+        // coarse plane K once r of 2K - 1, 2K, 2K + 1 (mirrored at the ends) exists
+        int K = -1;
+        if (zr >= 1 && (zr & 1) && zr <= zr_hi) K = (zr - 1) >> 1;
+        else if (zr == nz - 1 && !(zr & 1)) K = zr >> 1;
+        if (K >= K0 && K < K1) {
+            const int I = I0 + tx, J = J0 + ty;
+            if (I < Cv.nx && J < Cv.ny) {
+                T ax = 0, ay = 0;
+#pragma unroll
+                for (int oz = -1; oz <= 1; ++oz) {
+                    const C *srp = sr_ + (mirror(2 * K + oz, nz) % 3) * UP;
+                    const T wz = oz == 0 ? T(0.5) : T(0.25);
+#pragma unroll
+                    for (int oy = -1; oy <= 1; ++oy) {
+                        const int ly = mirror_if<INT>(2 * J + oy, F.ny) - Y0;
+                        const T wy = oy == 0 ? T(0.5) : T(0.25);
+#pragma unroll
+                        for (int ox = -1; ox <= 1; ++ox) {
+                            const int lx = mirror_if<INT>(2 * I + ox, F.nx) - X0;
+                            const T wgt = (ox == 0 ? T(0.5) : T(0.25)) * wy * wz;
+                            const C v = srp[ly * UX + lx];
+                            ax = fmaT(wgt, v.x, ax);
+                            ay = fmaT(wgt, v.y, ay);
+                        }
+                    }
+                }
+                C o;
+                o.x = ax;
+                o.y = ay;
+                bc[(size_t)K * Cv.nx * Cv.ny + (size_t)J * Cv.nx + I] = o;
+            }
+        }
+        if (more) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                bq[k] = bq2[k];
+                dq[k] = dq2[k];
+            }
+#pragma unroll
+            for (int k = 0; k < HP; ++k) {
+                bh[k] = bh2[k];
+                dh[k] = dh2[k];
+            }
+        }
+    }
+}
+
+template <typename T, typename CB, typename TL>
+__global__ void __launch_bounds__(TL::NT)
+k_down_zm(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t sb,
+          cplx_t<T> *__restrict__ u, size_t su, cplx_t<T> *__restrict__ bc, size_t sbc,
+          const int *__restrict__ active) {
+    const int gz = (Cv.nz + TL::SZ - 1) / TL::SZ;
+    const int rr = blockIdx.z / gz;
+    if (active && !active[rr]) return;
+    b += rr * sb;
+    u += rr * su;
+    bc += rr * sbc;
+    // the x, y box spans fine [2 I0 - 2, 2 I0 + 2 S] (as k_down)
+    const int x0 = 2 * (int)blockIdx.x * TL::SX - 2, y0 = 2 * (int)blockIdx.y * TL::SY - 2;
+    const bool inside = x0 >= 0 && x0 + 2 * TL::SX + 2 <= F.nx - 1 && y0 >= 0 && y0 + 2 * TL::SY + 2 <= F.ny - 1;
+    if (inside) down_zm_tile<T, CB, TL, true>(F, Cv, wj, b, sb, u, su, bc, sbc);
+    else down_zm_tile<T, CB, TL, false>(F, Cv, wj, b, sb, u, su, bc, sbc);
+}
+
 template <int DIM, typename TL> constexpr size_t down_smem(size_t csz) {
     constexpr int UX = 2 * TL::SX + 3, UY = 2 * TL::SY + 3, UZ = DIM == 3 ? 2 * TL::SZ + 3 : 1;
-    return csz * 3 * UX * UY * UZ;
+    if constexpr (TL::MARCH) return csz * 8 * UX * UY;   // u: 3 planes, b: 2, r: 3
+    else return csz * 3 * UX * UY * UZ;
 }
 template <int DIM, typename TL> constexpr size_t up_smem(size_t csz) {
     constexpr int VX = 2 * TL::SX + 2, VY = 2 * TL::SY + 2, VZ = DIM == 3 ? 2 * TL::SZ + 2 : 1;
@@ -569,7 +779,12 @@ void down_impl(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB *b,
     const size_t sm = down_smem<DIM, TL>(sizeof(cplx_t<T>));
     const int gz = DIM == 3 ? (Cv.nz + TL::SZ - 1) / TL::SZ : 1;
     dim3 g((Cv.nx + TL::SX - 1) / TL::SX, (Cv.ny + TL::SY - 1) / TL::SY, gz * nb);
-    k_down<T, CB, DIM, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, b, sb, u, su, bc, sbc, active);
+    if constexpr (TL::MARCH) {
+        static_assert(DIM == 3, "marching tiles are 3D");
+        k_down_zm<T, CB, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, b, sb, u, su, bc, sbc, active);
+    } else {
+        k_down<T, CB, DIM, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, b, sb, u, su, bc, sbc, active);
+    }
 }
 
 template <typename T, typename CB, int DIM, typename TL>
@@ -604,13 +819,17 @@ void up_sel(int shape, std::index_sequence<I...>, const LevelView<T> &F, const L
      ...);
 }
 
+template <typename T, typename CB, int DIM, typename TL> void set_attr_down() {
+    const int sm = (int)down_smem<DIM, TL>(sizeof(cplx_t<T>));
+    if constexpr (TL::MARCH)
+        cudaFuncSetAttribute(k_down_zm<T, CB, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    else
+        cudaFuncSetAttribute(k_down<T, CB, DIM, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
 template <typename T, typename CB, int DIM, size_t... I>
 void set_attr_all(std::index_sequence<I...>) {
-    (cudaFuncSetAttribute(k_down<T, CB, DIM, std::tuple_element_t<I, typename Shapes<DIM>::Down>>,
-                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)down_smem<DIM, std::tuple_element_t<I, typename Shapes<DIM>::Down>>(
-                              sizeof(cplx_t<T>))),
-     ...);
+    (set_attr_down<T, CB, DIM, std::tuple_element_t<I, typename Shapes<DIM>::Down>>(), ...);
     (cudaFuncSetAttribute(k_up<T, CB, DIM, std::tuple_element_t<I, typename Shapes<DIM>::Up>>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)up_smem<DIM, std::tuple_element_t<I, typename Shapes<DIM>::Up>>(
