@@ -211,9 +211,11 @@ helm_status helm_true_residual_noalloc(helm_grid *g, int nrhs, const helm_c128 *
  * pre-smoothing, residual and restriction; "up": prolongation and
  * post-smoothing) are compiled for helm_num_tile_shapes(dim) shapes each
  * (0 for 1D). helm_tile_shape gives a shape's extents and block size: the
- * block's tile of coarse nodes (one thread per coarse node, each computing
- * the node's 2^d fine children), for both kernels. The arithmetic per node
- * does not depend on the shape:
+ * block's tile of coarse nodes, computed by `threads` threads (one, two, four
+ * or 2^d threads per coarse node share its 2^d fine children); for the 3D
+ * down kernel that marches along z (the last 3D down shape) the extents are
+ * x, y of the tile and the number of coarse planes a block walks, one thread
+ * per coarse (x, y) node. The arithmetic per node does not depend on the shape:
  * results are bitwise identical for every choice. helm_set_tiles /
  * helm_get_tiles set and read the shapes used on fine level `level` (the
  * pair level, level+1); -1 (the initial setting) selects the shape
