@@ -107,13 +107,19 @@ __device__ __forceinline__ float4 node_out(float2 zp, float2 xa, float2 xb, floa
         si = add_pairs(si, ds_norm(two_sum(za.y, zb.y)));
     }
     const dsf dre = {d.x, d.y}, dim_ = {d.z, d.w};
-    // d z
-    const dsf ar = ds_add(ds_mul_f(dre, zp.x), ds_mul_f(dim_, -zp.y));
-    const dsf ai = ds_add(ds_mul_f(dre, zp.y), ds_mul_f(dim_, zp.x));
-    // (1/h^2) sum
+    // w = (d z) - (1/h^2) sum as one three-term sum per part: the products
+    // d_re z_re, -d_im z_im (error-free, unnormalised) and -(1/h^2) sum; the
+    // leading parts are added with two two-sums, the rest folded in once
+    const dsf pr1 = ds_mul_f(dre, zp.x), pr2 = ds_mul_f(dim_, -zp.y);
+    const dsf pi1 = ds_mul_f(dre, zp.y), pi2 = ds_mul_f(dim_, zp.x);
     const dsf br = ds_mul(ih, sr), bi = ds_mul(ih, si);
-    const dsf wr = ds_add(ar, {-br.h, -br.l});
-    const dsf wi = ds_add(ai, {-bi.h, -bi.l});
+    auto sum3 = [](dsf a, dsf b, dsf c) {
+        const dsf s1 = two_sum(a.h, b.h);
+        const dsf s2 = two_sum(s1.h, -c.h);
+        return ds_norm({s2.h, ((a.l + b.l) - c.l) + (s1.l + s2.l)});
+    };
+    const dsf wr = sum3(pr1, pr2, br);
+    const dsf wi = sum3(pi1, pi2, bi);
     return make_float4(wr.h, wr.l, wi.h, wi.l);
 }
 
