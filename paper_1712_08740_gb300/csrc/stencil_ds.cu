@@ -36,13 +36,6 @@ __device__ __forceinline__ dsf ds_mul(dsf a, dsf b) {          // unnormalised
     e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
     return {p, e};
 }
-__device__ __forceinline__ dsf ds_add(dsf a, dsf b) {
-    const float s = a.h + b.h;
-    const float bb = s - a.h;
-    float e = (a.h - (s - bb)) + (b.h - bb);
-    e += a.l + b.l;
-    return ds_norm({s, e});
-}
 
 template <typename T> __device__ __forceinline__ T dsqrt(T v);
 template <> __device__ __forceinline__ double dsqrt<double>(double v) { return sqrt(v); }
@@ -75,11 +68,6 @@ __device__ __forceinline__ dsf two_sum(float a, float b) {
     const float bb = s - a;
     return {s, (a - (s - bb)) + (b - bb)};
 }
-// (s.h, s.l) + (t.h, t.l) for two exact pair sums; renormalised
-__device__ __forceinline__ dsf add_pairs(dsf s, dsf t) {
-    const dsf u = two_sum(s.h, t.h);
-    return ds_norm({u.h, (s.l + t.l) + u.l});
-}
 
 // Scaled neighbour values: the mirrored ghost of the absorbing boundary
 // doubles the inner neighbour at the first and last node of an axis, and the
@@ -94,17 +82,25 @@ __device__ __forceinline__ float2 scaled(float2 v, bool exists, bool twice) {
 template <int DIM>
 __device__ __forceinline__ float4 node_out(float2 zp, float2 xa, float2 xb, float2 ya, float2 yb, float2 za,
                                            float2 zb, float4 d, dsf ih) {
+    // cascade of two-sums over the neighbours (x-, x+, y-, y+, z-, z+): the
+    // leading part is exact, the errors are added once at the end; the pair
+    // is left unnormalised (the product with 1/h^2 below takes it as it is)
     dsf sr = two_sum(xa.x, xb.x), si = two_sum(xa.y, xb.y);
     if (DIM >= 2) {
-        sr = add_pairs(sr, two_sum(ya.x, yb.x));
-        si = add_pairs(si, two_sum(ya.y, yb.y));
-    } else {
-        sr = ds_norm(sr);
-        si = ds_norm(si);
-    }
-    if (DIM == 3) {
-        sr = add_pairs(sr, ds_norm(two_sum(za.x, zb.x)));
-        si = add_pairs(si, ds_norm(two_sum(za.y, zb.y)));
+        const dsf r2 = two_sum(sr.h, ya.x), i2 = two_sum(si.h, ya.y);
+        const dsf r3 = two_sum(r2.h, yb.x), i3 = two_sum(i2.h, yb.y);
+        float lr = (sr.l + r2.l) + r3.l, li = (si.l + i2.l) + i3.l;
+        float hr = r3.h, hi = i3.h;
+        if (DIM == 3) {
+            const dsf r4 = two_sum(hr, za.x), i4 = two_sum(hi, za.y);
+            const dsf r5 = two_sum(r4.h, zb.x), i5 = two_sum(i4.h, zb.y);
+            lr = (lr + r4.l) + r5.l;
+            li = (li + i4.l) + i5.l;
+            hr = r5.h;
+            hi = i5.h;
+        }
+        sr = {hr, lr};
+        si = {hi, li};
     }
     const dsf dre = {d.x, d.y}, dim_ = {d.z, d.w};
     // w = (d z) - (1/h^2) sum as one three-term sum per part: the products
