@@ -407,6 +407,28 @@ def test_double_single_batch_equals_single(helm):
         assert its == its_b[k] and np.array_equal(Ub[k], uk.cpu().numpy())
 
 
+def test_double_single_basis_with_a_long_restart(helm):
+    """FGMRES(64): up to 65 basis vectors per Gram-Schmidt pass (nine groups of
+    the streamed multi-dot, 65 coefficients per warp in the multi-axpy); the
+    double-single solve agrees with the complex128-basis one."""
+    w = workload("2d_smooth")
+    f = w.rhs().ravel()
+    out = {}
+    for prec in ("mixed", "mixed_ds"):
+        g = helm.Grid(w.n, w.h, restart=64, precision=prec)
+        g.set_model(dev(w.slowness()), w.omega(), w.alpha)
+        g.set_shift(*w.beta)
+        fd = dev(f)
+        ud = torch.empty_like(fd)
+        _, its, rr = g.solve(fd, 1e-8, ud)
+        assert rr <= 1e-8
+        out[prec] = (ud.cpu().numpy(), its)
+        g.close()
+    assert out["mixed"][1] > 31                      # the cycle did grow past 32 vectors
+    assert abs(out["mixed"][1] - out["mixed_ds"][1]) <= 2
+    assert rel(out["mixed_ds"][0], out["mixed"][0]) < 1e-9
+
+
 def test_more_than_64_sources_batch_equals_single(helm):
     """70 sources: the tensor-core coarse product takes them in two blocks of
     64 (the second partly filled); every source still equals its single solve."""
