@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default="plain", choices=["plain", "batched"],
+    ap.add_argument("--profile", default="plain", choices=["plain", "batched", "3d"],
                     help="region bracketed by cudaProfilerStart/Stop for ncu --profile-from-start "
                          "off: the plain timed solves, or one extra (untimed) solve of the "
                          "64-source batch with the double-single basis")
@@ -250,6 +250,35 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def profile_3d(helm, dev, stream):
+    """--profile 3d: only the 3D workload (tiles tuned, graphs warm), one
+    batched solve bracketed by cudaProfilerStart/Stop for ncu's launch list."""
+    import torch
+    from workloads import workload
+    wx = workload("3d_smooth")
+    mx = torch.from_numpy(wx.slowness().ravel().copy()).to(dev)
+    gx = helm.Grid(wx.n, wx.h, restart=wx.restart, precond=wx.precond, precision="mixed_ds")
+    gx.set_stream(stream.cuda_stream)
+    gx.set_model(mx, wx.omega(), wx.alpha)
+    gx.set_shift(*wx.beta)
+    Fx = torch.from_numpy(np.stack([wx.rhs(k).ravel() for k in range(len(wx.sources))])).to(dev)
+    Ux = torch.empty_like(Fx)
+    gx.autotune(Fx.shape[0], None, wx.tol, tiles=True, smoother=False)
+    gx.solve_batch(Fx.shape[0], Fx, wx.tol, Ux)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.cudart().cudaProfilerStart()
+    e0.record(stream)
+    _, itx, rrx = gx.solve_batch(Fx.shape[0], Fx, wx.tol, Ux)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"profile": "3d", "grid": list(wx.n), "sources": int(Fx.shape[0]),
+                      "solve_ms": e0.elapsed_time(e1), "iterations_max": int(itx.max()),
+                      "true_rel_residual_max": float(rrx.max())}), flush=True)
+    gx.close()
+
+
 def main():
     args = parse()
     from paper_1712_08740_gb300.replicas import max_over_ranks, rank_env, whole_job_rate
@@ -268,6 +297,10 @@ def main():
     __graft_entry__.build()
     from paper_1712_08740_gb300 import helm
     from workloads import point_sources, workload
+
+    if args.profile == "3d":
+        profile_3d(helm, dev, torch.cuda.current_stream(dev))
+        return
 
     w = workload("2d_smooth")
     m = w.slowness()
@@ -489,8 +522,12 @@ def main():
         t_setup = time.perf_counter() - t
         Fx = torch.from_numpy(np.stack([wx.rhs(k).ravel() for k in range(len(wx.sources))])).to(dev)
         Ux = torch.empty_like(Fx)
-        if name == "1d_well":
-            gx.solve_batch(Fx.shape[0], Fx, wx.tol, Ux)       # warm (graph capture)
+        tune_x = None
+        if wx.precond == "mg":
+            # set-up, untimed: tile shapes per level for this grid and batch
+            tune_x = gx.autotune(Fx.shape[0], None, wx.tol, tiles=True, smoother=False)
+        gx.solve_batch(Fx.shape[0], Fx, wx.tol, Ux)           # warm (graph capture)
+        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         _, itx, rrx = gx.solve_batch(Fx.shape[0], Fx, wx.tol, Ux)
@@ -502,7 +539,8 @@ def main():
                        "setup_ms": t_setup * 1e3, "solve_ms": ms,
                        "solves_per_s": Fx.shape[0] / (ms / 1e3),
                        "iterations_max": int(itx.max()), "true_rel_residual_max": float(rrx.max()),
-                       "unknown_iterations_per_s": float(wx.unknowns * itx.sum() / (ms / 1e3))}
+                       "unknown_iterations_per_s": float(wx.unknowns * itx.sum() / (ms / 1e3)),
+                       "autotune": tune_summary(helm, len(wx.n), tune_x) if tune_x else None}
         del gx, Fx, Ux
 
     cpu = None
