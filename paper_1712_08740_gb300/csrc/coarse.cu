@@ -325,8 +325,6 @@ void prepare_coarse_kernels() {
     const int big = 100 * 1024;
     cudaFuncSetAttribute(k_coarse_gemm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_coarse_gemm<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_coarse_gemm<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_coarse_gemm<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     done = true;
 }
 
@@ -362,8 +360,6 @@ template void launch_assemble_dense<double>(const LevelView<double> &, OpShift<d
                                             cudaStream_t);
 template void launch_gauss_jordan<float>(float2 *, float2 *, int, cudaStream_t);
 template void launch_gauss_jordan<double>(double2 *, double2 *, int, cudaStream_t);
-template void launch_dense_gemv<float>(const float2 *, int, const float2 *, size_t, float2 *,
-                                       size_t, int, const int *, void *, unsigned *, cudaStream_t);
 template void launch_dense_gemv<double>(const double2 *, int, const double2 *, size_t, double2 *,
                                         size_t, int, const int *, void *, unsigned *, cudaStream_t);
 template void launch_transpose_square<float>(float2 *, int, cudaStream_t);

@@ -233,7 +233,7 @@ template <typename T>
 void launch_assemble_dense(const LevelView<T> &L, OpShift<T> s, cplx_t<T> *A, cudaStream_t st);
 template <typename T>
 void launch_gauss_jordan(cplx_t<T> *A, cplx_t<T> *colbuf, int n, cudaStream_t st);
-// z = Ainv r for nb right-hand sides
+// z = Ainv r for nb right-hand sides (complex128; the complex64 product is launch_coarse_tc)
 template <typename T>
 void launch_dense_gemv(const cplx_t<T> *At, int n, const cplx_t<T> *r, size_t sr,
                        cplx_t<T> *z, size_t sz, int nb, const int *active, void *part,
