@@ -146,6 +146,25 @@ def test_vcycle_mixed_close_to_oracle(helm):
     assert rel(z.cpu().numpy(), mg.vcycle(levels, r, 1, 1, 0.8)) < 2e-4
 
 
+def test_single_level_complex64_coarse_solve(helm):
+    """A grid no larger than coarse_max has one level: the complex64
+    preconditioner is the coarse solve alone (FP32 Gauss-Jordan inverse,
+    tensor-core product on a TF32 hi/lo split). It matches M^-1 r to FP32
+    accuracy (cond(M) ~ 160 here: ~1.4e-6 for an FP32 inverse); TF32 without
+    the split would be ~1e-3 off."""
+    n, h, om, al = (33, 17), 10.0, 2 * np.pi * 10.0, 0.01
+    m = rand_model(n, 9)
+    g = helm.Grid(n, h, precision="mixed")
+    g.set_model(dev(m), om, al)
+    g.set_shift(1.0, 0.5)
+    assert g.num_levels == 1
+    r = rand_c(33 * 17, 10)
+    z = torch.empty(len(r), dtype=torch.complex128, device=DEV)
+    g.apply_precond(dev(r), z)
+    M = op.assemble_M(n, h, m, om, al, 1.0, 0.5)
+    assert rel(z.cpu().numpy(), direct.spla.splu(M.tocsc()).solve(r)) < 2e-5
+
+
 def test_exact_precond_is_M_inverse(helm):
     n, h, om, al = (61,), 5.0, 2 * np.pi * 10.0, 0.01
     m = rand_model(n, 9)
