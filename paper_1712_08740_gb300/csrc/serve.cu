@@ -78,43 +78,64 @@ size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o)
     const int m = o.restart;
     const double zsz = (o.precond == HELM_PRECOND_NONE) ? 0.0 : (o.precision == HELM_PREC_F64 ? 16.0 : 8.0);
     const double csz = (o.precision == HELM_PREC_F64) ? 16.0 : 8.0;
-    // coarsest level size by the same rule as the hierarchy
+    // level sizes by the same rule as the hierarchy
     int c[3] = {n[0], n[1], n[2]};
-    double levels_sum = 0.0;
-    while (true) {
+    double level_N[32];
+    int nlev = 0;
+    while (nlev < 32) {
         const double Nl = (double)c[0] * c[1] * c[2];
-        levels_sum += Nl;
+        level_N[nlev++] = Nl;
         bool odd = true;
         for (int a = 0; a < dim; ++a) odd = odd && c[a] >= 3 && (c[a] % 2) == 1;
         if (o.precond != HELM_PRECOND_MG || Nl <= o.coarse_max || !odd) break;
         for (int a = 0; a < dim; ++a) c[a] = (c[a] + 1) / 2;
     }
     const double nc = (double)c[0] * c[1] * c[2];
+    // every device buffer as the solver allocates it; the driver hands out
+    // large allocations in whole 2 MiB pages
     double b = 0.0;
-    b += nrhs * (m + 1.0) * N * 16.0;                    // basis V
-    b += nrhs * (double)m * N * zsz;                     // preconditioned vectors Z
-    b += 4.0 * nrhs * levels_sum * csz;                  // V-cycle work vectors
-    b += levels_sum * (8.0 + 8.0 + 4.0 + csz);           // slowness, coefficients, 1/diag(M)
+    auto add = [&](double bytes) {
+        const double page = 2.0 * 1024 * 1024;
+        b += bytes > page / 2 ? std::ceil(bytes / page) * page : bytes;
+    };
+    add(nrhs * (m + 1.0) * N * 16.0);                    // basis V
+    if (zsz > 0.0) add(nrhs * (double)m * N * zsz);      // preconditioned vectors Z
+    for (int l = 0; l < nlev; ++l) {                     // per level of the hierarchy
+        const double Nl = level_N[l];
+        for (int k = 0; k < 4; ++k) add(nrhs * Nl * csz);  // V-cycle work vectors
+        add(Nl * 8.0);                                   // slowness
+        add(Nl * 8.0);                                   // coefficient (FP64)
+        add(Nl * 4.0);                                   // coefficient (FP32)
+        add(Nl * csz);                                   // 1/diag(M)
+    }
     if (o.precond != HELM_PRECOND_NONE) {
-        b += nc * nc * csz + nc * csz;                   // coarse inverse
+        add(nc * nc * csz);                              // coarse inverse
+        add(nc * csz);                                   // Gauss-Jordan column
         double part = (double)coarse_part_elems((int)nc, nrhs) * csz;
         if (csz == 8.0) {
             // complex64: TF32 tensor-core tiles of the inverse and their partial products
-            b += (double)coarse_tc_tile_floats((int)nc) * 4.0;
+            add((double)coarse_tc_tile_floats((int)nc) * 4.0);
             part = std::max(part, (double)coarse_tc_part_floats((int)nc, nrhs) * 4.0);
         }
-        b += part + coarse_tickets((int)nc, nrhs) * 4.0;
+        add(part);
+        add(coarse_tickets((int)nc, nrhs) * 4.0);
     }
-    b += 2.0 * nrhs * N * 16.0;                          // staging of host f and u
-    if (o.precision == HELM_PREC_MIXED_DS) b += nrhs * N * 16.0;   // complex128 residuals
-    b += (double)nrhs * (m + 1.0) * (m + 1.0) * 16.0 * 3.0;   // Hessenberg, rotations
+    add(nrhs * N * 16.0);                                // staging of host f
+    add(nrhs * N * 16.0);                                // staging of host u
+    if (o.precision == HELM_PREC_MIXED_DS) {
+        add(nrhs * N * 16.0);                            // complex128 residuals
+        add(N * 16.0);                                   // diagonal of H, double-single
+    }
+    add((double)nrhs * (m + 1.0) * m * 16.0);            // rotated Hessenberg R
+    add((double)nrhs * (m + 1.0) * (m + 1.0) * 16.0);    // rotation product Q
+    add((double)nrhs * 2.0 * (m + 1.0) * 16.0);          // Hessenberg column buffer
     {
         double per_rhs = (m + 1.0) * kMaxBlocks;         // reduction partials
         if (o.precision == HELM_PREC_MIXED_DS)
             per_rhs = std::max(per_rhs, (double)ds_partial_per_rhs((size_t)N, m + 1));
-        b += (double)nrhs * per_rhs * 16.0;
+        add((double)nrhs * per_rhs * 16.0);
     }
-    b += 1 << 20;                                        // small buffers
+    b += 4.0 * 1024 * 1024;                              // small buffers and captured graphs
     return (size_t)b;
 }
 

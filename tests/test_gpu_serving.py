@@ -68,6 +68,44 @@ def test_results_same_alone_and_in_the_mix(helm, precision):
     assert np.linalg.norm(alone[1][0] - u_lu.ravel()) <= 1e-6 * np.linalg.norm(u_lu)
 
 
+@pytest.mark.parametrize("precision,nrhs", [("f64", 1), ("mixed", 4), ("mixed_ds", 8)])
+def test_footprint_bounds_the_memory_a_solve_holds(helm, precision, nrhs):
+    """Admission relies on helm_solve_footprint: it must not be below the
+    device memory a grid actually holds after a batched solve (model,
+    hierarchy, coarse inverse and its tensor-core tiles, basis, scratch,
+    captured graphs)."""
+    n, h = (257, 129), 10.0
+    from workloads import point_sources, smooth_random
+    m = (1.0 / smooth_random(n, h, seed=11)).ravel()
+    F = np.stack([point_sources(n, h, [(20 + 25 * k, 2)]).ravel() for k in range(nrhs)])
+    o = helm.helm_default_options()
+    o.precision = {"f64": 0, "mixed": 1, "mixed_ds": 2}[precision]
+    fp = helm.helm_solve_footprint(2, n, nrhs, o)
+    Fd = torch.from_numpy(F).cuda()
+    Ud = torch.empty_like(Fd)
+
+    def one_grid():
+        g = helm.Grid(n, h, precision=precision)
+        g.set_model(m, 2 * np.pi * 10.0, 0.01)
+        g.set_shift(1.0, 0.5)
+        _, its, rr = g.solve_batch(nrhs, Fd, 1e-8, Ud)
+        torch.cuda.synchronize()
+        return g, rr
+
+    # a first grid of the same kind loads the kernels' code (lazy module
+    # loading is a one-time cost of the process, not of a grid)
+    g, _ = one_grid()
+    g.close()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    g, rr = one_grid()
+    free1, _ = torch.cuda.mem_get_info()
+    held = free0 - free1
+    assert (rr <= 1e-8).all()
+    assert held <= fp, (held, fp)
+    g.close()
+
+
 def test_admission_by_memory_budget(helm):
     # three requests on one grid size: their footprints differ by little, so a
     # budget of 1.2 x the largest holds one of them but never two
