@@ -317,8 +317,11 @@ typedef struct {
 } helm_result;
 
 /* Device bytes a solve of nrhs right-hand sides on an n grid holds under `opt`
- * (an upper estimate: basis x restart, multigrid work vectors, coefficients,
- * coarse inverse, staging). 0 on bad arguments. */
+ * (an upper estimate: each buffer the solver allocates -- basis x restart,
+ * multigrid work vectors and coefficients, coarse inverse and its tensor-core
+ * tiles, staging, Hessenberg and reduction scratch -- rounded up to 2 MiB
+ * allocation pages, plus a margin for small buffers and captured graphs).
+ * 0 on bad arguments. */
 size_t helm_solve_footprint(int dim, const int64_t n[3], int nrhs, const helm_options *opt);
 
 /* Creates the server on the current device and starts its threads.
