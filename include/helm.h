@@ -149,6 +149,17 @@ helm_status helm_solve(helm_grid *g, const helm_c128 *f, double tol, helm_c128 *
 helm_status helm_solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double tol,
                              helm_c128 *u, int *iterations, double *true_rel_residual);
 
+/* As helm_solve_batch, but restarted FGMRES starts from the initial guess x0
+ * that u holds on entry instead of from 0 (Eq. 7 with x0 given; e.g. the
+ * solution of the same source at the previous frequency of a sweep). u:
+ * nrhs x N complex values, read as x0 and overwritten by the solution; host
+ * or device. The stopping test stays ||f - H u||_2 / ||f||_2 <= tol; a
+ * right-hand side whose x0 already meets it returns x0 with 0 iterations,
+ * and one with f = 0 returns u = 0. Errors as helm_solve_batch, with
+ * HELM_ERR_NONFINITE also for a non-finite x0. */
+helm_status helm_solve_batch_warm(helm_grid *g, int nrhs, const helm_c128 *f, double tol,
+                                  helm_c128 *u, int *iterations, double *true_rel_residual);
+
 /* Eq. 3: y = H x on the fine grid (x, y: N complex values, host or device,
  * not overlapping). Errors: HELM_ERR_STATE, HELM_ERR_ARG, HELM_ERR_CUDA. */
 helm_status helm_apply_H(helm_grid *g, const helm_c128 *x, helm_c128 *y);

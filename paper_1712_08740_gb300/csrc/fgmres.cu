@@ -326,7 +326,7 @@ helm_status workspace_for(helm_grid *g, int nrhs) { return ensure_workspace(g, n
 
 // Core solver on device arrays f (nrhs x N) and u (nrhs x N), stride N.
 helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, double2 *u,
-                         int *iterations, double *relres_out) {
+                         int *iterations, double *relres_out, bool warm) {
     helm_status s;
     if ((s = ensure_ready(g))) return s;
     if ((s = ensure_workspace(g, nrhs))) return s;
@@ -347,22 +347,37 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
     if (graphs && (s = capture_steps(g, nrhs, tol))) return s;
     g->last_nrhs = nrhs;
 
-    // non-finite input check, x = 0, v_0 = f, ||f||, flags
+    // non-finite input check, x = x0 (0 unless warm), ||f||, r_0 = f - H x0, flags
     int *flag = g->flag.as<int>();
     cudaMemsetAsync(flag, 0, sizeof(int), st);
     launch_finite_check((const double *)f, 2 * N * (size_t)nrhs, flag, st);
-    cudaMemsetAsync(u, 0, (size_t)nrhs * N * sizeof(double2), st);
-    // r = f: into basis slot 0 (complex128 basis) or the residual buffer (double-single basis)
+    if (warm)
+        launch_finite_check((const double *)u, 2 * N * (size_t)nrhs, flag, st);
+    else
+        cudaMemsetAsync(u, 0, (size_t)nrhs * N * sizeof(double2), st);
+    // r_0: into basis slot 0 (complex128 basis) or the residual buffer (double-single basis)
     const bool ds = g->opt.precision == HELM_PREC_MIXED_DS;
     double2 *rvec = ds ? g->rbuf.as<double2>() : V;
     const size_t sr = ds ? N : sV;
-    launch_convert<double2, double2>(f, N, rvec, sr, N, nrhs, st);
+    if (!warm) launch_convert<double2, double2>(f, N, rvec, sr, N, nrhs, st);
     launch_norm2(f, N, N, nrm, nrhs, nullptr, ks, st);
     launch_cycle_init(S, nrm, nrhs, g->hflag, st);
+    if (warm) {
+        // a right-hand side f = 0 has the solution 0 whatever x0 was; the
+        // others start from r_0 = f - H x0, and one whose x0 already meets
+        // the tolerance ends here with no iteration (the end-of-cycle test)
+        launch_zero_inactive(u, N, S.act_cy, nrhs, st);
+        launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, rvec, sr,
+                                                 nrhs, 0.0, S.act_cy, st);
+        launch_norm2(rvec, sr, N, nrm, nrhs, S.act_cy, ks, st);
+        launch_cycle_check(S, nrm, nrhs, tol, g->opt.max_iters, g->hflag, st);
+    }
     int bad = 0;
     cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if ((s = sync_stream(g, "solve start"))) return s;
-    if (bad) return fail(HELM_ERR_NONFINITE, "right-hand side contains NaN or Inf");
+    if (bad)
+        return fail(HELM_ERR_NONFINITE, warm ? "right-hand side or initial guess contains NaN or Inf"
+                                             : "right-hand side contains NaN or Inf");
 
     while (*(volatile int *)g->hflag) {
         // v_0 = r / ||r|| (||r||^2 in nrm)
@@ -470,10 +485,10 @@ helm_status copy_out(helm_grid *g, void *dst, const void *dev, size_t bytes) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-helm_status helm_solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double tol, helm_c128 *u,
-                             int *iterations, double *true_rel_residual) {
+helm_status solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double tol, helm_c128 *u,
+                        int *iterations, double *true_rel_residual, bool warm) {
     clear_error();
     if (!g || !f || !u) return fail(HELM_ERR_ARG, "null argument");
     if (nrhs < 1 || nrhs > 65535) return fail(HELM_ERR_ARG, "nrhs must be 1..65535");
@@ -484,9 +499,16 @@ helm_status helm_solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double 
     void *ud;
     helm_status s;
     if ((s = stage_in(g, f, bytes, g->fst, &fd))) return s;
-    if ((s = out_buf(g, u, bytes, g->ust, &ud))) return s;
+    if (warm) {
+        // u carries x0 in: staged like f when it is host memory
+        const void *x0;
+        if ((s = stage_in(g, u, bytes, g->ust, &x0))) return s;
+        ud = const_cast<void *>(x0);
+    } else if ((s = out_buf(g, u, bytes, g->ust, &ud))) {
+        return s;
+    }
     helm_status rs = solve_device(g, nrhs, (const double2 *)fd, tol, (double2 *)ud, iterations,
-                                  true_rel_residual);
+                                  true_rel_residual, warm);
     if (rs != HELM_OK && rs != HELM_ERR_NOT_CONVERGED && rs != HELM_ERR_BREAKDOWN) return rs;
     std::string keep = last_error();
     if ((s = copy_out(g, u, ud, bytes))) return s;
@@ -494,9 +516,23 @@ helm_status helm_solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double 
     return HELM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+helm_status helm_solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double tol, helm_c128 *u,
+                             int *iterations, double *true_rel_residual) {
+    return solve_batch(g, nrhs, f, tol, u, iterations, true_rel_residual, false);
+}
+
+helm_status helm_solve_batch_warm(helm_grid *g, int nrhs, const helm_c128 *f, double tol,
+                                  helm_c128 *u, int *iterations, double *true_rel_residual) {
+    return solve_batch(g, nrhs, f, tol, u, iterations, true_rel_residual, true);
+}
+
 helm_status helm_solve(helm_grid *g, const helm_c128 *f, double tol, helm_c128 *u, int *iterations,
                        double *true_rel_residual) {
-    return helm_solve_batch(g, 1, f, tol, u, iterations, true_rel_residual);
+    return solve_batch(g, 1, f, tol, u, iterations, true_rel_residual, false);
 }
 
 helm_status helm_apply_H(helm_grid *g, const helm_c128 *x, helm_c128 *y) {

@@ -336,5 +336,7 @@ void launch_apply_H_ds(const LevelView<double> &L, const float4 *hd, const float
 
 // finite check: flag[0] |= 1 if any entry is NaN/Inf
 void launch_finite_check(const double *x, size_t n, int *flag, cudaStream_t st);
+// x_r = 0 (N complex128 values) for each right-hand side r with active[r] == 0
+void launch_zero_inactive(double2 *x, size_t N, const int *active, int nrhs, cudaStream_t st);
 
 }  // namespace helm

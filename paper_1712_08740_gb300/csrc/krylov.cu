@@ -430,6 +430,17 @@ __global__ void k_finite(const double *__restrict__ x, size_t n, int *__restrict
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// x_r = 0 for every right-hand side r with active[r] == 0
+__global__ void k_zero_inactive(double2 *__restrict__ x, size_t N, const int *__restrict__ active,
+                                int nrhs) {
+    const int r = blockIdx.y;
+    if (active[r]) return;
+    double2 *xr = x + (size_t)r * N;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (size_t)gridDim.x * blockDim.x)
+        xr[p] = make_double2(0.0, 0.0);
+}
+
 // Reduction grids are whole multiples of the SM count (152 on GB300): one,
 // two, four or eight blocks per SM, so that no SM runs an extra block while
 // the others idle, with roughly `per_thread` points per thread.
@@ -559,6 +570,12 @@ void launch_reorth_flags(const int *act, const double2 *h1, double2 *h2, int hst
 void launch_finite_check(const double *x, size_t n, int *flag, cudaStream_t st) {
     const int nb = blocks_for(n, kThreads * kItems, 1024);
     k_finite<<<nb, kThreads, 0, st>>>(x, n, flag);
+    count_launch();
+}
+
+void launch_zero_inactive(double2 *x, size_t N, const int *active, int nrhs, cudaStream_t st) {
+    const int nb = blocks_for(N, kThreads * kItems, 1024);
+    k_zero_inactive<<<dim3(nb, nrhs), kThreads, 0, st>>>(x, N, active, nrhs);
     count_launch();
 }
 

@@ -25,8 +25,9 @@ helm_status sync_stream(helm_grid *g, const char *where);
 helm_status ensure_ready(helm_grid *g);
 helm_status ensure_level_work(helm_grid *g, int nrhs);
 helm_status workspace_for(helm_grid *g, int nrhs);
+// warm: u holds the initial guess x0 on entry (else x0 = 0)
 helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, double2 *u,
-                         int *iterations, double *relres_out);
+                         int *iterations, double *relres_out, bool warm = false);
 const char *last_error();
 
 template <typename T> inline LevelView<T> level_view(const helm_grid *g, int l) {

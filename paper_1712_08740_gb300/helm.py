@@ -28,7 +28,7 @@ PRECISION = {"f64": 0, "mixed": 1, "mixed_ds": 2}
 
 EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "helm_set_stream",
             "helm_set_options", "helm_get_options", "helm_set_model", "helm_set_shift",
-            "helm_solve", "helm_solve_batch", "helm_apply_H", "helm_apply_H_ds", "helm_apply_M",
+            "helm_solve", "helm_solve_batch", "helm_solve_batch_warm", "helm_apply_H", "helm_apply_H_ds", "helm_apply_M",
             "helm_apply_precond", "helm_true_residual", "helm_num_levels", "helm_level_info",
             "helm_last_error", "helm_kernel_launches", "helm_profile_start", "helm_profile_stop",
             "helm_time_kernel", "helm_true_residual_noalloc", "helm_solve_footprint",
@@ -105,6 +105,7 @@ def _load():
         "helm_set_shift": (I, [P, D, D]),
         "helm_solve": (I, [P, P, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "helm_solve_batch": (I, [P, I, P, D, P, P, P]),
+        "helm_solve_batch_warm": (I, [P, I, P, D, P, P, P]),
         "helm_apply_H": (I, [P, P, P]),
         "helm_apply_H_ds": (I, [P, P, P]),
         "helm_apply_M": (I, [P, I, P, P]),
@@ -233,12 +234,13 @@ def helm_solve(g, f, tol, u, check=True):
     return st, its.value, rel.value
 
 
-def helm_solve_batch(g, nrhs, f, tol, u, check=True):
+def helm_solve_batch(g, nrhs, f, tol, u, check=True, warm=False):
+    """warm=True: u holds the initial guess on entry (helm_solve_batch_warm)."""
     its = np.zeros(nrhs, dtype=np.int32)
     rel = np.zeros(nrhs, dtype=np.float64)
-    st = _lib.helm_solve_batch(g, int(nrhs), _ptr(f, np.complex128), float(tol),
-                               _ptr(u, np.complex128), its.ctypes.data_as(ctypes.c_void_p),
-                               rel.ctypes.data_as(ctypes.c_void_p))
+    fn = _lib.helm_solve_batch_warm if warm else _lib.helm_solve_batch
+    st = fn(g, int(nrhs), _ptr(f, np.complex128), float(tol), _ptr(u, np.complex128),
+            its.ctypes.data_as(ctypes.c_void_p), rel.ctypes.data_as(ctypes.c_void_p))
     if check:
         _check(st)
     return st, its, rel
@@ -394,11 +396,15 @@ class Grid:
     def set_stream(self, stream):
         helm_set_stream(self._g, stream)
 
-    def solve(self, f, tol, u, check=True):
+    def solve(self, f, tol, u, check=True, warm=False):
+        """warm=True: start from the initial guess that u holds."""
+        if warm:
+            st, its, rel = helm_solve_batch(self._g, 1, f, tol, u, check, warm=True)
+            return st, int(its[0]), float(rel[0])
         return helm_solve(self._g, f, tol, u, check)
 
-    def solve_batch(self, nrhs, f, tol, u, check=True):
-        return helm_solve_batch(self._g, nrhs, f, tol, u, check)
+    def solve_batch(self, nrhs, f, tol, u, check=True, warm=False):
+        return helm_solve_batch(self._g, nrhs, f, tol, u, check, warm)
 
     def apply_H(self, x, y):
         helm_apply_H(self._g, x, y)
