@@ -7,7 +7,8 @@ z_j = P^-1 v_j, so the update is u = u0 + Z y. With a fixed P this is
 plain right-preconditioned GMRES. A preconditioner that changes from one
 step to the next (an inexact V-cycle) is also allowed.
 
-Readings where the paper says nothing: x0 = 0; modified Gram-Schmidt;
+Readings where the paper says nothing: x0 = 0 unless one is given (a warm
+start; f = 0 then still returns 0, the unique solution); modified Gram-Schmidt;
 complex Givens rotations with a real cosine; stop when the least-squares
 residual estimate falls to tol * ||f||, then check the true residual and
 restart from the current iterate if it is still above tol.
@@ -75,7 +76,8 @@ def gmres_right(A, f, tol, restart, maxiter, Pinv=None, x0=None):
     out = {"history": [], "true_residuals": [], "iterations": 0, "restarts": 0,
            "converged": False}
     if fnorm == 0.0:
-        out.update(x=x, converged=True)
+        # H is non-singular (alpha > 0), so f = 0 has the solution 0 whatever x0 is
+        out.update(x=np.zeros(N, dtype=np.complex128), converged=True)
         return out
     its = 0
     while its < maxiter:

@@ -281,6 +281,28 @@ def test_full_gmres_terminates_in_N_steps():
     assert r["converged"] and r["iterations"] <= N
 
 
+def test_gmres_from_an_initial_guess():
+    """Eq. 7 with x0 given: the stopping test stays relative to ||f||, so the
+    exact solution as x0 takes no iteration, any x0 reaches the LU solution,
+    a close x0 takes fewer iterations than x0 = 0, and f = 0 gives 0."""
+    H, M, f = _small_system()
+    luM = spla.splu(M.tocsc())
+    u_lu = spla.splu(H.tocsc()).solve(f)
+    A = lambda x: H @ x  # noqa: E731
+    r = gmres.gmres_right(A, f, 1e-10, 10, 500, Pinv=luM.solve, x0=u_lu)
+    assert r["converged"] and r["iterations"] == 0 and np.array_equal(r["x"], u_lu)
+    rng = np.random.default_rng(3)
+    x0 = (rng.standard_normal(f.shape) + 1j * rng.standard_normal(f.shape)) * np.abs(u_lu).max()
+    r = gmres.gmres_right(A, f, 1e-10, 10, 500, Pinv=luM.solve, x0=x0)
+    assert r["converged"] and np.linalg.norm(r["x"] - u_lu) < 1e-8 * np.linalg.norm(u_lu)
+    cold = gmres.gmres_right(A, f, 1e-10, 10, 500, Pinv=luM.solve)
+    loose = gmres.gmres_right(A, f, 1e-4, 10, 500, Pinv=luM.solve)
+    warm = gmres.gmres_right(A, f, 1e-10, 10, 500, Pinv=luM.solve, x0=loose["x"])
+    assert warm["converged"] and 0 < warm["iterations"] < cold["iterations"]
+    z = gmres.gmres_right(A, np.zeros_like(f), 1e-10, 10, 500, Pinv=luM.solve, x0=x0)
+    assert z["converged"] and z["iterations"] == 0 and not z["x"].any()
+
+
 def test_preconditioning_cuts_iterations_1d_well():
     """Example section: plain GMRES converges slowly, shifted-Laplace GMRES fast."""
     n, h, om, al = 401, 5.0, 2 * np.pi * 10.0, 0.01
