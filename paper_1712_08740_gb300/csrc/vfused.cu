@@ -772,18 +772,34 @@ template <int DIM, typename TL> constexpr size_t up_smem(size_t csz) {
     return csz * (VX * VY * VZ + EX * EY * EZ);
 }
 
+// right-hand sides one launch can take when each needs gz blocks along z
+inline int rhs_per_launch(int gz, int nb) {
+    const int cap = 65535 / gz;
+    return nb < cap ? nb : cap;
+}
+
 template <typename T, typename CB, int DIM, typename TL>
 void down_impl(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB *b,
                size_t sb, cplx_t<T> *u, size_t su, cplx_t<T> *bc, size_t sbc, int nb,
                const int *active, cudaStream_t st) {
     const size_t sm = down_smem<DIM, TL>(sizeof(cplx_t<T>));
     const int gz = DIM == 3 ? (Cv.nz + TL::SZ - 1) / TL::SZ : 1;
-    dim3 g((Cv.nx + TL::SX - 1) / TL::SX, (Cv.ny + TL::SY - 1) / TL::SY, gz * nb);
-    if constexpr (TL::MARCH) {
-        static_assert(DIM == 3, "marching tiles are 3D");
-        k_down_zm<T, CB, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, b, sb, u, su, bc, sbc, active);
-    } else {
-        k_down<T, CB, DIM, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, b, sb, u, su, bc, sbc, active);
+    // gridDim.z = z tiles x right-hand sides; a batch beyond its 65535 limit
+    // runs as several launches over consecutive right-hand sides
+    const int chunk = rhs_per_launch(gz, nb);
+    for (int r0 = 0; r0 < nb; r0 += chunk) {
+        const int n = nb - r0 < chunk ? nb - r0 : chunk;
+        dim3 g((Cv.nx + TL::SX - 1) / TL::SX, (Cv.ny + TL::SY - 1) / TL::SY, gz * n);
+        const int *act = active ? active + r0 : nullptr;
+        if constexpr (TL::MARCH) {
+            static_assert(DIM == 3, "marching tiles are 3D");
+            k_down_zm<T, CB, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, b + r0 * sb, sb, u + r0 * su, su,
+                                                        bc + r0 * sbc, sbc, act);
+        } else {
+            k_down<T, CB, DIM, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, b + r0 * sb, sb, u + r0 * su,
+                                                          su, bc + r0 * sbc, sbc, act);
+        }
+        count_launch();
     }
 }
 
@@ -793,8 +809,15 @@ void up_impl(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
              size_t sb, cplx_t<T> *uout, size_t sout, int nb, const int *active, cudaStream_t st) {
     const size_t sm = up_smem<DIM, TL>(sizeof(cplx_t<T>));
     const int gz = DIM == 3 ? (Cv.nz + TL::SZ - 1) / TL::SZ : 1;
-    dim3 g((Cv.nx + TL::SX - 1) / TL::SX, (Cv.ny + TL::SY - 1) / TL::SY, gz * nb);
-    k_up<T, CB, DIM, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, uin, sin, ec, sec, b, sb, uout, sout, active);
+    const int chunk = rhs_per_launch(gz, nb);
+    for (int r0 = 0; r0 < nb; r0 += chunk) {
+        const int n = nb - r0 < chunk ? nb - r0 : chunk;
+        dim3 g((Cv.nx + TL::SX - 1) / TL::SX, (Cv.ny + TL::SY - 1) / TL::SY, gz * n);
+        k_up<T, CB, DIM, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, uin + r0 * sin, sin, ec + r0 * sec,
+                                                    sec, b + r0 * sb, sb, uout + r0 * sout, sout,
+                                                    active ? active + r0 : nullptr);
+        count_launch();
+    }
 }
 
 // shape index -> instantiation
@@ -926,7 +949,6 @@ void launch_vdown(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB 
     else
         down_sel<T, CB, 3>(shape, std::make_index_sequence<n_down<3>()>{}, F, Cv, wj, b, sb, u, su,
                            bc, sbc, nb, active, st);
-    count_launch();
     if (prof_on()) {
         // per right-hand side: b in, u and the coarse right-hand side out;
         // D^-1 once per launch (shared by the right-hand sides)
@@ -950,7 +972,6 @@ void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
     else
         up_sel<T, CB, 3>(shape, std::make_index_sequence<n_up<3>()>{}, F, Cv, wj, uin, sin, ec, sec, b,
                          sb, uout, sout, nb, active, st);
-    count_launch();
     if (prof_on()) {
         // per right-hand side: u and b in, the sweep out, the coarse
         // correction in; D^-1 once per launch
