@@ -319,6 +319,72 @@ def test_preconditioning_cuts_iterations_1d_well():
     assert not r0["converged"]
 
 
+# ---------------------------------------------------------------- split preconditioning (Eq. 5)
+
+def _krylov_minimiser(B, b, x0_map, k):
+    """Brute force: the u = x0_map(K c) over the Krylov basis K = [b, B b, ...,
+    B^(k-1) b] that minimises ||b - B K c||_2 (numpy least squares)."""
+    K = np.empty((b.shape[0], k), dtype=np.complex128)
+    K[:, 0] = b
+    for i in range(1, k):
+        K[:, i] = B @ K[:, i - 1]
+    c = np.linalg.lstsq(B @ K, b, rcond=None)[0]
+    return x0_map(K @ c)
+
+
+@pytest.mark.parametrize("side", ["left", "right", "split"])
+def test_split_gmres_minimises_the_preconditioned_residual(side):
+    """After k steps (no restart, x0 = 0), GMRES on Ml^-1 A Mr^-1 z = Ml^-1 f
+    returns u = Mr^-1 z_k, where z_k minimises the preconditioned residual over
+    K_k(Ml^-1 A Mr^-1, Ml^-1 f). This is checked against an explicit Krylov
+    basis and numpy least squares, for left, right and two-sided
+    preconditioning."""
+    H, M, f = _small_system(n=(6, 5))
+    Hd, Md = H.toarray(), M.toarray()
+    D = np.diag(np.diag(Md))                       # a second, different preconditioner
+    Ml, Mr = {"left": (Md, None), "right": (None, Md), "split": (D, Md)}[side]
+    Li = np.eye(Hd.shape[0]) if Ml is None else np.linalg.inv(Ml)
+    Ri = np.eye(Hd.shape[0]) if Mr is None else np.linalg.inv(Mr)
+    B = Li @ Hd @ Ri
+    b = Li @ f
+    for k in (1, 2, 4, 6):
+        r = gmres.gmres_split(lambda x: Hd @ x, f, 1e-300, 100, k,
+                              Ml_inv=None if Ml is None else (lambda v: Li @ v),
+                              Mr_inv=None if Mr is None else (lambda v: Ri @ v))
+        assert r["iterations"] == k
+        ref = _krylov_minimiser(B, b, lambda z: Ri @ z, k)
+        assert np.linalg.norm(r["x"] - ref) <= 1e-8 * np.linalg.norm(ref), k
+
+
+def test_left_preconditioning_by_H_itself_takes_one_step():
+    H, M, f = _small_system(n=(6, 5))
+    lu = spla.splu(H.tocsc())
+    r = gmres.gmres_split(lambda x: H @ x, f, 1e-12, 10, 50, Ml_inv=lu.solve)
+    assert r["converged"] and r["iterations"] == 1
+    assert np.linalg.norm(r["x"] - lu.solve(f)) <= 1e-12 * np.linalg.norm(r["x"])
+
+
+def test_left_preconditioned_shifted_laplacian_1d_well():
+    """The left variant (Ml = P, Mr = I in Eq. 5) on the 1D three-layer well:
+    it converges to the LU solution; its preconditioned operator P^-1 H has the
+    spectrum of H P^-1, so it needs about as many steps as the right variant."""
+    n, h, om, al = 401, 5.0, 2 * np.pi * 10.0, 0.01
+    i = np.arange(n)
+    m = 1.0 / np.where(i < n // 3, 1500.0, np.where(i < 2 * n // 3, 2500.0, 3500.0))
+    H = op.assemble_H((n,), h, m, om, al)
+    M = op.assemble_M((n,), h, m, om, al, 1.0, 0.5)
+    f = np.zeros(n, complex)
+    f[n // 2] = 1 / h
+    luM = spla.splu(M.tocsc())
+    u_lu = spla.splu(H.tocsc()).solve(f)
+    left = gmres.gmres_split(lambda x: H @ x, f, 1e-10, 50, 2000, Ml_inv=luM.solve)
+    right = gmres.gmres_right(lambda x: H @ x, f, 1e-10, 50, 2000, Pinv=luM.solve)
+    assert left["converged"] and right["converged"]
+    assert np.linalg.norm(left["x"] - u_lu) <= 1e-7 * np.linalg.norm(u_lu)
+    assert left["true_residuals"][-1] <= 1e-8
+    assert 0.5 * right["iterations"] <= left["iterations"] <= 2 * right["iterations"]
+
+
 # ---------------------------------------------------------------- multigrid pieces
 
 def test_level_sizes_of_reference_grids():
