@@ -14,7 +14,9 @@ Helmholtz equation, part 1: Data modelling"):
                      (Eq. 6) as sparse matrices, in complex128.
 * ``direct``      -- the exact solve u = H^-1 f by sparse LU (Eq. 4).
 * ``gmres``       -- restarted, right-preconditioned GMRES (Eq. 7), with the
-                     flexible variant that stores the preconditioned vectors.
+                     flexible variant that stores the preconditioned vectors,
+                     optionally from an initial guess; GMRES on the
+                     split-preconditioned system of Eq. 5.
 * ``multigrid``   -- the geometric V-cycle used on the GPU to apply the
                      inverse of the shifted Laplacian, written out step by
                      step (Jacobi, residual, full weighting, bilinear
@@ -22,8 +24,10 @@ Helmholtz equation, part 1: Data modelling"):
 * ``closed_form`` -- closed forms that pin the above: the exact 1D discrete
                      solution, the continuous Green's function and a
                      manufactured 2D/3D solution.
+* ``density``     -- the variable-density operator of Eq. 1, node by node.
 
-Parity status: ``operator``, ``direct``, ``gmres`` and ``multigrid`` are
+Parity status: ``operator``, ``direct``, ``gmres``, ``multigrid`` and
+``density`` are
 pinned by tests that do not reuse their formulas (closed forms, brute force,
 invariants). The paper's figures (spectra, convergence curves, wavefields)
 carry no numbers, so any comparison with them is "parity unpinned".
