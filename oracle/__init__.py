@@ -27,8 +27,7 @@ Helmholtz equation, part 1: Data modelling"):
 * ``density``     -- the variable-density operator of Eq. 1, node by node.
 
 Parity status: ``operator``, ``direct``, ``gmres``, ``multigrid`` and
-``density`` are
-pinned by tests that do not reuse their formulas (closed forms, brute force,
-invariants). The paper's figures (spectra, convergence curves, wavefields)
+``density`` are pinned by tests that do not reuse their formulas (closed
+forms, brute force, invariants). The paper's figures (spectra, convergence curves, wavefields)
 carry no numbers, so any comparison with them is "parity unpinned".
 """
