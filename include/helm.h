@@ -112,6 +112,9 @@ helm_status helm_set_stream(helm_grid *g, void *stream);
  * coarse_max, precond or precision rebuilds the hierarchy.
  * Errors: HELM_ERR_ARG on an out-of-range field. */
 helm_status helm_set_options(helm_grid *g, const helm_options *opt);
+
+/* Copies the grid's current options into *opt (caller-owned).
+ * Errors: HELM_ERR_ARG on a null argument. */
 helm_status helm_get_options(const helm_grid *g, helm_options *opt);
 
 /* Eq. 2: sets the medium and frequency. m: slowness 1/c in s/m, one real
@@ -271,6 +274,9 @@ typedef struct {
     int nu1, nu2;                                 /* smoother counts now in use      */
 } helm_tune_report;
 
+/* helm_tile_shape: kernel 0 = down, 1 = up; extent[3] (caller-owned) gets the
+ * tile's extents in coarse nodes (x, y, z; z = 1 in 2D), *threads the block
+ * size. Errors: HELM_ERR_ARG for a dim, kernel or shape out of range. */
 int         helm_num_tile_shapes(int dim);
 helm_status helm_tile_shape(int dim, int kernel, int shape, int extent[3], int *threads);
 helm_status helm_set_tiles(helm_grid *g, int level, int down_shape, int up_shape);
