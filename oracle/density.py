@@ -40,15 +40,18 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-__all__ = ["assemble_H_rho"]
+__all__ = ["assemble_shifted_rho", "assemble_H_rho", "assemble_M_rho", "build_levels_rho"]
 
 
-def assemble_H_rho(n, h, m, rho, omega, alpha) -> sp.csr_matrix:
-    """H of Eq. 1 (variable rho) as a CSR matrix, assembled node by node.
+def assemble_shifted_rho(n, h, m, rho, omega, alpha, shift) -> sp.csr_matrix:
+    """-div(rho grad) with the absorbing rows above, minus shift * omega^2 m^2,
+    as a CSR matrix assembled node by node.
 
     n: node counts per axis (axis 0 fastest, each >= 2); h: spacing;
     m: slowness and rho: the coefficient of Eq. 1, one value per node (shape
-    n[::-1] or flat); omega: angular frequency; alpha: damping.
+    n[::-1] or flat); omega: angular frequency; alpha: damping, which enters
+    the boundary rows through kappa; shift: the complex factor of the
+    zero-order term (1 - j alpha for H, beta1 - j beta2 for M).
     """
     n = tuple(int(k) for k in n)
     if any(k < 2 for k in n):
@@ -67,7 +70,7 @@ def assemble_H_rho(n, h, m, rho, omega, alpha) -> sp.csr_matrix:
     A = sp.lil_matrix((N, N), dtype=np.complex128)
     for p in range(N):
         idx = [(p // stride[a]) % n[a] for a in range(d)]
-        diag = -omega ** 2 * m[p] ** 2 * (1.0 - 1j * alpha)
+        diag = -shift * omega ** 2 * m[p] ** 2
         for a in range(d):
             i = idx[a]
             lo = p - stride[a] if i > 0 else None
@@ -86,3 +89,36 @@ def assemble_H_rho(n, h, m, rho, omega, alpha) -> sp.csr_matrix:
                 A[p, inner] += -2.0 * b_in * ih2
         A[p, p] += diag
     return A.tocsr()
+
+
+def assemble_H_rho(n, h, m, rho, omega, alpha) -> sp.csr_matrix:
+    """H of Eq. 1 (variable rho): the zero-order factor is 1 - j alpha."""
+    return assemble_shifted_rho(n, h, m, rho, omega, alpha, 1.0 - 1j * alpha)
+
+
+def assemble_M_rho(n, h, m, rho, omega, alpha, beta1, beta2) -> sp.csr_matrix:
+    """The shifted Laplacian of Eq. 6 for the operator of Eq. 1: the same
+    -div(rho grad) and boundary rows as H_rho, zero-order factor
+    beta1 - j beta2 (so that H_rho - M_rho is diagonal, as without rho)."""
+    return assemble_shifted_rho(n, h, m, rho, omega, alpha, beta1 - 1j * beta2)
+
+
+def build_levels_rho(n, h, m, rho, omega, alpha, beta1, beta2, coarse_max=1500, max_levels=32):
+    """Multigrid levels of M_rho: the coarsening rule of the constant-density
+    hierarchy, with both the slowness and rho injected (coarse node =
+    coincident fine node) and M_rho rediscretised on every level. The result
+    feeds multigrid.vcycle unchanged."""
+    from .multigrid import Level, can_coarsen
+    n = tuple(int(k) for k in n)
+    m = np.asarray(m, dtype=np.float64).reshape(n[::-1])
+    rho = np.asarray(rho, dtype=np.float64).reshape(n[::-1])
+    levels = []
+    while True:
+        levels.append(Level(n, h, m, assemble_M_rho(n, h, m, rho, omega, alpha, beta1, beta2)))
+        if int(np.prod(n)) <= coarse_max or not can_coarsen(n) or len(levels) >= max_levels:
+            break
+        sl = tuple(slice(None, None, 2) for _ in n)
+        m, rho = m[sl], rho[sl]
+        n = tuple((k + 1) // 2 for k in n)
+        h = 2.0 * h
+    return levels
