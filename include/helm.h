@@ -77,6 +77,19 @@ typedef enum {
                              /* Hessenberg, norms and the true residual in complex128  */
 } helm_precision;
 
+/* Where M^-1 enters the Krylov operator (Eq. 5: Ml^-1 H Mr^-1 z = Ml^-1 f,
+ * u = Mr^-1 z). The paper solves Eq. 7, i.e. Ml = I, Mr = M. */
+typedef enum {
+    HELM_SIDE_RIGHT = 0,     /* Ml = I, Mr = M (Eq. 7, default): flexible GMRES;       */
+                             /* stops on ||f - H u|| <= tol ||f||                       */
+    HELM_SIDE_LEFT = 1,      /* Ml = M, Mr = I: GMRES on M^-1 H u = M^-1 f              */
+    HELM_SIDE_SPLIT = 2      /* Ml = Mr = M: GMRES on M^-1 H M^-1 z = M^-1 f            */
+    /* LEFT and SPLIT minimise, and stop on, the preconditioned residual:        */
+    /* ||M^-1 (f - H u)|| <= tol ||M^-1 f||. They need a fixed M^-1 (the V-cycle  */
+    /* or the dense inverse) and a complex128 Arnoldi basis (not                 */
+    /* HELM_PREC_MIXED_DS); with HELM_PRECOND_NONE the side has no effect.       */
+} helm_side;
+
 typedef struct {
     int restart;             /* Krylov dimension m per cycle (1..256); default 30     */
     int max_iters;           /* cap on inner iterations over all cycles; default 5000 */
@@ -91,6 +104,7 @@ typedef struct {
                              /* is recomputed after every cycle in all three.        */
     int graphs;              /* 1: replay each Arnoldi step as a captured CUDA graph   */
                              /*    (default); 0: launch kernels one by one             */
+    int side;                /* helm_side; default HELM_SIDE_RIGHT                     */
 } helm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -124,6 +138,22 @@ helm_status helm_get_options(const helm_grid *g, helm_options *opt);
  * helm_set_shift. Errors: HELM_ERR_ARG, HELM_ERR_NONFINITE, HELM_ERR_CUDA. */
 helm_status helm_set_model(helm_grid *g, const double *m, double omega, double alpha);
 
+/* Eq. 1: sets a variable density. rho: one real double per node (host or
+ * device), all finite and > 0, the coefficient inside the divergence as the
+ * paper prints it (-div(rho grad u) - omega^2 m^2 (1 - j alpha) u = f; for the
+ * acoustic equation pass 1/density). Null removes it (rho = 1, Eq. 2). The
+ * library copies rho. Discretisation: each face between two neighbours takes
+ * the mean of rho at its two nodes; a boundary face absorbs with the local
+ * wavenumber kappa / sqrt(rho) (ghost face mirrored from the inner face). M
+ * keeps the same -div(rho grad) and boundary rows (Eq. 6 with rho), so H - M
+ * stays diagonal; coarser levels inject rho like the slowness. With a density
+ * the V-cycle runs the general (unfused) level kernels, and the
+ * HELM_PREC_MIXED_DS basis, helm_apply_H_ds and helm_true_residual_noalloc
+ * are not available (HELM_ERR_UNSUPPORTED). Invalidates the preconditioner.
+ * Errors: HELM_ERR_ARG, HELM_ERR_NONFINITE, HELM_ERR_UNSUPPORTED,
+ * HELM_ERR_NOMEM, HELM_ERR_CUDA. */
+helm_status helm_set_density(helm_grid *g, const double *rho);
+
 /* Eq. 6: sets the shift (beta1, beta2) of M = -Lap - (beta1 - j beta2) w^2 m^2
  * and builds the multigrid hierarchy and the coarse-grid inverse on the
  * device. Default (1, 0.5). Errors: HELM_ERR_STATE (no model),
@@ -133,9 +163,11 @@ helm_status helm_set_shift(helm_grid *g, double beta1, double beta2);
 
 /* Eq. 7: solves H u = f by restarted flexible GMRES, right-preconditioned
  * by M, from u0 = 0, until ||f - H u||_2 / ||f||_2 <= tol (recomputed in
- * complex128 after each cycle). f, u: N complex values (host or device,
- * not overlapping). iterations (nullable): inner iterations used.
- * true_rel_residual (nullable): the final true relative residual.
+ * complex128 after each cycle). With options.side LEFT or SPLIT it runs GMRES
+ * on Eq. 5 instead and stops on the preconditioned residual (see helm_side).
+ * f, u: N complex values (host or device, not overlapping). iterations
+ * (nullable): inner iterations used. true_rel_residual (nullable): the final
+ * true relative residual ||f - H u||_2 / ||f||_2 (on every side).
  * Errors: HELM_ERR_STATE, HELM_ERR_ARG, HELM_ERR_NONFINITE (f not finite),
  * HELM_ERR_NOT_CONVERGED (u holds the last iterate), HELM_ERR_BREAKDOWN,
  * HELM_ERR_NOMEM, HELM_ERR_CUDA. */
@@ -192,17 +224,18 @@ helm_status helm_true_residual(helm_grid *g, const helm_c128 *f, const helm_c128
 /* Allocation-free variant of helm_true_residual for nrhs right-hand sides:
  * rel[k] = ||f_k - H u_k||_2 / ||f_k||_2 in complex128, f_k and u_k at
  * offset k*N of the device arrays f and u (both must be device pointers of
- * the current device; nothing is staged). The paper has no counterpart.
+ * the current device, each holding at least nrhs*N values; nothing is
+ * staged). The paper has no counterpart.
  *
- * Who needs it: callers that cannot call cudaMalloc -- code running while a
- * stream is captured into a CUDA graph (allocation cannot be captured and
- * breaks the capture), services that hand out device memory from their own
- * fixed budget, and latency-critical loops that must not wait on the
- * allocator. helm_true_residual may allocate staging and reduction buffers on
- * first use; this entry point allocates nothing (no cudaMalloc or cudaFree, no
- * allocating library call). Its scratch is one static device array of
- * 305 KiB inside the library, which every GPU that loads the library holds until
- * the process exits. Limits and behaviour:
+ * Who needs it: callers that cannot call cudaMalloc. A serving process that
+ * reserves the GPU's memory up front and hands it out from its own pool
+ * leaves nothing for cudaMalloc to take, and a caller that must not stall
+ * other streams cannot afford cudaMalloc/cudaFree, which may synchronise the
+ * device. helm_true_residual may allocate staging and reduction buffers on
+ * first use; this entry point allocates nothing (no cudaMalloc or cudaFree,
+ * no allocating library call). Its scratch is one static device array of
+ * 305 KiB inside the library, which every GPU that loads the library holds
+ * until the process exits. Limits and behaviour:
  *  - nrhs must be 1..64 (the size of that array); larger values return
  *    HELM_ERR_ARG;
  *  - the first call on a device looks up the array's device address
@@ -211,8 +244,12 @@ helm_status helm_true_residual(helm_grid *g, const helm_c128 *f, const helm_c128
  *  - every call shares the array: calls whose work overlaps on the GPU (for
  *    example on two streams at once) race and give wrong results; calls in
  *    sequence on one stream are safe (each call clears what must start at 0);
- *  - it synchronises the grid's stream to return rel on the host.
- * Errors: HELM_ERR_ARG, HELM_ERR_STATE (no model), HELM_ERR_CUDA. */
+ *  - it copies rel to host memory and synchronises the grid's stream before
+ *    it returns;
+ *  - grids with a variable-density coefficient (helm_set_density) are not
+ *    served: HELM_ERR_UNSUPPORTED.
+ * Errors: HELM_ERR_ARG (also for a pointer of another device),
+ * HELM_ERR_STATE (no model), HELM_ERR_UNSUPPORTED, HELM_ERR_CUDA. */
 helm_status helm_true_residual_noalloc(helm_grid *g, int nrhs, const helm_c128 *f,
                                        const helm_c128 *u, double *rel);
 
@@ -233,8 +270,8 @@ helm_status helm_true_residual_noalloc(helm_grid *g, int nrhs, const helm_c128 *
  * results are bitwise identical for every choice. helm_set_tiles /
  * helm_get_tiles set and read the shapes used on fine level `level` (the
  * pair level, level+1); -1 (the initial setting) selects the shape
- * automatically per solve: the first shape whose grid has at least 2 x 152
- * blocks for the batch, else the shape with the most blocks.
+ * automatically per solve: the first shape whose grid has at least 2 blocks per
+ * SM for the batch, else the shape with the most blocks.
  *
  * helm_autotune(g, nrhs, f, tol, flags, report) measures on the grid's
  * current model, shift, options and batch size nrhs:
@@ -387,6 +424,16 @@ helm_status helm_profile_stop(char *json, size_t cap);
  * HELM_ERR_CUDA. The paper has no counterpart: this is instrumentation. */
 helm_status helm_time_kernel(helm_grid *g, const char *kernel, int j, int reps,
                              double *us_per_launch, double *bytes, double *flops64);
+
+/* Time limit of the waits in which the streamed double-single Arnoldi kernels
+ * (HELM_PREC_MIXED_DS) wait for a tile copy to land in shared memory, on the
+ * current device; ns = 0 restores the default of 0.5 s. A wait that runs out
+ * ends the kernel early: its results become NaN and the solve returns
+ * HELM_ERR_BREAKDOWN, after the copies already issued have landed (those
+ * waits keep the default limit). The grid stays usable. This exists to test
+ * that timeout path; leave it at the default otherwise. The paper has no
+ * counterpart. Errors: HELM_ERR_CUDA. */
+helm_status helm_set_wait_limit_ns(uint64_t ns);
 
 /* Number of kernels this library has launched in this process (all grids).
  * Used to report launch counts; not thread-safe across concurrent grids. */

@@ -125,9 +125,18 @@ helm_status build_hierarchy(helm_grid *g) {
                               C.n[2], g->st);
         launch_make_w(C.m.as<double>(), C.N, g->omega, C.w64.as<double>(), C.w32.as<float>(),
                       g->flag.as<int>(), g->st);
+        if (g->has_rho) {
+            // rho of Eq. 1 injected like the slowness
+            if ((s = C.rho64.ensure(C.N * sizeof(double))) || (s = C.rho32.ensure(C.N * sizeof(float))))
+                return s;
+            launch_inject<double>(F.rho64.as<double>(), F.n[0], F.n[1], C.rho64.as<double>(), C.n[0],
+                                  C.n[1], C.n[2], g->st);
+            launch_make_rho(C.rho64.as<double>(), C.N, C.rho32.as<float>(), nullptr, g->st);
+        }
     }
-    // inverse diagonal of M per level, in the V-cycle's precision (fused kernels)
-    for (size_t l = 0; l < g->lv.size(); ++l) {
+    // inverse diagonal of M per level, in the V-cycle's precision (fused
+    // kernels, which run with a constant density only)
+    for (size_t l = 0; l < g->lv.size() && !g->has_rho; ++l) {
         MGLevel &L = g->lv[l];
         const size_t esz = (prec == HELM_PREC_F64) ? sizeof(double2) : sizeof(float2);
         if ((s = L.dinv.ensure(L.N * esz))) return s;
@@ -218,11 +227,23 @@ void helm_default_options(helm_options *o) {
     o->coarse_max = 1500;
     o->reorth = 0;
     o->graphs = 1;
+    o->side = HELM_SIDE_RIGHT;
 }
 
 const char *helm_last_error(void) { return helm::last_error(); }
 
 uint64_t helm_kernel_launches(void) { return helm::launch_count(); }
+
+helm_status helm_set_wait_limit_ns(uint64_t ns) {
+    clear_error();
+    const unsigned long long v = ns ? (unsigned long long)ns : 500ull * 1000 * 1000;
+    cudaError_t e = set_consumer_wait_ns(v);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HELM_ERR_CUDA, "setting the wait limit: %s", cudaGetErrorString(e));
+    }
+    return HELM_OK;
+}
 
 helm_status helm_create_grid(int dim, const int64_t n[3], double h, helm_grid **out) {
     clear_error();
@@ -292,6 +313,14 @@ helm_status helm_set_options(helm_grid *g, const helm_options *o) {
         return fail(HELM_ERR_ARG, "omega_jacobi must be in (0, 1]");
     if (o->coarse_max < 1) return fail(HELM_ERR_ARG, "coarse_max must be >= 1");
     if (o->reorth < 0 || o->reorth > 2) return fail(HELM_ERR_ARG, "reorth must be 0, 1 or 2");
+    if (o->side < 0 || o->side > 2) return fail(HELM_ERR_ARG, "side must be 0, 1 or 2");
+    if (g->has_rho && o->precision == HELM_PREC_MIXED_DS)
+        return fail(HELM_ERR_UNSUPPORTED, "a variable density needs precision HELM_PREC_F64 or HELM_PREC_MIXED");
+    if (o->side != HELM_SIDE_RIGHT && o->precond != HELM_PRECOND_NONE &&
+        o->precision == HELM_PREC_MIXED_DS)
+        return fail(HELM_ERR_UNSUPPORTED,
+                    "left and two-sided preconditioning need a complex128 Arnoldi basis "
+                    "(precision HELM_PREC_F64 or HELM_PREC_MIXED)");
     if (o->precond == HELM_PRECOND_EXACT && g->N > 4096)
         return fail(HELM_ERR_UNSUPPORTED, "exact preconditioner needs <= 4096 nodes");
     const bool rebuild = o->precond != g->opt.precond || o->precision != g->opt.precision ||
@@ -331,6 +360,35 @@ helm_status helm_set_model(helm_grid *g, const double *m, double omega, double a
     g->omega = omega;
     g->alpha = alpha;
     g->has_model = true;
+    return HELM_OK;
+}
+
+helm_status helm_set_density(helm_grid *g, const double *rho) {
+    clear_error();
+    if (!g) return fail(HELM_ERR_ARG, "grid is null");
+    if (!rho) {
+        g->has_rho = false;
+        g->ready = false;
+        return HELM_OK;
+    }
+    if (g->opt.precision == HELM_PREC_MIXED_DS)
+        return fail(HELM_ERR_UNSUPPORTED, "a variable density needs precision HELM_PREC_F64 or HELM_PREC_MIXED");
+    MGLevel &L = g->lv[0];
+    helm_status s;
+    if ((s = L.rho64.ensure(g->N * sizeof(double))) || (s = L.rho32.ensure(g->N * sizeof(float)))) return s;
+    cudaError_t e = cudaMemcpyAsync(L.rho64.p, rho, g->N * sizeof(double), cudaMemcpyDefault, g->st);
+    if (e != cudaSuccess) return fail(HELM_ERR_CUDA, "copy of rho: %s", cudaGetErrorString(e));
+    cudaMemsetAsync(g->flag.p, 0, sizeof(int), g->st);
+    launch_make_rho(L.rho64.as<double>(), g->N, L.rho32.as<float>(), g->flag.as<int>(), g->st);
+    int bad = 0;
+    cudaMemcpyAsync(&bad, g->flag.p, sizeof(int), cudaMemcpyDeviceToHost, g->st);
+    if ((s = sync_stream(g, "helm_set_density"))) return s;
+    g->ready = false;
+    if (bad) {
+        g->has_rho = false;
+        return fail(HELM_ERR_NONFINITE, "rho must be finite and > 0 at every node");
+    }
+    g->has_rho = true;
     return HELM_OK;
 }
 

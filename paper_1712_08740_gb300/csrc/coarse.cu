@@ -29,27 +29,33 @@ __global__ void k_assemble_dense(LevelView<T> L, OpShift<T> s, cplx_t<T> *__rest
     const int n[3] = {L.nx, L.ny, L.nz};
     const int stride[3] = {1, L.nx, L.nx * L.ny};
     cplx_t<T> *row = A + (size_t)p * N;
-    int nf = 0;
+    // neighbour weights c (times the face coefficient of Eq. 1 when rho is
+    // set), their sum (Laplacian part of the diagonal) and the boundary factor
+    const T rp = L.rho ? L.rho[p] : T(1);
+    T dsum = 0, bsum = 0;
     for (int a = 0; a < L.dim; ++a) {
         const int i = coord[a];
         if (i > 0) {
-            T c = (i == n[a] - 1) ? T(2) : T(1);
+            const T face = L.rho ? T(0.5) * (rp + L.rho[p - stride[a]]) : T(1);
+            T c = ((i == n[a] - 1) ? T(2) : T(1)) * face;
             row[p - stride[a]].x += -c * L.inv_h2;
-        } else {
-            ++nf;
+            dsum += c;
+            if (i == n[a] - 1) bsum += face;
         }
         if (i < n[a] - 1) {
-            T c = (i == 0) ? T(2) : T(1);
+            const T face = L.rho ? T(0.5) * (rp + L.rho[p + stride[a]]) : T(1);
+            T c = ((i == 0) ? T(2) : T(1)) * face;
             row[p + stride[a]].x += -c * L.inv_h2;
-        } else {
-            ++nf;
+            dsum += c;
+            if (i == 0) bsum += face;
         }
     }
+    if (L.rho) bsum /= dsqrt<T>(rp);
     const T wp = L.w[p];
-    T dre = T(2 * L.dim) * L.inv_h2 - s.s_re * wp;
+    T dre = dsum * L.inv_h2 - s.s_re * wp;
     T dim_ = -s.s_im * wp;
-    if (nf) {
-        const T f = T(nf) * L.two_over_h * dsqrt<T>(wp);
+    if (bsum != T(0)) {
+        const T f = bsum * L.two_over_h * dsqrt<T>(wp);
         dre -= f * s.q_im;
         dim_ += f * s.q_re;
     }
@@ -129,16 +135,16 @@ __global__ void k_transpose_square(cplx_t<T> *__restrict__ A, int n) {
 // Work: a warp owns 32 consecutive rows (one per lane, so each column read is
 // one coalesced row of At), one column group and a tile of RT (1 or 4) right-hand
 // sides, whose slice of R it stages in shared memory. G is chosen so that
-// the single-right-hand-side grid is about one wave of 152 x 8 warps with
+// the single-right-hand-side grid is about one wave of (SMs) x 8 warps with
 // every SM given the same number of warps up to one (contiguous task ranges
 // per block). Each warp writes its group sums to `part`; the last of the G
 // warps of a (row group, right-hand-side tile) to finish (atomic ticket)
 // adds them in group order and writes Z.
 constexpr int kGemmWarps = 8;
 
-__host__ __device__ inline int gemm_groups(int n) {
+inline int gemm_groups(int n) {
     const int rgs = (n + 31) / 32;
-    int G = (152 * kGemmWarps) / rgs;
+    int G = (device_sms() * kGemmWarps) / rgs;
     if (G < 1) G = 1;
     if (G > 64) G = 64;
     const int gmin = (n + 127) / 128;      // groups of at most 128 columns (shared-memory slice)
@@ -151,11 +157,10 @@ template <typename T, int RT>
 __global__ void __launch_bounds__(kGemmWarps * 32, 1)
 k_coarse_gemm(const cplx_t<T> *__restrict__ At, int n, const cplx_t<T> *__restrict__ R, size_t sr,
               cplx_t<T> *__restrict__ Z, size_t sz, int nb, const int *__restrict__ active,
-              cplx_t<T> *__restrict__ part, unsigned *__restrict__ ticket, int ntask) {
+              cplx_t<T> *__restrict__ part, unsigned *__restrict__ ticket, int ntask, int G) {
     using C = cplx_t<T>;
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int G = gemm_groups(n);
     const int cw = (n + G - 1) / G;
     const int rgs = (n + 31) / 32;
     // contiguous task range of this block: every SM gets the same count up to one
@@ -308,13 +313,14 @@ void gemm_impl(const cplx_t<T> *At, int n, const cplx_t<T> *r, size_t sr, cplx_t
     const int G = gemm_groups(n);
     const int cw = (n + G - 1) / G;
     const int ntask = ((n + 31) / 32) * G * ((nb + RT - 1) / RT);
-    const int per_sm = (ntask + 151) / 152;
+    const int sms = device_sms();
+    const int per_sm = (ntask + sms - 1) / sms;
     // up to 8 warps (tasks) per block; when one wave suffices, one block per SM
-    const int blocks = per_sm <= kGemmWarps ? (ntask < 152 ? ntask : 152)
+    const int blocks = per_sm <= kGemmWarps ? (ntask < sms ? ntask : sms)
                                             : (ntask + kGemmWarps - 1) / kGemmWarps;
     const size_t sm = (size_t)kGemmWarps * RT * cw * sizeof(cplx_t<T>);
     k_coarse_gemm<T, RT><<<blocks, kGemmWarps * 32, sm, st>>>(At, n, r, sr, z, sz, nb, active, part,
-                                                              ticket, ntask);
+                                                              ticket, ntask, G);
 }
 
 }  // namespace

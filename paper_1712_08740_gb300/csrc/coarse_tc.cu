@@ -112,9 +112,10 @@ inline TcGeom tc_geom(int n, int nb) {
     g.nkc = (n + kK - 1) / kK;
     g.Mp = g.nrt * kM;
     g.nsb = (nb + kN - 1) / kN;
-    // about one CTA per SM per block of sources; depends on n only, so the
-    // order of every sum is fixed by n
-    g.kch = (g.nrt * g.nkc + 151) / 152;
+    // about one CTA per SM per block of sources; depends on n and the SM
+    // count only, so the order of every sum is fixed by n on a device
+    const int sms = device_sms();
+    g.kch = (g.nrt * g.nkc + sms - 1) / sms;
     g.nkg = (g.nkc + g.kch - 1) / g.kch;
     return g;
 }
@@ -185,14 +186,15 @@ k_coarse_tc(const float *__restrict__ tiles, TcGeom G, const float2 *__restrict_
     for (int i = 0; i < nch; ++i) {
         const int st = i & 1, kc = c0 + i;
         const unsigned ph = (unsigned)(i >> 1) & 1u;
-        // stage st was last read by the MMAs of chunk i - 2
+        // stage st was last read by the MMAs of chunk i - 2; after an abort the
+        // stage is no longer written (those MMAs may not have finished)
         if (i >= 2 && !pipe::mbar_wait_drain(&S.mbar[st], ph ^ 1u)) S.abort = 1;
         tc_fence_after();
         // this chunk's slice of R, split into TF32 hi and lo planes. Thread
         // (warp w, lane l) owns source j = 8 w + l / 4 and columns 4 g + l % 4,
         // g = 0..7: all eight loads are issued first, and each warp's stores
         // cover 32 consecutive floats of a plane (one core-matrix row group)
-        {
+        if (!*(volatile int *)&S.abort) {
             float2 v[kK / 4];
             const size_t base = (size_t)src_j * sr + (size_t)kc * kK + (lane & 3);
 #pragma unroll
@@ -263,8 +265,13 @@ k_coarse_tc(const float *__restrict__ tiles, TcGeom G, const float2 *__restrict_
     }
     const uint32_t tmem = S.tmem;
     {
+        // the accumulators are read and TMEM is freed only after the last
+        // MMAs have completed: a wait that runs out is retried (each bounded)
+        // before the block gives up on them
         const int il = nch - 1;
-        if (!pipe::mbar_wait_drain(&S.mbar[il & 1], (unsigned)(il >> 1) & 1u)) S.abort = 1;
+        bool done = false;
+        for (int a = 0; a < 4 && !done; ++a) done = pipe::mbar_wait_drain(&S.mbar[il & 1], (unsigned)(il >> 1) & 1u);
+        if (!done) S.abort = 1;
     }
     __syncthreads();   // every thread sees the same abort word
     tc_fence_after();

@@ -15,6 +15,12 @@
 // decision are no-ops for them. The host runs at most kLookahead steps ahead
 // of the device, polling a host-mapped "any right-hand side still stepping"
 // flag written by the Givens kernel, and synchronises once per cycle.
+//
+// Left and two-sided preconditioning (Eq. 5 with Ml = M, and Ml = Mr = M):
+// the step forms w = M^-1 H x_j (x_j = v_j, or z_j = M^-1 v_j), the cycle
+// starts from r = M^-1 (f - H u), and the stopping tests compare the
+// preconditioned residual with tol ||M^-1 f||; the update is u += V y (left)
+// or u += Z y (two-sided). The true residual is reported at the end.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -32,11 +38,18 @@ namespace {
 
 constexpr int kLookahead = 2;
 
+// left or two-sided preconditioning (M^-1 applied after H in every step)
+inline bool left_side(const helm_grid *g) {
+    return g->opt.side != HELM_SIDE_RIGHT && g->opt.precond != HELM_PRECOND_NONE;
+}
+
 helm_status ensure_workspace(helm_grid *g, int nrhs) {
     const int m = g->opt.restart;
     const int prec = g->opt.precision;
     const int pc = g->opt.precond;
-    if (g->cap_rhs >= nrhs && g->cap_m == m && g->cap_prec == prec) return HELM_OK;
+    const int side = g->opt.side;
+    if (g->cap_rhs >= nrhs && g->cap_m == m && g->cap_prec == prec && g->cap_side == side)
+        return HELM_OK;
     const size_t N = g->N;
     helm_status s;
     const size_t zsz = (prec == HELM_PREC_F64) ? sizeof(double2) : sizeof(float2);
@@ -49,6 +62,9 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
     const size_t R = (size_t)nrhs;
     if (prec == HELM_PREC_MIXED_DS && ((s = g->rbuf.ensure(R * N * sizeof(double2))) ||
                                        (s = g->hdiag.ensure(N * sizeof(float4)))))
+        return s;
+    if (left_side(g) && ((s = g->rbuf.ensure(R * N * sizeof(double2))) ||
+                         (s = g->tnrm.ensure(2 * R * sizeof(double)))))
         return s;
     if ((s = g->hbuf.ensure(R * 2 * nv * sizeof(double2)))) return s;
     if ((s = g->nrm.ensure(R * sizeof(double)))) return s;
@@ -88,6 +104,7 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
     g->cap_rhs = nrhs;
     g->cap_m = m;
     g->cap_prec = prec;
+    g->cap_side = side;
     return HELM_OK;
 }
 
@@ -173,6 +190,44 @@ void apply_H_j(helm_grid *g, int j, int nrhs, const int *act) {
     }
 }
 
+// dst = M^-1 src (complex128 in and out, stride sd per right-hand side) in
+// the preconditioner's arithmetic: the complex64 V-cycle writes the level-0
+// iterate buffer, widened into dst
+void precond_into(helm_grid *g, const double2 *src, size_t ss, double2 *dst, size_t sd, int nrhs,
+                  const int *act) {
+    const size_t N = g->N;
+    if (g->vc_prec == HELM_PREC_F64) {
+        vcycle<double, double2>(g, src, ss, dst, sd, nrhs, act);
+    } else {
+        float2 *u = g->lv[0].u.as<float2>();
+        vcycle<float, double2>(g, src, ss, u, N, nrhs, act);
+        launch_convert<float2, double2>(u, N, dst, sd, N, nrhs, g->st);
+    }
+}
+
+// w = M^-1 H x_j into basis slot j+1 (left: x_j = v_j; two-sided: x_j = z_j),
+// H x_j staged in the residual buffer
+void apply_left_j(helm_grid *g, int j, int nrhs, const int *act) {
+    const size_t N = g->N;
+    const int m = g->opt.restart;
+    const size_t sV = (size_t)(m + 1) * N, sZ = (size_t)m * N;
+    double2 *V = g->V.as<double2>();
+    double2 *t = g->rbuf.as<double2>();
+    const LevelView<double> Lv = level_view<double>(g, 0);
+    if (g->opt.side == HELM_SIDE_LEFT)
+        launch_stencil<double, double2, double2>(ST_APPLY, Lv, shift_H(g), V + (size_t)j * N, sV,
+                                                 (const double2 *)nullptr, 0, t, N, nrhs, 0.0, act, g->st);
+    else if (g->opt.precision == HELM_PREC_F64)
+        launch_stencil<double, double2, double2>(ST_APPLY, Lv, shift_H(g),
+                                                 g->Z.as<double2>() + (size_t)j * N, sZ,
+                                                 (const double2 *)nullptr, 0, t, N, nrhs, 0.0, act, g->st);
+    else
+        launch_stencil<double, float2, double2>(ST_APPLY, Lv, shift_H(g),
+                                                g->Z.as<float2>() + (size_t)j * N, sZ,
+                                                (const double2 *)nullptr, 0, t, N, nrhs, 0.0, act, g->st);
+    precond_into(g, t, N, V + (size_t)(j + 1) * N, sV, nrhs, act);
+}
+
 // One Arnoldi step j for all right-hand sides still stepping.
 void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
     const size_t N = g->N;
@@ -185,14 +240,19 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
     double2 *hb = g->hbuf.as<double2>();
     double *nrm = g->nrm.as<double>();
     const int *act = g->act_it.as<int>();
-    if (g->opt.precond != HELM_PRECOND_NONE) apply_precond_j(g, j, nrhs, act);
+    const bool left = left_side(g);
+    if (g->opt.precond != HELM_PRECOND_NONE && !(left && g->opt.side == HELM_SIDE_LEFT))
+        apply_precond_j(g, j, nrhs, act);
     double2 *w = V + (size_t)(j + 1) * N;
     const int nvec = j + 1;
     const int mode = g->opt.reorth;      // 0: CGS once, 1: CGS twice, 2: twice only when needed
     // complex128 basis with a plain first Gram-Schmidt pass: H z_j is formed
     // inside that pass (k_multidot_h); otherwise by its own kernel
-    const bool fuse_h = g->opt.precision != HELM_PREC_MIXED_DS && mode != 2;
-    if (!fuse_h) apply_H_j(g, j, nrhs, act);
+    const bool fuse_h = !left && !g->has_rho && g->opt.precision != HELM_PREC_MIXED_DS && mode != 2;
+    if (left)
+        apply_left_j(g, j, nrhs, act);
+    else if (!fuse_h)
+        apply_H_j(g, j, nrhs, act);
     if (g->opt.precision == HELM_PREC_MIXED_DS) {
         float4 *Vd = g->V.as<float4>();
         float4 *wd = Vd + (size_t)(j + 1) * N;
@@ -224,6 +284,14 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
         launch_reorth_flags(act, hb, hb + nv, 2 * nv, nvec, nrm, 0.5, act2, nvec, nrhs, st);
         launch_multidot(V, sV, nvec, w, sV, N, hb + nv, 2 * nv, nrhs, act2, ks, st);
         launch_multiaxpy(V, sV, nvec, hb + nv, 2 * nv, w, sV, N, nrm, nrhs, act2, ks, st);
+    } else if (!fuse_h) {
+        // w was formed by its own kernels (M^-1 H x_j): classical Gram-Schmidt
+        launch_multidot(V, sV, nvec, w, sV, N, hb, 2 * nv, nrhs, act, ks, st);
+        launch_multiaxpy(V, sV, nvec, hb, 2 * nv, w, sV, N, mode ? nullptr : nrm, nrhs, act, ks, st);
+        if (mode) {
+            launch_multidot(V, sV, nvec, w, sV, N, hb + nv, 2 * nv, nrhs, act, ks, st);
+            launch_multiaxpy(V, sV, nvec, hb + nv, 2 * nv, w, sV, N, nrm, nrhs, act, ks, st);
+        }
     } else {
         const LevelView<double> L0 = level_view<double>(g, 0);
         if (g->opt.precond == HELM_PRECOND_NONE)
@@ -267,6 +335,9 @@ long long graph_key_of(const helm_grid *g, int nrhs, double tol) {
     mixd(g->alpha); mixd(g->beta1); mixd(g->beta2); mixd(g->opt.omega_jacobi); mixd(tol);
     mixu((unsigned long long)nrhs); mixu(g->opt.restart); mixu(g->opt.precond); mixu(g->opt.precision);
     mixu(g->opt.nu1); mixu(g->opt.nu2); mixu(g->opt.reorth); mixu(g->opt.max_iters);
+    mixu((unsigned long long)g->opt.side + 101);
+    mixu(g->has_rho ? 7u : 3u);
+    for (const auto &L : g->lv) { mixp(L.rho64.p); mixp(L.rho32.p); }
     mixu(prof_on() ? 1u : 0u);
     return (long long)(ph & 0x7fffffffffffffffull);
 }
@@ -357,12 +428,28 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         cudaMemsetAsync(u, 0, (size_t)nrhs * N * sizeof(double2), st);
     // r_0: into basis slot 0 (complex128 basis) or the residual buffer (double-single basis)
     const bool ds = g->opt.precision == HELM_PREC_MIXED_DS;
+    const bool left = left_side(g);
     double2 *rvec = ds ? g->rbuf.as<double2>() : V;
     const size_t sr = ds ? N : sV;
-    if (!warm) launch_convert<double2, double2>(f, N, rvec, sr, N, nrhs, st);
-    launch_norm2(f, N, N, nrm, nrhs, nullptr, ks, st);
+    if (left) {
+        // preconditioned system: ||M^-1 f|| is the reference of every test;
+        // M^-1 f is r_0 from x0 = 0
+        precond_into(g, f, N, V, sV, nrhs, nullptr);
+        launch_norm2(V, sV, N, nrm, nrhs, nullptr, ks, st);
+    } else {
+        if (!warm) launch_convert<double2, double2>(f, N, rvec, sr, N, nrhs, st);
+        launch_norm2(f, N, N, nrm, nrhs, nullptr, ks, st);
+    }
     launch_cycle_init(S, nrm, nrhs, g->hflag, st);
-    if (warm) {
+    if (warm && left) {
+        launch_zero_inactive(u, N, S.act_cy, nrhs, st);
+        double2 *t = g->rbuf.as<double2>();
+        launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, t, N, nrhs, 0.0,
+                                                 S.act_cy, st);
+        precond_into(g, t, N, V, sV, nrhs, S.act_cy);
+        launch_norm2(V, sV, N, nrm, nrhs, S.act_cy, ks, st);
+        launch_cycle_check(S, nrm, nrhs, tol, g->opt.max_iters, g->hflag, st);
+    } else if (warm) {
         // a right-hand side f = 0 has the solution 0 whatever x0 was; the
         // others start from r_0 = f - H x0, and one whose x0 already meets
         // the tolerance ends here with no iteration (the end-of-cycle test)
@@ -405,7 +492,9 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         // end of cycle: y = R^-1 g, x += Z y, r = f - H x into slot 0, ||r||^2
         launch_backsolve(S, g->yv.as<double2>(), nrhs, st);
         // each right-hand side uses only the S.k columns it filled in this cycle
-        if (g->opt.precond == HELM_PRECOND_NONE && ds)
+        if (left && g->opt.side == HELM_SIDE_LEFT)
+            launch_update<double2>(V, sV, m, g->yv.as<double2>(), m, u, N, N, nrhs, S.act_cy, st, S.k);
+        else if (g->opt.precond == HELM_PRECOND_NONE && ds)
             launch_update_ds(g->V.as<float4>(), sV, m, g->yv.as<double2>(), m, u, N, N, nrhs,
                              S.act_cy, st, S.k);
         else if (g->opt.precond == HELM_PRECOND_NONE)
@@ -420,11 +509,32 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         else
             launch_update<float2>(g->Z.as<float2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u, N,
                                   N, nrhs, S.act_cy, st, S.k);
-        launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, rvec, sr,
-                                                 nrhs, 0.0, S.act_cy, st);
-        launch_norm2(rvec, sr, N, nrm, nrhs, S.act_cy, ks, st);
+        if (left) {
+            // r = M^-1 (f - H u) into slot 0
+            double2 *t = g->rbuf.as<double2>();
+            launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, t, N, nrhs,
+                                                     0.0, S.act_cy, st);
+            precond_into(g, t, N, V, sV, nrhs, S.act_cy);
+            launch_norm2(V, sV, N, nrm, nrhs, S.act_cy, ks, st);
+        } else {
+            launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, rvec, sr,
+                                                     nrhs, 0.0, S.act_cy, st);
+            launch_norm2(rvec, sr, N, nrm, nrhs, S.act_cy, ks, st);
+        }
         launch_cycle_check(S, nrm, nrhs, tol, g->opt.max_iters, g->hflag, st);
         if ((s = sync_stream(g, "cycle end"))) return s;
+    }
+    std::vector<double> true_rel;
+    if (left) {
+        // the cycles stopped on the preconditioned residual; report the true one
+        double2 *t = g->rbuf.as<double2>();
+        double *tn = g->tnrm.as<double>();
+        launch_stencil<double, double2, double2>(ST_RESID, L0, shift_H(g), u, N, f, N, t, N, nrhs, 0.0,
+                                                 nullptr, st);
+        launch_norm2(t, N, N, tn, nrhs, nullptr, ks, st);
+        launch_norm2(f, N, N, tn + nrhs, nrhs, nullptr, ks, st);
+        true_rel.resize(2 * (size_t)nrhs);
+        cudaMemcpyAsync(true_rel.data(), tn, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st);
     }
     std::vector<int> its(nrhs), stat(nrhs);
     std::vector<double> rel(nrhs);
@@ -434,6 +544,10 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
     if ((s = sync_stream(g, "solve end"))) return s;
     bool all_conv = true, any_broke = false;
     for (int k = 0; k < nrhs; ++k) {
+        if (left) {
+            const double fn2 = true_rel[(size_t)nrhs + k];
+            rel[k] = fn2 > 0.0 ? std::sqrt(true_rel[k] / fn2) : 0.0;
+        }
         if (iterations) iterations[k] = its[k];
         if (relres_out) relres_out[k] = rel[k];
         all_conv = all_conv && stat[k] == ST_CONVERGED;
@@ -556,6 +670,7 @@ helm_status helm_apply_H_ds(helm_grid *g, const helm_c128 *x, helm_c128 *y) {
     clear_error();
     if (!g || !x || !y) return fail(HELM_ERR_ARG, "null argument");
     if (!g->has_model) return fail(HELM_ERR_STATE, "helm_set_model has not been called");
+    if (g->has_rho) return fail(HELM_ERR_UNSUPPORTED, "the double-single H has no variable density");
     const size_t N = g->N;
     const size_t bytes = N * sizeof(double2);
     const void *xd;

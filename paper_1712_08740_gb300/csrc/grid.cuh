@@ -33,6 +33,7 @@ struct MGLevel {
     double h = 0.0;
     size_t N = 0;
     DevBuf m;                  // slowness on this level (injected)
+    DevBuf rho64, rho32;       // rho of Eq. 1 (variable density only; injected)
     DevBuf w64, w32;           // omega^2 m^2
     DevBuf dinv;               // 1 / diagonal of M, V-cycle precision (complex)
     DevBuf u, t, b, r;         // V-cycle work vectors, [cap_rhs][N] in the V-cycle type
@@ -48,6 +49,7 @@ struct helm_grid {
     cudaStream_t st = 0;
     helm_options opt{};
     bool has_model = false;
+    bool has_rho = false;      // a variable density (Eq. 1) is set
     bool ready = false;        // hierarchy + coarse inverse match model/shift/options
     double omega = 0.0, alpha = 0.0, beta1 = 1.0, beta2 = 0.5;
 
@@ -61,11 +63,13 @@ struct helm_grid {
     int cpart_rhs = 0;                  // right-hand sides cpart/cticket are sized for
 
     // Krylov workspace
-    int cap_rhs = 0, cap_m = 0, cap_prec = -1;
+    int cap_rhs = 0, cap_m = 0, cap_prec = -1, cap_side = -1;
     helm::DevBuf V, Z, hbuf, nrm, yv, partial, counter, act_it, act_cy, act2, flag;
     helm::DevBuf cR, cg, ccs, csn, cfn, cbeta, crel, ck, cits, cstat, cany, cQ;   // FGMRES state
     helm::DevBuf fst, ust, xst, yst;    // staging for host pointers / helper vectors
-    helm::DevBuf rbuf;                  // residuals in complex128 (double-single basis)
+    helm::DevBuf rbuf;                  // residuals in complex128 (double-single basis), or H x
+                                        // before M^-1 (left and two-sided preconditioning)
+    helm::DevBuf tnrm;                  // true-residual norms of the left/two-sided sides
     helm::DevBuf hdiag;                 // diagonal of H as double-single pairs
     bool hdiag_ok = false;              // hdiag matches the current model
     int *hflag = nullptr;               // host-mapped "any right-hand side active" flag

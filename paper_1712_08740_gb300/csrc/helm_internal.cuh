@@ -9,6 +9,13 @@
 // boundary node (centred ghost node of the absorbing condition) and c = 0
 // for the missing outer neighbour. s = 1 - j alpha gives H (Eq. 2-3);
 // s = beta1 - j beta2 gives the shifted Laplacian M (Eq. 6).
+//
+// Variable density (Eq. 1, -div(rho grad u) in place of -Lap u): each
+// neighbour weight is multiplied by the face coefficient, the mean of rho at
+// the node and at that neighbour (the inward weight of a boundary node stays
+// doubled), the Laplacian part of d_p is the sum of those weights over h^2,
+// and a boundary face adds (2/h) j (kappa_p / sqrt(rho_p)) times the face
+// coefficient of the inner face instead of (2/h) j kappa_p.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -97,6 +104,7 @@ template <typename T> struct LevelView {
     T two_over_h;            // 2 / h
     const T *w;              // omega^2 m^2 per node
     const cplx_t<T> *dinv;   // 1 / diagonal of M per node (fused V-cycle), or null
+    const T *rho;            // rho of Eq. 1 per node (variable density), or null (rho = 1)
 };
 
 // Shift of the zero-order term and the boundary factor q = sqrt(1 - j alpha).
@@ -213,7 +221,7 @@ void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
 int num_tile_shapes(int dim);
 bool tile_shape(int dim, int kernel, int shape, int ext[3], int *threads);
 // automatic shape for a fine level of `fine` nodes and nb right-hand sides:
-// the first shape in list order whose grid has at least 2 x 152 blocks, else
+// the first shape in list order whose grid has at least 2 blocks per SM, else
 // the shape with the most blocks (small levels need every SM)
 int auto_tile_shape(int dim, int kernel, const int fine[3], int nb);
 void prepare_vfused();   // sets shared-memory attributes; call outside graph capture
@@ -223,6 +231,8 @@ void prepare_vfused();   // sets shared-memory attributes; call outside graph ca
 // not finite or not > 0
 void launch_make_w(const double *m, size_t n, double omega, double *w64, float *w32, int *flag,
                    cudaStream_t st);
+// rho32 = float(rho64); flag |= 1 where rho is not finite or not > 0
+void launch_make_rho(const double *rho64, size_t n, float *rho32, int *flag, cudaStream_t st);
 // coarse[I] = fine[2 I] (injection) on an nx x ny x nz coarse grid
 template <typename T>
 void launch_inject(const T *fine, int fnx, int fny, T *coarse, int cnx, int cny, int cnz,
@@ -260,7 +270,11 @@ void prepare_coarse_kernels();   // shared-memory attributes; call outside graph
 // ------------------------------------------------------------ Krylov (complex128 outer)
 // All vectors of right-hand side k sit at base + k * stride_rhs; basis vector i
 // of right-hand side k at V + k * stride_rhs + i * N.
-constexpr int kMaxBlocks = 8 * 152;   // reduction grids: up to 8 blocks per SM
+constexpr int kMaxBlocks = 8 * 152;   // reduction grids: at most this many blocks (scratch size)
+
+// Number of SMs of the current device (read once per device and cached).
+// Grid shapes derive from it, so every sum's order is fixed per device.
+int device_sms();
 
 struct KrylovScratch {
     double2 *partial;        // [nrhs][max_blocks][nvec_max] block partial sums
@@ -315,6 +329,9 @@ void launch_multidot_ds(const float4 *V, size_t sV, int nvec, const float4 *w, s
 void launch_multiaxpy_ds(const float4 *V, size_t sV, int nvec, const double2 *c, size_t c_stride,
                          float4 *w, size_t sw, size_t N, double *norm2, int nrhs, const int *active,
                          KrylovScratch &ks, cudaStream_t st);
+// time limit (ns) of the consumer waits of the streamed double-single kernels
+// on the current device (synchronous copy to a device variable)
+cudaError_t set_consumer_wait_ns(unsigned long long ns);
 // y = x / sqrt(norm2[k]) with x complex128 or DS, y DS
 template <typename CIn>
 void launch_scale_ds(const CIn *x, size_t sx, const double *norm2, float4 *y, size_t sy, size_t N,

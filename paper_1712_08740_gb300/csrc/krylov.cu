@@ -445,10 +445,11 @@ __global__ void k_zero_inactive(double2 *__restrict__ x, size_t N, const int *__
 // two, four or eight blocks per SM, so that no SM runs an extra block while
 // the others idle, with roughly `per_thread` points per thread.
 inline int sm_blocks_for(size_t N, int per_thread, int cap) {
-    const size_t per_wave = (size_t)152 * kThreads * per_thread;
+    const int sms = device_sms();
+    const size_t per_wave = (size_t)sms * kThreads * per_thread;
     int k = 1;
-    while (k < 8 && (size_t)k * per_wave < N && 152 * 2 * k <= cap) k *= 2;
-    return 152 * k <= cap ? 152 * k : cap;
+    while (k < 8 && (size_t)k * per_wave < N && sms * 2 * k <= cap) k *= 2;
+    return sms * k <= cap ? sms * k : cap;
 }
 
 inline int blocks_for(size_t N, int per_block, int cap) {

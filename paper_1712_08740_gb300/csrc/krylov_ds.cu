@@ -142,12 +142,22 @@ template <int S> __device__ __forceinline__ void ring_init(uint64_t (&full)[S], 
 }
 
 // Producer teardown: wait (bounded) for the copies of the last stages issued
-// (the stages issued always form a prefix 0 .. issued - 1).
+// (the stages issued always form a prefix 0 .. issued - 1; a slot is reused
+// only after its previous copy was consumed, so earlier stages have landed).
+// Each stage gets its own bounded wait, so one late copy does not cut the
+// wait for the others short.
 template <int S> __device__ __forceinline__ void ring_drain(uint64_t (&full)[S], unsigned issued) {
     const unsigned k0 = issued > (unsigned)S ? issued - S : 0u;
-    for (unsigned k = k0; k < issued; ++k)
-        if (!pipe::mbar_wait_drain(&full[k % S], (k / S) & 1u)) return;
+    for (unsigned k = k0; k < issued; ++k) pipe::mbar_wait_drain(&full[k % S], (k / S) & 1u);
 }
+
+// Time limit of the consumers' waits for a copy to land. The default is the
+// pipeline's own bound; helm_set_wait_limit_ns lowers it to make those waits
+// run out on purpose (tests of the timeout path). Producer and teardown waits
+// keep the default, so no block exits with a copy in flight.
+__device__ unsigned long long g_cons_wait_ns = pipe::kWaitNs;
+
+__device__ __forceinline__ bool aborted(const int &abort) { return *(volatile const int *)&abort != 0; }
 
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ll); }
 
@@ -179,7 +189,9 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
                         const size_t p0 = (size_t)tl * kDotTile;
                         const unsigned bytes = (unsigned)min((size_t)kDotTile, N - p0) * 16u;
                         const int s = (int)(k % kDotStages);
-                        if (!pipe::mbar_wait(&S.empty[s], ((k / kDotStages) & 1u) ^ 1u, &S.abort)) continue;
+                        if (!pipe::mbar_wait(&S.empty[s], ((k / kDotStages) & 1u) ^ 1u, &S.abort) ||
+                            aborted(S.abort))
+                            continue;
                         pipe::mbar_arrive_expect_tx(&S.full[s], bytes * (nq + 1));
                         pipe::bulk_load(&S.slot[s][0][0], wr + p0, bytes, &S.full[s]);
                         for (int q = 0; q < nq; ++q)
@@ -196,6 +208,7 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
     }
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const int t = threadIdx.x;
+    const unsigned long long wait_ns = g_cons_wait_ns;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         const int r = it / nch, c = it % nch;
         if (active && !active[r]) continue;
@@ -212,7 +225,7 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
             for (int tl = t0; tl < t1; ++tl, ++k) {
                 const int nodes = (int)min((size_t)kDotTile, N - (size_t)tl * kDotTile);
                 const int s = (int)(k % kDotStages);
-                const bool ok = pipe::mbar_wait(&S.full[s], (k / kDotStages) & 1u, &S.abort);
+                const bool ok = pipe::mbar_wait(&S.full[s], (k / kDotStages) & 1u, &S.abort, wait_ns);
                 const bool in = ok && t < nodes;
                 const float4 x = in ? S.slot[s][0][t] : zero;
                 float4 v[kGroup];
@@ -307,7 +320,9 @@ k_multiaxpy_ds(const float4 *__restrict__ V, size_t sV, int nvec, const double2 
                 const float4 *Vr = V + r * sV, *wr = w + r * sw;
                 for (int i = -1; i < nvec; ++i, ++k) {
                     const int s = (int)(k % kAxpyStages);
-                    if (!pipe::mbar_wait(&S.empty[s], ((k / kAxpyStages) & 1u) ^ 1u, &S.abort)) continue;
+                    if (!pipe::mbar_wait(&S.empty[s], ((k / kAxpyStages) & 1u) ^ 1u, &S.abort) ||
+                        aborted(S.abort))
+                        continue;
                     pipe::mbar_arrive_expect_tx(&S.full[s], bytes);
                     pipe::bulk_load(&S.slot[s][0], i < 0 ? wr + p0 : Vr + (size_t)i * N + p0, bytes, &S.full[s]);
                     issued = k + 1;
@@ -321,9 +336,10 @@ k_multiaxpy_ds(const float4 *__restrict__ V, size_t sV, int nvec, const double2 
     }
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const int t = threadIdx.x;
+    const unsigned long long wait_ns = g_cons_wait_ns;
     auto take = [&](int nodes, float4 (&a)[NPT]) {
         const int s = (int)(k % kAxpyStages);
-        const bool ok = pipe::mbar_wait(&S.full[s], (k / kAxpyStages) & 1u, &S.abort);
+        const bool ok = pipe::mbar_wait(&S.full[s], (k / kAxpyStages) & 1u, &S.abort, wait_ns);
 #pragma unroll
         for (int m = 0; m < NPT; ++m) a[m] = (ok && t + m * kCons < nodes) ? S.slot[s][t + m * kCons] : zero;
         __syncwarp();
@@ -558,10 +574,14 @@ void set_pipe_attrs() {
     (void)once;
 }
 int pipe_grid(int items, int per_sm) {
-    const int cap = 152 * per_sm;
+    const int cap = device_sms() * per_sm;
     return items < cap ? (items > 0 ? items : 1) : cap;
 }
 }  // namespace
+
+cudaError_t set_consumer_wait_ns(unsigned long long ns) {
+    return cudaMemcpyToSymbol(g_cons_wait_ns, &ns, sizeof ns);
+}
 
 size_t ds_partial_per_rhs(size_t N, int nvec_max) {
     const size_t dot = (size_t)nvec_max * ceil_div(ceil_div(N, kDotTile), kDotTpi) * kConsWarps;

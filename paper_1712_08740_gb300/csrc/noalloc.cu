@@ -1,13 +1,12 @@
 // True relative residual ||f - H u|| / ||f|| without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (allocation is not a capturable operation and
-// invalidates the capture), services that run under a fixed device-memory
-// budget handed out by their own allocator, and latency-critical loops that
-// must not pay for allocation. helm_true_residual may allocate staging and
-// reduction buffers on its first use; this variant never does. Its scratch is
-// one file-scope device array of a fixed size, so it serves at most
-// kNaMaxRhs right-hand sides per call.
+// Some callers cannot call cudaMalloc: a serving process that reserves the
+// GPU's memory up front and hands it out from its own pool leaves nothing for
+// cudaMalloc to take, and a caller that must not stall other streams cannot
+// afford cudaMalloc/cudaFree, which may synchronise the device.
+// helm_true_residual may allocate staging and reduction buffers on its first
+// use; this variant never does. Its scratch is one file-scope device array of
+// a fixed size, so it serves at most kNaMaxRhs right-hand sides per call.
 //
 // The residual and the norms are fused into one kernel: each thread forms
 // r_p = f_p - (H u)_p in registers and accumulates |r_p|^2 and |f_p|^2, so
@@ -24,7 +23,7 @@ namespace helm {
 namespace {
 
 constexpr int kNaMaxRhs = 64;       // right-hand sides per call
-constexpr int kNaBlocks = 2 * 152;  // reduction grid: two blocks per SM
+constexpr int kNaBlocks = 304;      // reduction grid (fixed, so the summation order is too)
 constexpr int kNaThreads = 256;
 // layout of the scratch: partial sums [rhs][2][block], results [rhs][2],
 // then one ticket counter per right-hand side
@@ -164,8 +163,23 @@ extern "C" helm_status helm_true_residual_noalloc(helm_grid *g, int nrhs, const 
         return fail(HELM_ERR_ARG, "nrhs = %d is outside 1..%d, the size of the static scratch", nrhs,
                     kNaMaxRhs);
     if (!g->has_model) return fail(HELM_ERR_STATE, "helm_set_model has not been called");
+    if (g->has_rho) return fail(HELM_ERR_UNSUPPORTED, "variable density is not served by this entry point");
     if (!is_device_ptr(f) || !is_device_ptr(u))
         return fail(HELM_ERR_ARG, "f and u must be device pointers (this entry point stages nothing)");
+    {
+        // both arrays must live on the current device: another device's
+        // memory would be read through the wrong address space
+        int cur = -1;
+        cudaPointerAttributes af, au;
+        if (cudaGetDevice(&cur) != cudaSuccess || cudaPointerGetAttributes(&af, f) != cudaSuccess ||
+            cudaPointerGetAttributes(&au, u) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HELM_ERR_CUDA, "pointer attributes");
+        }
+        if ((af.type == cudaMemoryTypeDevice && af.device != cur) ||
+            (au.type == cudaMemoryTypeDevice && au.device != cur))
+            return fail(HELM_ERR_ARG, "f and u must be device pointers of the current device %d", cur);
+    }
     void *scr = nullptr;
     helm_status s = na_scratch(&scr);
     if (s) return s;

@@ -12,7 +12,10 @@
 // block's abort word; from then on no wait of the block blocks again, the
 // kernel walks the rest of its control flow (every named barrier included)
 // without data and reports NaN, and the producer waits, again bounded, for
-// the copies it already issued before the block exits.
+// the copies it already issued before the block exits. A consumer that gives
+// up still releases its slot, so the producer re-reads the abort word after
+// every wait on a released slot and issues no copy into a slot whose last
+// copy may still be landing (the abort store is ordered before the release).
 #pragma once
 #include <cstdint>
 
@@ -57,6 +60,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, unsigned parity) {
     return ok != 0;
 }
 
+// non-blocking test of the same phase (try_wait may suspend the thread for a
+// while before it reports an unfinished phase; test_wait returns at once)
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -64,16 +81,24 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Wait until the phase of parity `parity` of barrier b has completed. Returns
-// false at once when *abort is set, and false (setting *abort) after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, volatile int *abort) {
+// false at once when *abort is set, and false (setting *abort) after limit_ns.
+// A limit below 1 us gives up at the first check that finds the phase
+// unfinished (a non-blocking test): the form tests use to make waits run out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, volatile int *abort,
+                                          unsigned long long limit_ns = kWaitNs) {
     if (*abort) return false;
+    if (limit_ns < 1000ull) {
+        if (mbar_test_wait(b, parity)) return true;
+        *abort = 1;
+        return false;
+    }
     if (mbar_try_wait(b, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned n = 1;; ++n) {
         if (mbar_try_wait(b, parity)) return true;
         if ((n & 31) == 0) {
             if (*abort) return false;
-            if (global_ns() - t0 > kWaitNs || n > (1u << 30)) {
+            if (global_ns() - t0 > limit_ns || n > (1u << 30)) {
                 *abort = 1;
                 return false;
             }

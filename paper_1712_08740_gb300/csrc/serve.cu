@@ -125,6 +125,8 @@ size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o)
     if (o.precision == HELM_PREC_MIXED_DS) {
         add(nrhs * N * 16.0);                            // complex128 residuals
         add(N * 16.0);                                   // diagonal of H, double-single
+    } else if (o.side != HELM_SIDE_RIGHT && o.precond != HELM_PRECOND_NONE) {
+        add(nrhs * N * 16.0);                            // H x before M^-1
     }
     add((double)nrhs * (m + 1.0) * m * 16.0);            // rotated Hessenberg R
     add((double)nrhs * (m + 1.0) * (m + 1.0) * 16.0);    // rotation product Q
@@ -244,11 +246,22 @@ void dispatch_loop(helm_server *S) {
         size_t others = 0;
         for (auto &w : S->workers)
             if (w.get() != pick) others += w->held;
+        // grids dropped here are freed after the lock is released: freeing
+        // device memory synchronises the device, and the workers' completions
+        // must not wait for that behind the server lock
+        std::vector<helm_grid *> doomed;
+        auto release = [&] {
+            if (doomed.empty()) return;
+            lk.unlock();
+            for (helm_grid *dg : doomed) helm_destroy_grid(dg);
+            lk.lock();
+            doomed.clear();
+        };
         if (others + need > S->budget) {
             // make room by dropping grids cached by idle workers
             for (auto &w : S->workers) {
                 if (w.get() == pick || w->busy || !w->grid) continue;
-                helm_destroy_grid(w->grid);
+                doomed.push_back(w->grid);
                 w->grid = nullptr;
                 others -= w->held;
                 w->held = 0;
@@ -263,13 +276,18 @@ void dispatch_loop(helm_server *S) {
                 r->t_admit = r->t_done = S->now();
                 r->done = true;
                 S->cv_done.notify_all();
+                release();
+                continue;
+            }
+            if (!doomed.empty()) {
+                release();   // state may have changed meanwhile: decide again
                 continue;
             }
             S->cv_disp.wait(lk);   // wait for a running request to release memory
             continue;
         }
         if (!reuse && pick->grid) {
-            helm_destroy_grid(pick->grid);
+            doomed.push_back(pick->grid);
             pick->grid = nullptr;
         }
         S->queue.pop_front();
@@ -278,6 +296,7 @@ void dispatch_loop(helm_server *S) {
         pick->busy = true;
         pick->job = r;
         S->cv_work.notify_all();
+        release();
     }
 }
 

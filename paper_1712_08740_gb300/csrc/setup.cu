@@ -57,6 +57,18 @@ __global__ void k_make_w(const double *__restrict__ m, size_t n, double om2,
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+__global__ void k_make_rho(const double *__restrict__ rho, size_t n, float *__restrict__ rho32,
+                           int *__restrict__ flag) {
+    int bad = 0;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (size_t)gridDim.x * blockDim.x) {
+        const double v = rho[p];
+        bad |= !(isfinite(v) && v > 0.0);
+        rho32[p] = __double2float_rn(v);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && flag) atomicOr(flag, 1);
+}
+
 template <typename T>
 __global__ void k_inject(const T *__restrict__ fine, int fnx, int fny, T *__restrict__ coarse,
                          int cnx, int cny, int cnz) {
@@ -70,6 +82,23 @@ __global__ void k_inject(const T *__restrict__ fine, int fnx, int fny, T *__rest
     }
 }
 }  // namespace
+
+int device_sms() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+        cudaGetLastError();
+        v = 152;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
 
 void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 void uncount_launch(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
@@ -136,6 +165,13 @@ void launch_make_w(const double *m, size_t n, double omega, double *w64, float *
     size_t b = (n + 255) / 256;
     int nb = (int)(b < 4096 ? (b ? b : 1) : 4096);
     k_make_w<<<nb, 256, 0, st>>>(m, n, omega * omega, w64, w32, flag);
+    count_launch();
+}
+
+void launch_make_rho(const double *rho64, size_t n, float *rho32, int *flag, cudaStream_t st) {
+    size_t b = (n + 255) / 256;
+    int nb = (int)(b < 4096 ? (b ? b : 1) : 4096);
+    k_make_rho<<<nb, 256, 0, st>>>(rho64, n, rho32, flag);
     count_launch();
 }
 

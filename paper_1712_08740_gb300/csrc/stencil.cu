@@ -41,7 +41,40 @@ __device__ __forceinline__ void axis_terms(const CIn *__restrict__ x, size_t p, 
     }
 }
 
-template <typename T, int DIM, int MODE, typename CIn, typename COut>
+// The same with the face coefficients of Eq. 1: each neighbour weight is
+// c times the mean of rho at the node and the neighbour; dsum collects the
+// weights (the Laplacian part of the diagonal) and bsum, per boundary face,
+// the coefficient of the inner face (the absorbing term's factor). With
+// LOADX false only the weights are formed (the first Jacobi sweep).
+template <typename T, bool LOADX, typename CIn>
+__device__ __forceinline__ void axis_terms_rho(const CIn *__restrict__ x, const T *__restrict__ rho, T rp,
+                                               size_t p, int i, int n, size_t stride, T &sre, T &sim,
+                                               T &dsum, T &bsum) {
+    if (i > 0) {
+        const T face = T(0.5) * (rp + rho[p - stride]);
+        const T c = (i == n - 1) ? T(2) * face : face;
+        if (LOADX) {
+            auto v = cvt<cplx_t<T>>(x[p - stride]);
+            sre += c * v.x;
+            sim += c * v.y;
+        }
+        dsum += c;
+        if (i == n - 1) bsum += face;
+    }
+    if (i < n - 1) {
+        const T face = T(0.5) * (rp + rho[p + stride]);
+        const T c = (i == 0) ? T(2) * face : face;
+        if (LOADX) {
+            auto v = cvt<cplx_t<T>>(x[p + stride]);
+            sre += c * v.x;
+            sim += c * v.y;
+        }
+        dsum += c;
+        if (i == 0) bsum += face;
+    }
+}
+
+template <typename T, int DIM, int MODE, bool RHO, typename CIn, typename COut>
 __global__ void __launch_bounds__(kBX)
 k_stencil(LevelView<T> L, OpShift<T> s, const CIn *__restrict__ x, size_t sx,
           const COut *__restrict__ b, size_t sb, COut *__restrict__ y, size_t sy, T wj,
@@ -59,7 +92,22 @@ k_stencil(LevelView<T> L, OpShift<T> s, const CIn *__restrict__ x, size_t sx,
         const size_t p = (size_t)row * nx + ix;
         T sre = 0, sim = 0;
         int nf = 0;
-        if (MODE != ST_JACOBI0) {
+        T dsum = 0, bsum = 0;
+        if (RHO) {
+            constexpr bool LX = MODE != ST_JACOBI0;
+            const T rp = L.rho[p];
+            axis_terms_rho<T, LX>(x, L.rho, rp, p, ix, nx, 1, sre, sim, dsum, bsum);
+            if (DIM >= 2) {
+                const int iy = (DIM == 3) ? row % L.ny : row;
+                axis_terms_rho<T, LX>(x, L.rho, rp, p, iy, L.ny, (size_t)nx, sre, sim, dsum, bsum);
+            }
+            if (DIM == 3) {
+                const int iz = row / L.ny;
+                axis_terms_rho<T, LX>(x, L.rho, rp, p, iz, L.nz, (size_t)nx * L.ny, sre, sim, dsum, bsum);
+            }
+            // kappa_p / sqrt(rho_p) on the boundary faces, weighted by their inner faces
+            bsum /= dsqrt<T>(rp);
+        } else if (MODE != ST_JACOBI0) {
             axis_terms<T>(x, p, ix, nx, 1, sre, sim, nf);
             if (DIM >= 2) {
                 const int iy = (DIM == 3) ? row % L.ny : row;
@@ -81,10 +129,10 @@ k_stencil(LevelView<T> L, OpShift<T> s, const CIn *__restrict__ x, size_t sx,
             }
         }
         const T wp = L.w[p];
-        T dre = T(2 * DIM) * L.inv_h2 - s.s_re * wp;
+        T dre = (RHO ? dsum : T(2 * DIM)) * L.inv_h2 - s.s_re * wp;
         T dim_ = -s.s_im * wp;
-        if (nf) {
-            const T f = T(nf) * L.two_over_h * dsqrt<T>(wp);
+        if (RHO ? bsum != T(0) : nf != 0) {
+            const T f = (RHO ? bsum : T(nf)) * L.two_over_h * dsqrt<T>(wp);
             dre -= f * s.q_im;     // j * kappa = sqrt(w) (-q_im + j q_re)
             dim_ += f * s.q_re;
         }
@@ -133,17 +181,24 @@ void dispatch_dim(const LevelView<T> &L, OpShift<T> s, const CIn *x, size_t sx, 
                   cudaStream_t st) {
     dim3 g = grid_for(L.nx, L.ny * L.nz, nb);
     prof_begin(st);
-    if (L.dim == 1)
-        k_stencil<T, 1, MODE><<<g, kBX, 0, st>>>(L, s, x, sx, b, sb, y, sy, wj, active);
+    if (L.rho) {
+        if (L.dim == 1)
+            k_stencil<T, 1, MODE, true><<<g, kBX, 0, st>>>(L, s, x, sx, b, sb, y, sy, wj, active);
+        else if (L.dim == 2)
+            k_stencil<T, 2, MODE, true><<<g, kBX, 0, st>>>(L, s, x, sx, b, sb, y, sy, wj, active);
+        else
+            k_stencil<T, 3, MODE, true><<<g, kBX, 0, st>>>(L, s, x, sx, b, sb, y, sy, wj, active);
+    } else if (L.dim == 1)
+        k_stencil<T, 1, MODE, false><<<g, kBX, 0, st>>>(L, s, x, sx, b, sb, y, sy, wj, active);
     else if (L.dim == 2)
-        k_stencil<T, 2, MODE><<<g, kBX, 0, st>>>(L, s, x, sx, b, sb, y, sy, wj, active);
+        k_stencil<T, 2, MODE, false><<<g, kBX, 0, st>>>(L, s, x, sx, b, sb, y, sy, wj, active);
     else
-        k_stencil<T, 3, MODE><<<g, kBX, 0, st>>>(L, s, x, sx, b, sb, y, sy, wj, active);
+        k_stencil<T, 3, MODE, false><<<g, kBX, 0, st>>>(L, s, x, sx, b, sb, y, sy, wj, active);
     count_launch();
     if (prof_on()) {
         // algorithmic traffic per node: x (except JACOBI0), b (RESID/JACOBI*), y, w
         const double n = (double)L.nx * L.ny * L.nz * nb;
-        double per = sizeof(COut) + sizeof(T);
+        double per = sizeof(COut) + sizeof(T) * (L.rho ? 2 : 1);
         if (MODE != ST_JACOBI0) per += sizeof(CIn);
         if (MODE != ST_APPLY) per += sizeof(COut);
         // flops: neighbour sums, diagonal, d*x - S/h^2, plus residual / damped update

@@ -196,7 +196,8 @@ helm_status helm_autotune(helm_grid *g, int nrhs, const helm_c128 *f, double tol
     helm_status s;
     if ((s = ensure_ready(g)) || (s = workspace_for(g, nrhs)) || (s = ensure_level_work(g, nrhs)))
         return s;
-    if ((flags & HELM_TUNE_TILES) && g->dim >= 2 && g->lv.size() > 1) {
+    // with a variable density the V-cycle runs the general kernels: no tiles to tune
+    if ((flags & HELM_TUNE_TILES) && g->dim >= 2 && g->lv.size() > 1 && !g->has_rho) {
         if (g->opt.precision == HELM_PREC_F64) s = tune_tiles<double, double2>(g, nrhs, rep);
         else if (g->opt.precision == HELM_PREC_MIXED) s = tune_tiles<float, double2>(g, nrhs, rep);
         else s = tune_tiles<float, float4>(g, nrhs, rep);

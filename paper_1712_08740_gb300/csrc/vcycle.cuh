@@ -43,6 +43,8 @@ template <typename T> inline LevelView<T> level_view(const helm_grid *g, int l) 
     // the inverse diagonal exists in the V-cycle's own precision only
     const bool match = (sizeof(T) == sizeof(double)) == (g->vc_prec == HELM_PREC_F64);
     v.dinv = match ? (const cplx_t<T> *)L.dinv.p : nullptr;
+    v.rho = !g->has_rho ? nullptr
+                        : (sizeof(T) == sizeof(double)) ? (const T *)L.rho64.p : (const T *)L.rho32.p;
     return v;
 }
 
@@ -101,7 +103,8 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
     const T wj = (T)g->opt.omega_jacobi;
     const int nu1 = g->opt.nu1, nu2 = g->opt.nu2;
     cudaStream_t st = g->st;
-    const bool fused = L > 1 && g->dim >= 2 && nu1 == 1 && nu2 == 1;
+    // the fused level kernels carry the constant-density stencil only
+    const bool fused = L > 1 && g->dim >= 2 && nu1 == 1 && nu2 == 1 && !g->has_rho;
     if (fused) {
         // down: u_l (pre-smoothed, into the level's scratch) and b_{l+1}
         for (int l = 0; l < L - 1; ++l) {

@@ -919,7 +919,7 @@ int auto_tile_shape(int dim, int kernel, const int fine[3], int nb) {
         tile_shape(dim, kernel, sh, e, &nt);
         long long blocks = (long long)nb * ((ext_of[0] + e[0] - 1) / e[0]) * ((ext_of[1] + e[1] - 1) / e[1]);
         if (dim == 3) blocks *= (ext_of[2] + e[2] - 1) / e[2];
-        if (blocks >= 2 * 152) return sh;
+        if (blocks >= 2 * (long long)device_sms()) return sh;
         if (blocks > best_blocks) {
             best_blocks = blocks;
             best = sh;

@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "HELM_OK", 1: "HELM_ERR_ARG", 2: "HELM_ERR_NOMEM", 3: "HELM_E
                 7: "HELM_ERR_STATE", 8: "HELM_ERR_UNSUPPORTED"}
 PRECOND = {"mg": 0, "exact": 1, "none": 2}
 PRECISION = {"f64": 0, "mixed": 1, "mixed_ds": 2}
+SIDE = {"right": 0, "left": 1, "split": 2}
 
 EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "helm_set_stream",
             "helm_set_options", "helm_get_options", "helm_set_model", "helm_set_shift",
@@ -34,14 +35,15 @@ EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "he
             "helm_time_kernel", "helm_true_residual_noalloc", "helm_solve_footprint",
             "helm_server_create", "helm_server_submit", "helm_server_wait", "helm_server_poll",
             "helm_server_clock", "helm_server_destroy", "helm_num_tile_shapes", "helm_tile_shape",
-            "helm_set_tiles", "helm_get_tiles", "helm_autotune")
+            "helm_set_tiles", "helm_get_tiles", "helm_autotune", "helm_set_wait_limit_ns",
+            "helm_set_density")
 
 
 class helm_options(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("precond", ctypes.c_int),
                 ("precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega_jacobi", ctypes.c_double), ("coarse_max", ctypes.c_int),
-                ("reorth", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("graphs", ctypes.c_int), ("side", ctypes.c_int)]
 
 
 class helm_server_config(ctypes.Structure):
@@ -103,6 +105,7 @@ def _load():
         "helm_get_options": (I, [P, ctypes.POINTER(helm_options)]),
         "helm_set_model": (I, [P, P, D, D]),
         "helm_set_shift": (I, [P, D, D]),
+        "helm_set_density": (I, [P, P]),
         "helm_solve": (I, [P, P, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "helm_solve_batch": (I, [P, I, P, D, P, P, P]),
         "helm_solve_batch_warm": (I, [P, I, P, D, P, P, P]),
@@ -115,6 +118,7 @@ def _load():
         "helm_level_info": (I, [P, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]),
         "helm_last_error": (ctypes.c_char_p, []),
         "helm_kernel_launches": (ctypes.c_uint64, []),
+        "helm_set_wait_limit_ns": (I, [ctypes.c_uint64]),
         "helm_profile_start": (I, []),
         "helm_profile_stop": (I, [ctypes.c_char_p, ctypes.c_size_t]),
         "helm_time_kernel": (I, [P, ctypes.c_char_p, I, I, ctypes.POINTER(D), ctypes.POINTER(D),
@@ -218,6 +222,11 @@ def helm_set_model(g, m, omega, alpha):
     _check(_lib.helm_set_model(g, _ptr(m, np.float64), float(omega), float(alpha)))
 
 
+def helm_set_density(g, rho):
+    """rho of Eq. 1 per node (None: constant density)."""
+    _check(_lib.helm_set_density(g, None if rho is None else _ptr(rho, np.float64)))
+
+
 def helm_set_shift(g, beta1, beta2):
     _check(_lib.helm_set_shift(g, float(beta1), float(beta2)))
 
@@ -271,9 +280,15 @@ def helm_true_residual(g, f, u):
 
 def helm_true_residual_noalloc(g, nrhs, f, u):
     """Relative residuals of nrhs device-resident pairs (f_k, u_k), computed by
-    the library without allocating device memory (see include/helm.h)."""
+    the library without allocating device memory (see include/helm.h).
+    ``g`` is a Grid: its node count bounds what f and u must hold."""
+    N = g.N
+    for name, a in (("f", f), ("u", u)):
+        size = a.numel() if hasattr(a, "numel") else np.size(a)
+        if size < int(nrhs) * N:
+            raise ValueError(f"{name} holds {size} values, fewer than nrhs * N = {int(nrhs) * N}")
     rel = np.zeros(int(nrhs), dtype=np.float64)
-    _check(_lib.helm_true_residual_noalloc(g, int(nrhs), _ptr(f, np.complex128),
+    _check(_lib.helm_true_residual_noalloc(g._g, int(nrhs), _ptr(f, np.complex128),
                                            _ptr(u, np.complex128),
                                            rel.ctypes.data_as(ctypes.c_void_p)))
     return rel
@@ -292,6 +307,11 @@ def helm_level_info(g, level):
 
 def helm_last_error():
     return _lib.helm_last_error().decode()
+
+
+def helm_set_wait_limit_ns(ns):
+    """Time limit of the streamed double-single kernels' copy waits (0: default)."""
+    _check(_lib.helm_set_wait_limit_ns(int(ns)))
 
 
 def helm_kernel_launches():
@@ -363,7 +383,8 @@ class Grid:
     """Owns one helm_grid. ``n`` is the node count per axis, x first."""
 
     def __init__(self, n, h, *, restart=30, precond="mg", precision="f64", nu1=1, nu2=1,
-                 omega_jacobi=0.8, coarse_max=1500, reorth=0, max_iters=5000, graphs=True):
+                 omega_jacobi=0.8, coarse_max=1500, reorth=0, max_iters=5000, graphs=True,
+                 side="right"):
         self.n = tuple(int(k) for k in n)
         self.N = int(np.prod(self.n))
         self.h = float(h)
@@ -371,7 +392,7 @@ class Grid:
         _live.add(self)
         self.set_options(restart=restart, precond=precond, precision=precision, nu1=nu1,
                          nu2=nu2, omega_jacobi=omega_jacobi, coarse_max=coarse_max,
-                         reorth=reorth, max_iters=max_iters, graphs=graphs)
+                         reorth=reorth, max_iters=max_iters, graphs=graphs, side=side)
 
     def set_options(self, **kw):
         o = helm_get_options(self._g)
@@ -384,6 +405,8 @@ class Grid:
                 v = int(bool(v))
             elif k == "reorth":
                 v = int(v)
+            elif k == "side":
+                v = SIDE[v]
             setattr(o, k, v)
         helm_set_options(self._g, o)
 
@@ -392,6 +415,9 @@ class Grid:
 
     def set_shift(self, beta1, beta2):
         helm_set_shift(self._g, beta1, beta2)
+
+    def set_density(self, rho):
+        helm_set_density(self._g, rho)
 
     def set_stream(self, stream):
         helm_set_stream(self._g, stream)
