@@ -133,6 +133,38 @@ def test_vcycle_matches_oracle_f64(helm, n, nu):
     assert rel(z.cpu().numpy(), ref) < 1e-10
 
 
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("mixed", 2e-4)])
+def test_fused_3d_vcycle_every_shape_matches_oracle(helm, precision, tol):
+    """The fused 3D V(1,1) level kernels (down: Jacobi from zero + residual +
+    full weighting; up: prolongation + Jacobi), every compiled tile shape,
+    including the down kernel that marches along z, element-wise against the
+    oracle's V-cycle. 65 x 65 x 49 nodes: the first coarse level has 25
+    planes, so the z-march (16 coarse planes per block) crosses a block
+    boundary, and every level has interior tiles."""
+    n, h, om, al, b, wj = (65, 65, 49), 10.0, 2 * np.pi * 10.0, 0.01, (1.0, 0.5), 0.8
+    m = rand_model(n, 31)
+    g = helm.Grid(n, h, precision=precision, nu1=1, nu2=1, omega_jacobi=wj)
+    g.set_model(dev(m), om, al)
+    g.set_shift(*b)
+    levels = mg.build_levels(n, h, m, om, al, *b, coarse_max=1500)
+    assert g.num_levels == len(levels) == 4
+    assert levels[1].n[2] > 16
+    r = rand_c(int(np.prod(n)), 32)
+    ref = mg.vcycle(levels, r, 1, 1, wj)
+    rd = dev(r)
+    for s in range(helm.helm_num_tile_shapes(3)):
+        for lev in range(g.num_levels - 1):
+            g.set_tiles(lev, s, s)
+        z = torch.empty_like(rd)
+        g.apply_precond(rd, z)
+        zc = z.cpu().numpy()
+        err = rel(zc, ref)
+        assert err < tol, (s, err)
+        # element by element, relative to the largest entry
+        assert np.abs(zc - ref).max() <= 10 * tol * np.abs(ref).max(), s
+    g.close()
+
+
 def test_vcycle_mixed_close_to_oracle(helm):
     n, h, om, al, b = (129, 65), 10.0, 2 * np.pi * 10.0, 0.01, (1.0, 0.5)
     m = rand_model(n, 7)
@@ -265,6 +297,16 @@ def test_solve_host_pointers_equal_device(helm):
 def test_solve_3d_small_mixed(helm):
     w = workload("3d_smooth_small")
     u, its, rr, m, f = solve_workload(helm, w, "mixed")
+    u_lu = direct.lu_solve(w.n, w.h, m, w.omega(), w.alpha, f).ravel()
+    assert rr <= 1e-8 and rel(u, u_lu) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed_ds"])
+def test_solve_3d_small_other_precisions(helm, precision):
+    """The 3D solve in complex128 and with the double-single basis (the form
+    the 3D benchmark runs) against sparse LU."""
+    w = workload("3d_smooth_small")
+    u, its, rr, m, f = solve_workload(helm, w, precision)
     u_lu = direct.lu_solve(w.n, w.h, m, w.omega(), w.alpha, f).ravel()
     assert rr <= 1e-8 and rel(u, u_lu) <= 1e-6
 

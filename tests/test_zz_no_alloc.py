@@ -1,13 +1,14 @@
 """The allocation-free residual entry point (helm_true_residual_noalloc).
 
-Callers that cannot call cudaMalloc (code inside a CUDA-graph stream capture,
-services that hand out device memory from a fixed budget, latency-critical
-loops) use this variant; it keeps its scratch in a static device array of
-the library. These tests call it through the C ABI and compare it with the
-allocating helm_true_residual on the same device data, on two calls in a
-row. The file is collected last so that a stop-at-first-failure run has
-already run every other test; it also passes alone in a fresh process
-(the first call there performs the one-time look-up of the array's address).
+Callers that cannot call cudaMalloc -- a serving process that reserved the
+GPU's memory up front for its own pool, or a caller that must not stall other
+streams on cudaMalloc/cudaFree -- use this variant; it keeps its scratch in a
+static device array of the library. These tests call it through the C ABI
+and compare it with the allocating helm_true_residual on the same device
+data, on two calls in a row, in 1D, 2D and 3D. The file is collected last so
+that a stop-at-first-failure run has already run every other test; it also
+passes alone in a fresh process (the first call there performs the one-time
+look-up of the array's address).
 """
 import numpy as np
 import pytest
@@ -40,12 +41,15 @@ def _pairs(nrhs, N, seed):
     return torch.from_numpy(a[0]).to("cuda:0"), torch.from_numpy(a[1]).to("cuda:0")
 
 
+# 1D, 2D and 3D grids: the kernel carries its own stencil for each dimension
+# (boundary faces, corner counts, plane strides)
+@pytest.mark.parametrize("n", [(101,), (130, 67), (17, 13, 9)])
 @pytest.mark.parametrize("nrhs", [1, 3])
-def test_noalloc_residual_matches_allocating_entry_point(helm, nrhs):
-    g = _grid(helm)
+def test_noalloc_residual_matches_allocating_entry_point(helm, n, nrhs):
+    g = _grid(helm, n=n)
     for call in range(2):                       # two calls in a row, new data each time
         F, U = _pairs(nrhs, g.N, seed=10 + call)
-        rel = helm.helm_true_residual_noalloc(g._g, nrhs, F, U)
+        rel = helm.helm_true_residual_noalloc(g, nrhs, F, U)
         for k in range(nrhs):
             ref = g.true_residual(F[k].contiguous(), U[k].contiguous())
             assert abs(rel[k] - ref) <= 1e-12 * ref
@@ -57,7 +61,7 @@ def test_noalloc_residual_of_a_solution(helm):
     f[2 * 65 + 32] = 1.0 / 100.0
     u = torch.empty_like(f)
     g.solve(f, 1e-9, u)
-    rel = helm.helm_true_residual_noalloc(g._g, 1, f, u)
+    rel = helm.helm_true_residual_noalloc(g, 1, f, u)
     assert rel[0] <= 1e-9 and abs(rel[0] - g.true_residual(f, u)) <= 1e-12
 
 
@@ -65,9 +69,11 @@ def test_noalloc_rejects_what_it_cannot_serve(helm):
     g = _grid(helm, n=(9, 7))
     F, U = _pairs(65, g.N, seed=1)
     with pytest.raises(helm.HelmError) as e:
-        helm.helm_true_residual_noalloc(g._g, 65, F, U)
+        helm.helm_true_residual_noalloc(g, 65, F, U)
     assert e.value.status == 1 and "static scratch" in e.value.message
     fh = np.zeros(g.N, dtype=np.complex128)
     with pytest.raises(helm.HelmError) as e:
-        helm.helm_true_residual_noalloc(g._g, 1, fh, fh)   # host arrays are not staged
+        helm.helm_true_residual_noalloc(g, 1, fh, fh)   # host arrays are not staged
     assert e.value.status == 1
+    with pytest.raises(ValueError):                      # too short for nrhs right-hand sides
+        helm.helm_true_residual_noalloc(g, 2, F[0].contiguous(), U[0].contiguous())
