@@ -16,7 +16,8 @@ Helmholtz equation, part 1: Data modelling"):
 * ``gmres``       -- restarted, right-preconditioned GMRES (Eq. 7), with the
                      flexible variant that stores the preconditioned vectors,
                      optionally from an initial guess; GMRES on the
-                     split-preconditioned system of Eq. 5.
+                     split-preconditioned system of Eq. 5; block flexible
+                     GMRES (many sources sharing one block Krylov space).
 * ``multigrid``   -- the geometric V-cycle used on the GPU to apply the
                      inverse of the shifted Laplacian, written out step by
                      step (Jacobi, residual, full weighting, bilinear

@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["givens", "arnoldi", "gmres_right", "gmres_split"]
+__all__ = ["givens", "arnoldi", "gmres_right", "gmres_split", "block_fgmres"]
 
 
 def givens(a: complex, b: complex):
@@ -215,5 +215,81 @@ def gmres_split(A, f, tol, restart, maxiter, Ml_inv=None, Mr_inv=None, x0=None):
             out["converged"] = True
             break
     out["x"] = x
+    out["iterations"] = its
+    return out
+
+
+def block_fgmres(A, F, tol, restart, maxiter, Pinv=None):
+    """Restarted block flexible GMRES for A X = F with s right-hand sides
+    sharing one block Krylov space (right preconditioning as in Eq. 7).
+
+    ``F`` is N x s; ``A`` maps an N x s block to an N x s block; ``Pinv``
+    maps one vector (None: identity). Per cycle, from X (0 at first):
+    R = F - A X = V_0 B (thin QR); block step j forms Z_j = Pinv(V_j) column
+    by column, W = A Z_j, block modified Gram-Schmidt H_ij = V_i^H W,
+    W -= V_i H_ij (i <= j), then the thin QR W = V_{j+1} H_{j+1,j}. The
+    block Hessenberg least squares min ||E_1 B - Hbar_j Y|| decouples into
+    one least-squares problem per column, each column's residual norm is its
+    source's residual estimate, and a cycle stops when every estimate is at
+    most tol ||F_k|| (or after `restart` block steps); then X += [Z_0 ..
+    Z_j] Y and the true residuals decide whether to restart. Returns a dict
+    with X, the block steps taken ("iterations"), restarts, the estimate
+    history per step (an s-vector each), the true residuals per cycle and
+    ``converged``. maxiter bounds the block steps.
+    """
+    F = np.asarray(F, dtype=np.complex128)
+    if F.ndim == 1:
+        F = F[:, None]
+    N, s = F.shape
+    if Pinv is None:
+        Pinv = lambda v: v.copy()  # noqa: E731
+    fnorm = np.linalg.norm(F, axis=0)
+    X = np.zeros_like(F)
+    out = {"history": [], "true_residuals": [], "iterations": 0, "restarts": 0,
+           "converged": False}
+    live = fnorm > 0.0
+    its = 0
+    while its < maxiter:
+        R = F - A(X)
+        rn = np.linalg.norm(R, axis=0)
+        if np.all(rn[live] <= tol * fnorm[live]):
+            out["converged"] = True
+            break
+        V0, B = np.linalg.qr(R)
+        m = restart
+        V = [V0]
+        Z = []
+        Hb = np.zeros(((m + 1) * s, m * s), dtype=np.complex128)
+        k = 0
+        Y = None
+        for j in range(m):
+            Zj = np.column_stack([Pinv(V[j][:, c]) for c in range(s)])
+            Z.append(Zj)
+            W = A(Zj)
+            for i in range(j + 1):
+                Hij = V[i].conj().T @ W
+                Hb[i * s:(i + 1) * s, j * s:(j + 1) * s] = Hij
+                W = W - V[i] @ Hij
+            Vn, Rn = np.linalg.qr(W)
+            Hb[(j + 1) * s:(j + 2) * s, j * s:(j + 1) * s] = Rn
+            V.append(Vn)
+            its += 1
+            k = j + 1
+            E = np.zeros(((j + 2) * s, s), dtype=np.complex128)
+            E[:s, :] = B
+            Hj = Hb[:(j + 2) * s, :(j + 1) * s]
+            Y = np.linalg.lstsq(Hj, E, rcond=None)[0]
+            est = np.linalg.norm(E - Hj @ Y, axis=0)
+            out["history"].append(est / np.where(fnorm > 0, fnorm, 1.0))
+            if np.all(est[live] <= tol * fnorm[live]) or its >= maxiter:
+                break
+        X = X + np.hstack(Z[:k]) @ Y
+        out["restarts"] += 1
+        tr = np.linalg.norm(F - A(X), axis=0) / np.where(fnorm > 0, fnorm, 1.0)
+        out["true_residuals"].append(tr)
+        if np.all(tr[live] <= tol):
+            out["converged"] = True
+            break
+    out["X"] = X
     out["iterations"] = its
     return out

@@ -515,3 +515,71 @@ def test_vcycle_fgmres_matches_lu_small_2d():
                           Pinv=lambda v: mg.vcycle(lv, v, 1, 1, 0.8))
     assert r["converged"] and r["true_residuals"][-1] <= 1e-8
     assert np.linalg.norm(r["x"] - u_lu) <= 1e-6 * np.linalg.norm(u_lu)
+
+
+# ---------------------------------------------------------------- block FGMRES
+
+def _block_problem(n=(13, 9), seed=51, s=4):
+    rng = np.random.default_rng(seed)
+    h, om, al = 10.0, 2 * np.pi * 8.0, 0.05
+    m = 1.0 / rng.uniform(1500.0, 4500.0, size=n[::-1])
+    H = op.assemble_H(n, h, m, om, al).tocsr()
+    M = op.assemble_M(n, h, m, om, al, 1.0, 0.5).tocsc()
+    luM = spla.splu(M)
+    F = rng.standard_normal((H.shape[0], s)) + 1j * rng.standard_normal((H.shape[0], s))
+    return H, luM, F
+
+
+def test_block_fgmres_with_one_source_is_gmres():
+    """A block of one right-hand side is restarted FGMRES: same step count,
+    same iterate."""
+    H, luM, F = _block_problem(s=1)
+    A = lambda X: H @ X  # noqa: E731
+    b = gmres.block_fgmres(A, F, 1e-10, 15, 2000, Pinv=luM.solve)
+    r = gmres.gmres_right(lambda x: H @ x, F[:, 0], 1e-10, 15, 2000, Pinv=luM.solve)
+    assert b["converged"] and r["converged"]
+    assert b["iterations"] == r["iterations"]
+    assert np.linalg.norm(b["X"][:, 0] - r["x"]) <= 1e-9 * np.linalg.norm(r["x"])
+
+
+def test_block_fgmres_matches_lu_and_never_trails_single_sources():
+    """The block space contains each source's own Krylov space, so after k
+    block steps (no restart) every source's residual estimate is at most
+    that of its own GMRES after k steps; the solution matches sparse LU."""
+    H, luM, F = _block_problem(s=4)
+    A = lambda X: H @ X  # noqa: E731
+    b = gmres.block_fgmres(A, F, 1e-10, 200, 2000, Pinv=luM.solve)
+    assert b["converged"] and b["restarts"] == 1
+    X_lu = spla.splu(H.tocsc()).solve(F)
+    assert np.linalg.norm(b["X"] - X_lu) <= 1e-8 * np.linalg.norm(X_lu)
+    for k in range(F.shape[1]):
+        r = gmres.gmres_right(lambda x: H @ x, F[:, k], 1e-10, 200, 2000, Pinv=luM.solve)
+        hs = r["history"]
+        for step, est in enumerate(b["history"]):
+            if step < len(hs):
+                assert est[k] <= hs[step] * (1 + 1e-6) + 1e-14
+    assert b["iterations"] < min(gmres.gmres_right(lambda x: H @ x, F[:, k], 1e-10, 200, 2000,
+                                                    Pinv=luM.solve)["iterations"]
+                                 for k in range(F.shape[1]))
+
+
+def test_block_fgmres_terminates_within_the_block_dimension():
+    """Without restart the block Krylov space fills the whole space after
+    ceil(N / s) block steps: the solve ends in at most that many."""
+    n = (5, 4)
+    H, luM, F = _block_problem(n=n, s=5)
+    A = lambda X: H @ X  # noqa: E731
+    b = gmres.block_fgmres(A, F, 1e-11, 100, 100, Pinv=None)
+    assert b["converged"] and b["iterations"] <= int(np.ceil(20 / 5))
+
+
+def test_block_fgmres_restarts_and_zero_source():
+    H, luM, F = _block_problem(s=3)
+    F[:, 1] = 0.0
+    A = lambda X: H @ X  # noqa: E731
+    b = gmres.block_fgmres(A, F, 1e-9, 3, 2000, Pinv=luM.solve)
+    assert b["converged"] and b["restarts"] > 1
+    assert not b["X"][:, 1].any() or np.abs(b["X"][:, 1]).max() < 1e-12
+    X_lu = spla.splu(H.tocsc()).solve(F)
+    for k in (0, 2):
+        assert np.linalg.norm(b["X"][:, k] - X_lu[:, k]) <= 1e-6 * np.linalg.norm(X_lu[:, k])
