@@ -161,7 +161,7 @@ def cpu_baseline(w, budget_s=12.0):
             "_u": np.asarray(u_lu).ravel()}
 
 
-def oracle_errors(w, F, U_keep, wb, U2_keep, plain_keep, extra_keep, variants, rho):
+def oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, plain_keep, extra_keep, variants, rho):
     """Relative L2 error of every reported GPU result against the oracle's
     sparse-LU solution (factor once per operator, then triangular solves),
     and the strong CPU baseline of the 801x401 workload: one factorisation per
@@ -187,13 +187,14 @@ def oracle_errors(w, F, U_keep, wb, U2_keep, plain_keep, extra_keep, variants, r
     out["1d_well"] = max(err(Ux[k], lu1.solve(wx.rhs(k).ravel())) for k in range(Ux.shape[0]))
     # 801x401: per frequency, the sampled batched sources and the plain sample
     m2 = wb.slowness()
-    per_f, plain, cpu = [], [], None
+    per_f, per_fb, plain, cpu = [], [], [], None
     for fi, fq in enumerate(wb.freqs):
         t = time.perf_counter()
         lu2 = direct.lu_factor_H(wb.n, wb.h, m2, wb.omega(fi), wb.alpha)
         t_fac = time.perf_counter() - t
-        per_f.append(max(err(U2_keep[fi][i], lu2.solve(wb.rhs(k).ravel()))
-                         for i, k in enumerate(LU_SAMPLE)))
+        ref = {k: lu2.solve(wb.rhs(k).ravel()) for k in LU_SAMPLE}
+        per_f.append(max(err(U2_keep[fi][i], ref[k]) for i, k in enumerate(LU_SAMPLE)))
+        per_fb.append(max(err(U2b_keep[fi][i], ref[k]) for i, k in enumerate(LU_SAMPLE)))
         plain += [err(plain_keep[(fi, k)], lu2.solve(wb.rhs(k).ravel())) for k in PLAIN_SAMPLE]
         if fq == 10.0:
             Fb = np.stack([wb.rhs(k).ravel() for k in range(len(wb.sources))]).T
@@ -206,6 +207,7 @@ def oracle_errors(w, F, U_keep, wb, U2_keep, plain_keep, extra_keep, variants, r
                              f"{len(wb.sources)} triangular solves ({t_sol:.2f} s), complex128, "
                              f"single-threaded"}
     out["batched_801x401_per_frequency"] = per_f
+    out["block_801x401_per_frequency"] = per_fb
     out["plain_801x401_sample"] = max(plain)
     return out, cpu
 
@@ -481,14 +483,29 @@ def main():
     Ud = torch.empty_like(Fd)
     batched_forms = {}
     U_keep = {}
-    for form in ("mixed", "mixed_ds"):
-        gb = helm.Grid(w.n, w.h, restart=w.restart, precond="mg", precision=form)
+    tuned = None
+    for form in ("mixed", "mixed_ds", "block"):
+        if form == "block":
+            # block FGMRES: the 64 sources share one block Krylov space
+            gb = helm.Grid(w.n, w.h, restart=w.restart, precond="mg", precision="mixed", block=True)
+        else:
+            gb = helm.Grid(w.n, w.h, restart=w.restart, precond="mg", precision=form)
         gb.set_stream(stream.cuda_stream)
         gb.set_model(md, w.omega(), w.alpha)
         gb.set_shift(*w.beta)
-        # set-up, untimed: the autotuner picks each level's tile shapes and the
-        # smoother counts on this batch
-        tune = gb.autotune(BATCH_SOURCES, Fd, w.tol)
+        if form == "block":
+            # the V-cycle's tile shapes and smoother counts tuned for this batch
+            # on the double-single grid (same levels, same batch size)
+            for lev, (dn, up) in enumerate(tuned["tiles"]):
+                gb.set_tiles(lev, dn, up)
+            gb.set_options(nu1=tuned["nu"][0], nu2=tuned["nu"][1])
+        else:
+            # set-up, untimed: the autotuner picks each level's tile shapes and the
+            # smoother counts on this batch
+            tune = gb.autotune(BATCH_SOURCES, Fd, w.tol)
+            if form == "mixed_ds":
+                tuned = {"tiles": [gb.get_tiles(lev) for lev in range(gb.num_levels - 1)],
+                         "nu": (tune["nu1"], tune["nu2"])}
         gb.solve_batch(BATCH_SOURCES, Fd, w.tol, Ud)
         torch.cuda.synchronize()
         bt = []
@@ -508,7 +525,7 @@ def main():
             torch.cuda.synchronize()
             torch.cuda.cudart().cudaProfilerStop()
         bkern = None
-        if form == "mixed_ds":
+        if form in ("mixed_ds", "block"):
             # one more (untimed) solve with the library's per-launch CUDA-event
             # profiler: algorithmic bytes per kernel over its device time, as a
             # fraction of the measured copy bandwidth (all levels and steps)
@@ -527,7 +544,7 @@ def main():
             "ms_per_batch": bms, "iterations_max": int(bits.max()),
             "iterations_mean": float(bits.mean()), "true_rel_residual_max": float(brr.max()),
             "vs_plain": (world * BATCH_SOURCES / (bms / 1e3)) / value,
-            "autotune": tune_summary(helm, 2, tune)}
+            "autotune": tune_summary(helm, 2, tune) if form != "block" else "tiles and smoother of mixed_ds"}
         if bkern:
             batched_forms[form]["kernels"] = bkern
         del gb
@@ -535,6 +552,12 @@ def main():
     batched["precision"] = ("complex64 V-cycle, double-single Arnoldi basis, complex128 "
                             "Hessenberg/update/true residual")
     batched["complex128_arnoldi_basis"] = batched_forms["mixed"]
+    batched["block_fgmres"] = dict(batched_forms["block"])
+    batched["block_fgmres"]["precision"] = (
+        "block FGMRES: 64 sources share one block Krylov space; complex64 V-cycle and basis, "
+        "Gram matrices and block updates on the tensor cores (TF32 hi/lo split), complex128 "
+        "block Hessenberg least squares, solution and true residual; iterations = block steps")
+    batched["best_vs_plain"] = max(batched["vs_plain"], batched["block_fgmres"]["vs_plain"])
 
     # ---- the multi-frequency batched workload: 801x401, 64 surface sources x 4 frequencies
     wb = workload("2d_batched")
@@ -567,7 +590,34 @@ def main():
         U2_keep[fi] = U2[list(LU_SAMPLE)].cpu().numpy()
     t_all = time.perf_counter() - t_all
     nsol = len(wb.sources) * len(wb.freqs)
+    tiles2 = [g2.get_tiles(lev) for lev in range(g2.num_levels - 1)]
     del g2
+    # the same 256 solves by block FGMRES: per frequency the 64 sources share
+    # one block Krylov space (tile shapes as tuned above)
+    gk = helm.Grid(wb.n, wb.h, restart=wb.restart, precond="mg", precision="mixed", block=True)
+    gk.set_stream(stream.cuda_stream)
+    gk.set_model(m2, wb.omega(0), wb.alpha)
+    gk.set_shift(*wb.beta)
+    for lev, (dn, up) in enumerate(tiles2):
+        gk.set_tiles(lev, dn, up)
+    blk_f = []
+    U2b_keep = {}
+    torch.cuda.synchronize()
+    t_blk = time.perf_counter()
+    for fi, fq in enumerate(wb.freqs):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        gk.set_model(m2, wb.omega(fi), wb.alpha)
+        gk.set_shift(*wb.beta)
+        e1.record(stream)
+        _, itk, rrk = gk.solve_batch(len(wb.sources), F2, wb.tol, U2)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        blk_f.append({"freq_hz": fq, "setup_ms": e0.elapsed_time(e1), "solve_ms": e1.elapsed_time(e2),
+                      "block_steps": int(itk.max()), "true_rel_residual_max": float(rrk.max())})
+        U2b_keep[fi] = U2[list(LU_SAMPLE)].cpu().numpy()
+    t_blk = time.perf_counter() - t_blk
+    del gk
     # the plain one-at-a-time complex128 path on the same workload: a sample
     # of sources per frequency, each one helm_solve (FGMRES(30), complex128
     # V-cycle and basis), timed with CUDA events around each solve
@@ -602,7 +652,10 @@ def main():
                          "iterations": plain_its,
                          "note": "the plain one-at-a-time complex128 path (helm_solve) on a fixed "
                                  "sample of this workload's sources at every frequency"},
-                     "batched_vs_plain": (world * nsol / t_all) / plain_rate}
+                     "batched_vs_plain": (world * nsol / t_all) / plain_rate,
+                     "block_fgmres": {"solves": nsol, "wall_s": t_blk, "solves_per_s": world * nsol / t_blk,
+                                      "per_frequency": blk_f, "vs_plain": (world * nsol / t_blk) / plain_rate,
+                                      "vs_lockstep": t_all / t_blk}}
     del F2, U2
 
     serving = serving_run(helm)
@@ -687,9 +740,14 @@ def main():
         u_gpu = ud.cpu().numpy().ravel()
         rel_err_lu = float(np.linalg.norm(u_gpu - u_lu) / np.linalg.norm(u_lu))
         cpu["host_cores"] = os.cpu_count()
-        errs, cpu_801 = oracle_errors(w, F, U_keep, wb, U2_keep, plain_keep, extra_keep, variants, rho)
+        errs, cpu_801 = oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, plain_keep, extra_keep, variants,
+                                      rho)
         batched["rel_err_vs_oracle_lu_max"] = errs["batched_mixed_ds"]
         batched["complex128_arnoldi_basis"]["rel_err_vs_oracle_lu_max"] = errs["batched_mixed"]
+        batched["block_fgmres"]["rel_err_vs_oracle_lu_max"] = errs["batched_block"]
+        for pf, e in zip(batched_multi["block_fgmres"]["per_frequency"], errs["block_801x401_per_frequency"]):
+            pf["rel_err_vs_oracle_lu_max"] = e
+            pf["rel_err_sources"] = list(LU_SAMPLE)
         for pf, e in zip(batched_multi["per_frequency"], errs["batched_801x401_per_frequency"]):
             pf["rel_err_vs_oracle_lu_max"] = e
             pf["rel_err_sources"] = list(LU_SAMPLE)

@@ -105,6 +105,10 @@ typedef struct {
     int graphs;              /* 1: replay each Arnoldi step as a captured CUDA graph   */
                              /*    (default); 0: launch kernels one by one             */
     int side;                /* helm_side; default HELM_SIDE_RIGHT                     */
+    int block;               /* 0: the right-hand sides of a batch run as independent  */
+                             /*    recurrences in lock-step (default); 1: block FGMRES */
+                             /*    -- up to 64 sources share one block Krylov space    */
+                             /*    (see helm_solve_batch)                              */
 } helm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -180,7 +184,18 @@ helm_status helm_solve(helm_grid *g, const helm_c128 *f, double tol, helm_c128 *
  * complex values, right-hand side k at offset k*N. iterations and
  * true_rel_residual (nullable): nrhs entries each. Returns HELM_OK when all
  * converged, HELM_ERR_NOT_CONVERGED if any did not. Other errors as
- * helm_solve. */
+ * helm_solve.
+ *
+ * With options.block = 1 the sources, in groups of up to 64, run block
+ * flexible GMRES (Eq. 7): one block Krylov space per group, widened by one
+ * vector per source at every block step, so each source minimises its
+ * residual over the whole group's space. The basis is complex64; the Gram
+ * matrices V^H W and the block updates run on the tensor cores (TF32 with a
+ * hi/lo split, FP32 accuracy); the block Hessenberg least squares, the
+ * solution and the true residual stay complex128, and a group restarts until
+ * every true residual is <= tol. iterations then counts block steps. Needs
+ * precision HELM_PREC_MIXED, precond MG or EXACT, side RIGHT and restart <= 32
+ * (HELM_ERR_UNSUPPORTED otherwise, from helm_set_options). */
 helm_status helm_solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double tol,
                              helm_c128 *u, int *iterations, double *true_rel_residual);
 
@@ -252,6 +267,24 @@ helm_status helm_true_residual(helm_grid *g, const helm_c128 *f, const helm_c128
  * HELM_ERR_STATE (no model), HELM_ERR_UNSUPPORTED, HELM_ERR_CUDA. */
 helm_status helm_true_residual_noalloc(helm_grid *g, int nrhs, const helm_c128 *f,
                                        const helm_c128 *u, double *rel);
+
+/* The two tensor-core contractions of block FGMRES (helm_solve_batch with
+ * options.block = 1), exposed for checking them on their own. Vectors are
+ * complex64 (float re, im interleaved), device pointers of the current
+ * device, vector k at offset k*ld; ld is a multiple of 8 and >= N, and the
+ * entries N..ld-1 of every vector must be zero. Arithmetic: TF32 tensor-core
+ * MMAs on operands split into TF32 hi + lo parts, FP32 accumulation (FP32
+ * accuracy), partial sums added in FP64.
+ * helm_block_gram: G[i*s + c] = sum_p conj(V_i[p]) W_c[p] for i < nv, c < s
+ *   (the Gram matrix V^H W of block Gram-Schmidt, GMRES on Eq. 7); G (nv x s
+ *   complex128) may be host or device memory.
+ * helm_block_combine: W_c = alpha W_c + sum_i V_i C[i*s + c] (the block
+ *   update), C (nv x s complex128) host or device; W is overwritten.
+ * Limits: 1 <= nv <= 2048, 1 <= s <= 64. Both allocate their scratch and
+ * synchronise the device. Errors: HELM_ERR_ARG, HELM_ERR_NOMEM, HELM_ERR_CUDA. */
+helm_status helm_block_gram(int nv, int s, size_t N, size_t ld, const void *V, const void *W, helm_c128 *G);
+helm_status helm_block_combine(int nv, int s, size_t N, size_t ld, const void *V, const helm_c128 *C,
+                               float alpha, void *W);
 
 /* ------------------------------------------------------------ autotuning
  * Tile shapes and smoother counts of the multigrid preconditioner (the paper

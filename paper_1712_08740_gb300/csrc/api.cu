@@ -228,6 +228,7 @@ void helm_default_options(helm_options *o) {
     o->reorth = 0;
     o->graphs = 1;
     o->side = HELM_SIDE_RIGHT;
+    o->block = 0;
 }
 
 const char *helm_last_error(void) { return helm::last_error(); }
@@ -290,6 +291,7 @@ void helm_destroy_grid(helm_grid *g) {
     for (auto e : g->ring) cudaEventDestroy(e);
     if (g->cap_st) cudaStreamDestroy(g->cap_st);
     if (g->hflag) cudaFreeHost(g->hflag);
+    if (g->bhflag) cudaFreeHost(g->bhflag);
     delete g;
 }
 
@@ -314,6 +316,13 @@ helm_status helm_set_options(helm_grid *g, const helm_options *o) {
     if (o->coarse_max < 1) return fail(HELM_ERR_ARG, "coarse_max must be >= 1");
     if (o->reorth < 0 || o->reorth > 2) return fail(HELM_ERR_ARG, "reorth must be 0, 1 or 2");
     if (o->side < 0 || o->side > 2) return fail(HELM_ERR_ARG, "side must be 0, 1 or 2");
+    if (o->block < 0 || o->block > 1) return fail(HELM_ERR_ARG, "block must be 0 or 1");
+    if (o->block &&
+        (o->precision != HELM_PREC_MIXED || o->precond == HELM_PRECOND_NONE || o->side != HELM_SIDE_RIGHT ||
+         o->restart > 32))
+        return fail(HELM_ERR_UNSUPPORTED,
+                    "block FGMRES needs precision HELM_PREC_MIXED, a preconditioner, side RIGHT and "
+                    "restart <= 32");
     if (g->has_rho && o->precision == HELM_PREC_MIXED_DS)
         return fail(HELM_ERR_UNSUPPORTED, "a variable density needs precision HELM_PREC_F64 or HELM_PREC_MIXED");
     if (o->side != HELM_SIDE_RIGHT && o->precond != HELM_PRECOND_NONE &&

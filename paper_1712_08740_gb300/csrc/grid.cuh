@@ -75,6 +75,15 @@ struct helm_grid {
     int *hflag = nullptr;               // host-mapped "any right-hand side active" flag
     std::vector<cudaEvent_t> ring;      // look-ahead events of the Arnoldi loop
 
+    // block FGMRES workspace (helm_options.block): complex64 basis, Z and the
+    // new block with a padded per-vector stride; tensor-core scratch; the
+    // block Hessenberg, its reflectors and the least-squares right-hand sides
+    helm::DevBuf bV, bZ, bW, bpart, bimg, bG, bR, bRinv, bHb, bg, bVh, btau, bpub, bticket;
+    helm::DevBuf best, bflags, bY, bfn, bnp, bncnt, bnrm;
+    int bcap_m = 0;
+    int bls_epoch = 0;
+    int *bhflag = nullptr;              // host-mapped "cycle goes on" flag
+
     // CUDA graphs of one Arnoldi step per j, valid for graph_key
     std::vector<cudaGraphExec_t> step_graphs;
     std::vector<uint64_t> step_launches;                           // kernels per step graph

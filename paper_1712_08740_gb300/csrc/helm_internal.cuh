@@ -351,6 +351,19 @@ void launch_make_hdiag_ds(const LevelView<double> &L, OpShift<double> s, float4 
 void launch_apply_H_ds(const LevelView<double> &L, const float4 *hd, const float2 *z, size_t sz,
                        float4 *w, size_t sw, int nb, const int *active, cudaStream_t st);
 
+// ---- block FGMRES tensor-core contractions (block.cu), complex64 vectors with
+// per-vector stride, padded to Np nodes (a multiple of 8, zeros beyond N)
+// G = V^H W for nv basis vectors and s <= 64 sources, complex128 G[i * ldg + c];
+// with hacc non-null also hacc[c * ldh + i] = G (add = 0) or += G (add = 1)
+void launch_bgram(const float2 *V, size_t sv, int nv, const float2 *W, size_t sw, int s, size_t Np,
+                  float *part, double2 *G, int ldg, double2 *hacc, size_t ldh, int add, cudaStream_t st);
+// out = alpha win + V (sign C), C[i * ldc + c] complex128 (nv x s); out may be win or V
+void launch_bcomb(const float2 *V, size_t sv, int nv, const double2 *C, int ldc, double sign, float *img,
+                  const float2 *win, size_t sw, float alpha, float2 *out, size_t so, int s, size_t N,
+                  size_t Np, cudaStream_t st);
+size_t block_gram_part_floats(int nv_max, size_t Np);
+size_t block_image_floats(int nv_max);
+
 // finite check: flag[0] |= 1 if any entry is NaN/Inf
 void launch_finite_check(const double *x, size_t n, int *flag, cudaStream_t st);
 // x_r = 0 (N complex128 values) for each right-hand side r with active[r] == 0

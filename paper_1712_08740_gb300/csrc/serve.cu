@@ -98,8 +98,22 @@ size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o)
         const double page = 2.0 * 1024 * 1024;
         b += bytes > page / 2 ? std::ceil(bytes / page) * page : bytes;
     };
-    add(nrhs * (m + 1.0) * N * 16.0);                    // basis V
-    if (zsz > 0.0) add(nrhs * (double)m * N * zsz);      // preconditioned vectors Z
+    if (o.block) {
+        // block FGMRES: complex64 basis, Z and new block for 64 sources with
+        // a padded stride, tensor-core scratch, block Hessenberg and reflectors
+        const double Np = std::ceil(N / 8.0) * 8.0, S = 64.0, nv = m * S, ldh = (m + 1.0) * S;
+        add((m + 1.0) * S * Np * 8.0);
+        add(m * S * Np * 8.0);
+        add(S * Np * 8.0);
+        add((double)block_gram_part_floats((int)nv, (size_t)Np) * 4.0);
+        add((double)block_image_floats((int)nv) * 4.0);
+        add(ldh * nv * 16.0);                            // block Hessenberg
+        add(ldh * S * 16.0 + nv * (S + 1) * 16.0 + 2.0 * nv * S * 16.0);
+        add(S * N * 16.0);                               // complex128 residual block
+    } else {
+        add(nrhs * (m + 1.0) * N * 16.0);                // basis V
+        if (zsz > 0.0) add(nrhs * (double)m * N * zsz);  // preconditioned vectors Z
+    }
     for (int l = 0; l < nlev; ++l) {                     // per level of the hierarchy
         const double Nl = level_N[l];
         for (int k = 0; k < 4; ++k) add(nrhs * Nl * csz);  // V-cycle work vectors

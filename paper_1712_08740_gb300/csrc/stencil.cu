@@ -371,6 +371,7 @@ void launch_prolong_add(const LevelView<T> &fine, const LevelView<T> &coarse,
                                             const int *, cudaStream_t);
 HELM_INST_ST(double, double2, double2)
 HELM_INST_ST(double, float2, double2)
+HELM_INST_ST(double, float2, float2)
 HELM_INST_ST(float, float2, float2)
 HELM_INST_ST(double, float2, float4)
 HELM_INST_ST(double, float4, float4)

@@ -36,14 +36,15 @@ EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "he
             "helm_server_create", "helm_server_submit", "helm_server_wait", "helm_server_poll",
             "helm_server_clock", "helm_server_destroy", "helm_num_tile_shapes", "helm_tile_shape",
             "helm_set_tiles", "helm_get_tiles", "helm_autotune", "helm_set_wait_limit_ns",
-            "helm_set_density")
+            "helm_set_density", "helm_block_gram", "helm_block_combine")
 
 
 class helm_options(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("precond", ctypes.c_int),
                 ("precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega_jacobi", ctypes.c_double), ("coarse_max", ctypes.c_int),
-                ("reorth", ctypes.c_int), ("graphs", ctypes.c_int), ("side", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("graphs", ctypes.c_int), ("side", ctypes.c_int),
+                ("block", ctypes.c_int)]
 
 
 class helm_server_config(ctypes.Structure):
@@ -106,6 +107,8 @@ def _load():
         "helm_set_model": (I, [P, P, D, D]),
         "helm_set_shift": (I, [P, D, D]),
         "helm_set_density": (I, [P, P]),
+        "helm_block_gram": (I, [I, I, ctypes.c_size_t, ctypes.c_size_t, P, P, P]),
+        "helm_block_combine": (I, [I, I, ctypes.c_size_t, ctypes.c_size_t, P, P, ctypes.c_float, P]),
         "helm_solve": (I, [P, P, D, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "helm_solve_batch": (I, [P, I, P, D, P, P, P]),
         "helm_solve_batch_warm": (I, [P, I, P, D, P, P, P]),
@@ -314,6 +317,34 @@ def helm_set_wait_limit_ns(ns):
     _check(_lib.helm_set_wait_limit_ns(int(ns)))
 
 
+def _ptr_c64(a):
+    """Raw pointer of a contiguous complex64 torch tensor."""
+    import torch
+    if a.dtype != torch.complex64 or not a.is_contiguous() or not a.is_cuda:
+        raise TypeError("expected a contiguous complex64 CUDA tensor")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def helm_block_gram(V, W, N):
+    """G = V^H W on the tensor cores; V (nv x ld), W (s x ld) complex64 CUDA
+    tensors with zeros beyond column N. Returns G as an (nv, s) complex128 array."""
+    nv, ld = V.shape
+    s = W.shape[0]
+    G = np.zeros((nv, s), dtype=np.complex128)
+    _check(_lib.helm_block_gram(int(nv), int(s), int(N), int(ld), _ptr_c64(V), _ptr_c64(W),
+                                G.ctypes.data_as(ctypes.c_void_p)))
+    return G
+
+
+def helm_block_combine(V, C, alpha, W, N):
+    """W = alpha W + C^T-combination: W_c = alpha W_c + sum_i V_i C[i, c] (in place)."""
+    nv, ld = V.shape
+    s = W.shape[0]
+    C = np.ascontiguousarray(C, dtype=np.complex128)
+    _check(_lib.helm_block_combine(int(nv), int(s), int(N), int(ld), _ptr_c64(V),
+                                   C.ctypes.data_as(ctypes.c_void_p), float(alpha), _ptr_c64(W)))
+
+
 def helm_kernel_launches():
     return int(_lib.helm_kernel_launches())
 
@@ -384,7 +415,7 @@ class Grid:
 
     def __init__(self, n, h, *, restart=30, precond="mg", precision="f64", nu1=1, nu2=1,
                  omega_jacobi=0.8, coarse_max=1500, reorth=0, max_iters=5000, graphs=True,
-                 side="right"):
+                 side="right", block=False):
         self.n = tuple(int(k) for k in n)
         self.N = int(np.prod(self.n))
         self.h = float(h)
@@ -392,7 +423,7 @@ class Grid:
         _live.add(self)
         self.set_options(restart=restart, precond=precond, precision=precision, nu1=nu1,
                          nu2=nu2, omega_jacobi=omega_jacobi, coarse_max=coarse_max,
-                         reorth=reorth, max_iters=max_iters, graphs=graphs, side=side)
+                         reorth=reorth, max_iters=max_iters, graphs=graphs, side=side, block=block)
 
     def set_options(self, **kw):
         o = helm_get_options(self._g)
@@ -407,6 +438,8 @@ class Grid:
                 v = int(v)
             elif k == "side":
                 v = SIDE[v]
+            elif k == "block":
+                v = int(bool(v))
             setattr(o, k, v)
         helm_set_options(self._g, o)
 
