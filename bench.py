@@ -53,10 +53,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default="plain", choices=["plain", "batched", "3d"],
+    ap.add_argument("--profile", default="plain", choices=["plain", "batched", "3d", "block-tc", "block-ls"],
                     help="region bracketed by cudaProfilerStart/Stop for ncu --profile-from-start "
                          "off: the plain timed solves, or one extra (untimed) solve of the "
-                         "64-source batch with the double-single basis")
+                         "64-source batch with the double-single basis; block-tc / block-ls: only "
+                         "the block form's tensor-core contractions at the 801x401 shape, or one "
+                         "block solve capped at 20 steps, for ncu -k captures")
     return ap.parse_args()
 
 
@@ -346,6 +348,42 @@ def profile_3d(helm, dev, stream):
     gx.close()
 
 
+def profile_block(helm, dev, which):
+    """--profile block-tc: four rounds of one Gram V^H W and one block update
+    W - V C at the block form's average shape on the 801x401 grid (960 basis
+    vectors, 64 sources, complex64, seeded); block-ls: one block solve of the
+    64-source 401x201 batch capped at 20 block steps. For ncu -k captures."""
+    import torch
+    from workloads import point_sources, workload
+    if which == "block-tc":
+        N, nv, s = 321201, 960, 64
+        ld = (N + 7) // 8 * 8
+        gen = torch.Generator(device=dev).manual_seed(0)
+        V = torch.zeros(nv, ld, dtype=torch.complex64, device=dev)
+        V[:, :N] = torch.randn(nv, N, dtype=torch.complex64, device=dev, generator=gen)
+        W = torch.zeros(s, ld, dtype=torch.complex64, device=dev)
+        W[:, :N] = torch.randn(s, N, dtype=torch.complex64, device=dev, generator=gen)
+        C = np.random.default_rng(0).standard_normal((nv, s)) / 30 + 0j
+        for _ in range(4):
+            helm.helm_block_gram(V, W, N)
+            helm.helm_block_combine(V, C, 1.0, W, N)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": which, "nv": nv, "s": s, "N": N}), flush=True)
+        return
+    w = workload("2d_smooth")
+    m = torch.from_numpy(w.slowness().ravel().copy()).to(dev)
+    xs = [int(math.floor((k + 0.5) * (w.n[0] - 1) / BATCH_SOURCES + 0.5)) for k in range(BATCH_SOURCES)]
+    F = torch.from_numpy(np.stack([point_sources(w.n, w.h, [(x, 2)]).ravel() for x in xs])).to(dev)
+    U = torch.empty_like(F)
+    g = helm.Grid(w.n, w.h, restart=30, precision="mixed", block=True, max_iters=20)
+    g.set_model(m, w.omega(), w.alpha)
+    g.set_shift(*w.beta)
+    st, its, rr = g.solve_batch(BATCH_SOURCES, F, w.tol, U, check=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": which, "status": int(st), "block_steps": int(its.max())}), flush=True)
+    g.close()
+
+
 def main():
     args = parse()
     from paper_1712_08740_gb300.replicas import max_over_ranks, rank_env, whole_job_rate
@@ -367,6 +405,9 @@ def main():
 
     if args.profile == "3d":
         profile_3d(helm, dev, torch.cuda.current_stream(dev))
+        return
+    if args.profile in ("block-tc", "block-ls"):
+        profile_block(helm, dev, args.profile)
         return
 
     w = workload("2d_smooth")

@@ -404,77 +404,95 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 
 constexpr int kCh = 256;   // threads of the Cholesky kernel
 
+__device__ __forceinline__ float2 fmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 fconjmulc(float2 a, float2 b) {   // conj(a) b
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
 // Cholesky QR step on the s x s Gram G = W^H W (row-major, Hermitian):
-// R^H R = G + shift_rel * max(diag G) I with R upper triangular; a pivot at
-// or below 1e-12 max(diag G) marks a direction W has lost (its row of R and
-// column of R^-1 are zero). Writes Rinv (row-major, upper) for W <- W R^-1,
-// and Racc <- R Racc (upper, row-major: the accumulated R of the passes).
+// R^H R = G + shift_rel * max(diag G) I with R upper triangular, in FP32 (the
+// Gram itself is FP32-accurate). A pivot at or below 1e-7 max(diag G) marks
+// a direction W has lost: its row of R and column of R^-1 are zero. Writes
+// Rinv (row-major, upper) for W <- W R^-1, and Racc <- R Racc (upper,
+// row-major: the accumulated R of the passes), both as complex128.
 __global__ void __launch_bounds__(kCh)
 k_bchol(const double2 *__restrict__ G, int s, double shift_rel, double2 *__restrict__ Rinv,
         double2 *__restrict__ Racc, int first) {
-    extern __shared__ double2 ch_raw[];
-    double2 *A = ch_raw;                  // s x s working copy, then R
-    double2 *X = ch_raw + kBS * kBS;      // R^-1
-    double2 *T = X + kBS * kBS;           // R Racc
-    __shared__ double maxd;
+    extern __shared__ float2 chol_raw[];
+    float2 *A = chol_raw;                 // working copy, then R
+    float2 *X = chol_raw + kBS * kBS;     // R^-1
+    __shared__ float maxd;
     const int tid = threadIdx.x;
-    for (int e = tid; e < s * s; e += kCh) A[e] = G[e];
+    for (int e = tid; e < s * s; e += kCh) A[e] = make_float2((float)G[e].x, (float)G[e].y);
     __syncthreads();
     if (tid == 0) {
-        double m = 0.0;
-        for (int k = 0; k < s; ++k) m = fmax(m, A[k * s + k].x);
-        maxd = m;
+        float mx = 0.f;
+        for (int k = 0; k < s; ++k) mx = fmaxf(mx, A[k * s + k].x);
+        maxd = mx;
     }
     __syncthreads();
-    const double floor_ = 1e-12 * maxd, shift = shift_rel * maxd;
+    const float floor_ = 1e-7f * maxd, shift = (float)shift_rel * maxd;
     for (int k = tid; k < s; k += kCh) A[k * s + k].x += shift;
     __syncthreads();
     for (int k = 0; k < s; ++k) {
-        const double d = A[k * s + k].x;
+        const float d = A[k * s + k].x;
         const bool dead = !(d > floor_);
-        const double rk = dead ? 0.0 : sqrt(d);
+        const float rk = dead ? 0.f : sqrtf(d);
         __syncthreads();
-        // row k of R: R_kj = A_kj / r_kk (j > k), zero below the diagonal
         for (int jj = tid; jj < s; jj += kCh) {
-            if (jj < k) A[k * s + jj] = make_double2(0.0, 0.0);
-            else if (jj == k) A[k * s + jj] = make_double2(rk, 0.0);
-            else A[k * s + jj] = dead ? make_double2(0.0, 0.0) : cscal(1.0 / rk, A[k * s + jj]);
+            if (jj < k) A[k * s + jj] = make_float2(0.f, 0.f);
+            else if (jj == k) A[k * s + jj] = make_float2(rk, 0.f);
+            else A[k * s + jj] = dead ? make_float2(0.f, 0.f) : make_float2(A[k * s + jj].x / rk, A[k * s + jj].y / rk);
         }
         __syncthreads();
-        // trailing update A_ij -= conj(R_ki) R_kj, i <= j, i, j > k
         if (!dead)
             for (int e = tid; e < (s - k - 1) * (s - k - 1); e += kCh) {
-                const int i = k + 1 + e / (s - k - 1), j = k + 1 + e % (s - k - 1);
-                if (i <= j) A[i * s + j] = csub(A[i * s + j], cconjmul(A[k * s + i], A[k * s + j]));
+                const int i = k + 1 + e / (s - k - 1), jj = k + 1 + e % (s - k - 1);
+                if (i <= jj) {
+                    const float2 t = fconjmulc(A[k * s + i], A[k * s + jj]);
+                    A[i * s + jj] = make_float2(A[i * s + jj].x - t.x, A[i * s + jj].y - t.y);
+                }
             }
         __syncthreads();
     }
     // X = R^-1 by rows from the bottom: X_ij = (delta_ij - sum_{i<l<=j} R_il X_lj) / R_ii
-    for (int e = tid; e < s * s; e += kCh) X[e] = make_double2(0.0, 0.0);
+    for (int e = tid; e < s * s; e += kCh) X[e] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int i = s - 1; i >= 0; --i) {
-        const double2 rii = A[i * s + i];
-        for (int j = i + tid; j < s; j += kCh) {
-            double2 acc = make_double2(j == i ? 1.0 : 0.0, 0.0);
-            for (int l = i + 1; l <= j; ++l) acc = csub(acc, cmul(A[i * s + l], X[l * s + j]));
-            X[i * s + j] = rii.x > 0.0 ? cdiv(acc, rii) : make_double2(0.0, 0.0);
+        const float rii = A[i * s + i].x;
+        for (int jj = i + tid; jj < s; jj += kCh) {
+            float2 acc = make_float2(jj == i ? 1.f : 0.f, 0.f);
+            for (int l = i + 1; l <= jj; ++l) {
+                const float2 t = fmulc(A[i * s + l], X[l * s + jj]);
+                acc = make_float2(acc.x - t.x, acc.y - t.y);
+            }
+            X[i * s + jj] = rii > 0.f ? make_float2(acc.x / rii, acc.y / rii) : make_float2(0.f, 0.f);
         }
         __syncthreads();
     }
-    for (int e = tid; e < s * s; e += kCh) Rinv[e] = X[e];
-    // Racc <- R Racc (first pass: Racc <- R)
-    for (int e = tid; e < s * s; e += kCh) {
-        const int i = e / s, j = e % s;
-        double2 acc = make_double2(0.0, 0.0);
-        if (first) {
-            acc = A[e];
-        } else {
-            for (int l = i; l <= j; ++l) acc = cadd(acc, cmul(A[i * s + l], Racc[l * s + j]));
-        }
-        T[e] = acc;
-    }
+    for (int e = tid; e < s * s; e += kCh) Rinv[e] = make_double2((double)X[e].x, (double)X[e].y);
+    // Racc <- R Racc (first pass: Racc <- R), in FP32 like the factors: one
+    // thread per output, the previous Racc staged in shared memory (A's
+    // buffer is free once X is formed)
     __syncthreads();
-    for (int e = tid; e < s * s; e += kCh) Racc[e] = T[e];
+    if (first) {
+        for (int e = tid; e < s * s; e += kCh) Racc[e] = make_double2((double)A[e].x, (double)A[e].y);
+        return;
+    }
+    float2 *P = X;                         // X was written out above
+    for (int e = tid; e < s * s; e += kCh) P[e] = make_float2((float)Racc[e].x, (float)Racc[e].y);
+    __syncthreads();
+    for (int e = tid; e < s * s; e += kCh) {
+        const int i = e / s, jj = e % s;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int l = i; l <= jj; ++l) {
+            const float2 t = fmulc(A[i * s + l], P[l * s + jj]);
+            acc = make_float2(acc.x + t.x, acc.y + t.y);
+        }
+        Racc[e] = make_double2((double)acc.x, (double)acc.y);
+    }
 }
 
 // R (row-major s x s) into the block Hessenberg rows r0 .. r0 + s - 1 of block
@@ -495,25 +513,46 @@ __global__ void k_brhs_init(const double2 *__restrict__ B, int s, double2 *__res
 }
 
 constexpr unsigned long long kLsWaitNs = 500ull * 1000 * 1000;
-constexpr int kLsThreads = 64;
+constexpr int kLsThreads = 32;       // one warp per column of the new block
 constexpr int kMaxRows = 64 * 33;    // rows of the block Hessenberg kept in shared memory
+constexpr int kLsDepth = 4;          // reflectors of earlier blocks loaded ahead
 
-// Apply reflector (v, tau) (v[0] = 1 stored explicitly, length s + 1) to
-// x[0 .. s] held in shared memory: x -= tau v (v^H x). Two warps.
-__device__ __forceinline__ void apply_refl(const double2 *v, double tau, double2 *x, int s, double2 *red) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double2 a = make_double2(0.0, 0.0);
-    for (int k = tid; k <= s; k += kLsThreads) a = cadd(a, cconjmul(v[k], x[k]));
+__device__ __forceinline__ double2 warp_csum(double2 a) {
     for (int o = 16; o; o >>= 1) {
         a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
         a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
     }
-    if (lane == 0) red[warp] = a;
-    __syncthreads();
-    const double2 dot = cadd(red[0], red[1]);
-    const double2 f = cscal(tau, dot);
-    for (int k = tid; k <= s; k += kLsThreads) x[k] = csub(x[k], cmul(v[k], f));
-    __syncthreads();
+    return a;
+}
+
+// lane l's share v[l], v[l + 32], v[l + 64] of a reflector (k <= s; zeros beyond)
+__device__ __forceinline__ void load_refl(const double2 *v, int s, bool l2only, double2 (&r)[3]) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int k = lane + 32 * q;
+        r[q] = k <= s ? (l2only ? __ldcg(v + k) : __ldg(v + k)) : make_double2(0.0, 0.0);
+    }
+}
+
+// x[0 .. s] (shared memory) -= tau v (v^H x), one warp
+__device__ __forceinline__ void warp_refl(const double2 (&v)[3], double tau, double2 *x, int s) {
+    const int lane = threadIdx.x;
+    double2 xs[3], a = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int k = lane + 32 * q;
+        xs[q] = k <= s ? x[k] : make_double2(0.0, 0.0);
+        a = cadd(a, cconjmul(v[q], xs[q]));
+    }
+    a = warp_csum(a);
+    const double2 f = cscal(tau, a);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int k = lane + 32 * q;
+        if (k <= s) x[k] = csub(xs[q], cmul(v[q], f));
+    }
+    __syncwarp();
 }
 
 // bounded wait until flag == epoch (another block publishes it)
@@ -529,15 +568,23 @@ __device__ __forceinline__ bool wait_flag(const int *flag, int epoch) {
     }
 }
 
-// QR update of the block Hessenberg after block step j, one block per new
-// column q = j s + c (s co-resident blocks, cooperative launch): the column
-// takes every earlier reflector (earlier blocks: stored; this block: as the
-// blocks of the earlier columns publish them), then yields its own reflector
-// (Householder, v[0] = 1, real tau, so that H x = beta e1 with conj(alpha)
-// beta real) and its column of the triangular factor. Then block c applies
-// this block's s reflectors to source c's least-squares right-hand side,
-// whose rows (j+1) s .. (j+2) s - 1 give the source's residual estimate.
-// The last block to finish decides whether the cycle stops.
+// all lanes: lane 0 waits, the result is broadcast
+__device__ __forceinline__ bool warp_wait_flag(const int *flag, int epoch) {
+    int ok = 1;
+    if (threadIdx.x == 0) ok = wait_flag(flag, epoch) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// QR update of the block Hessenberg after block step j, one warp-sized block
+// per new column q = j s + c (s co-resident blocks, cooperative launch): the
+// column takes every earlier reflector (earlier blocks: stored, loaded a few
+// ahead; this block: as the blocks of the earlier columns publish them), then
+// yields its own reflector (Householder, v[0] = 1, real tau, so that
+// H x = beta e1 with conj(alpha) beta real) and its column of the triangular
+// factor. Then block c applies this block's s reflectors to source c's
+// least-squares right-hand side, whose rows (j+1) s .. (j+2) s - 1 give the
+// source's residual estimate. The last block to finish decides whether the
+// cycle stops.
 struct LsArgs {
     double2 *Hb;        // (m+1) s x m s, column-major, ldh
     size_t ldh;
@@ -558,95 +605,116 @@ struct LsArgs {
 __global__ void __launch_bounds__(kLsThreads) k_bls(LsArgs a) {
     extern __shared__ double2 ls_raw[];
     double2 *col = ls_raw;                 // rows 0 .. (j+2) s - 1 of the column / right-hand side
-    __shared__ double2 red[2];
-    __shared__ double2 vsh[kBS + 1];
-    __shared__ int ok_sh;
-    const int tid = threadIdx.x, c = blockIdx.x, s = a.s;
+    const int lane = threadIdx.x, c = blockIdx.x, s = a.s;
     const int q = a.j * s + c, rows = (a.j + 2) * s;
     double2 *hcol = a.Hb + (size_t)q * a.ldh;
-    for (int i = tid; i < rows; i += kLsThreads) col[i] = hcol[i];
-    if (tid == 0) ok_sh = 1;
-    __syncthreads();
-    // reflectors of the earlier blocks
-    for (int qq = 0; qq < a.j * s; ++qq) {
-        const double2 *v = a.Vh + (size_t)qq * (s + 1);
-        for (int k = tid; k <= s; k += kLsThreads) vsh[k] = v[k];
-        __syncthreads();
-        apply_refl(vsh, a.tau[qq], col + qq, s, red);
+    for (int i = lane; i < rows; i += kLsThreads) col[i] = hcol[i];
+    __syncwarp();
+    bool ok = true;
+    // reflectors of the earlier blocks, kLsDepth loads in flight
+    const int nprev = a.j * s;
+    {
+        double2 vr[kLsDepth][3];
+        double tr[kLsDepth];
+#pragma unroll
+        for (int d = 0; d < kLsDepth; ++d) {
+            if (d < nprev) {
+                load_refl(a.Vh + (size_t)d * (s + 1), s, false, vr[d]);
+                tr[d] = __ldg(a.tau + d);
+            }
+        }
+        for (int q0 = 0; q0 < nprev; q0 += kLsDepth) {
+#pragma unroll
+            for (int d = 0; d < kLsDepth; ++d) {
+                const int qq = q0 + d;
+                if (qq < nprev) {
+                    warp_refl(vr[d], tr[d], col + qq, s);
+                    const int qn = qq + kLsDepth;
+                    if (qn < nprev) {
+                        load_refl(a.Vh + (size_t)qn * (s + 1), s, false, vr[d]);
+                        tr[d] = __ldg(a.tau + qn);
+                    }
+                }
+            }
+        }
     }
     // reflectors of this block, as they are published
-    for (int cc = 0; cc < c; ++cc) {
+    for (int cc = 0; cc < c && ok; ++cc) {
         const int qq = a.j * s + cc;
-        if (tid == 0 && ok_sh && !wait_flag(a.pub + qq, a.epoch)) ok_sh = 0;
-        __syncthreads();
-        if (!ok_sh) break;
-        const double2 *v = a.Vh + (size_t)qq * (s + 1);
-        for (int k = tid; k <= s; k += kLsThreads) vsh[k] = __ldcg(v + k);
-        const double tq = __ldcg(a.tau + qq);
-        __syncthreads();
-        apply_refl(vsh, tq, col + qq, s, red);
+        ok = warp_wait_flag(a.pub + qq, a.epoch);
+        if (!ok) break;
+        double2 vr[3];
+        load_refl(a.Vh + (size_t)qq * (s + 1), s, true, vr);
+        warp_refl(vr, __ldcg(a.tau + qq), col + qq, s);
     }
     // own reflector from rows q .. q + s
-    if (tid == 0) {
+    {
         const double2 alpha = col[q];
-        double sig = 0.0;
-        for (int k = 1; k <= s; ++k) sig += col[q + k].x * col[q + k].x + col[q + k].y * col[q + k].y;
+        double2 xs[3];
+        double sg = 0.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int k = lane + 32 * r;
+            xs[r] = (k >= 1 && k <= s) ? col[q + k] : make_double2(0.0, 0.0);
+            sg += xs[r].x * xs[r].x + xs[r].y * xs[r].y;
+        }
+        for (int o = 16; o; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
         const double aa = hypot(alpha.x, alpha.y);
-        double2 beta = alpha;
+        double2 beta = alpha, v0 = make_double2(1.0, 0.0);
         double t = 0.0;
-        vsh[0] = make_double2(1.0, 0.0);
-        if (sig > 0.0) {
-            const double nrm = sqrt(aa * aa + sig);
+        if (sg > 0.0) {
+            const double nrm = sqrt(aa * aa + sg);
             const double2 ph = aa > 0.0 ? cscal(1.0 / aa, alpha) : make_double2(1.0, 0.0);
             beta = cscal(-nrm, ph);
-            const double2 v0 = csub(alpha, beta);          // = ph (aa + nrm)
-            double vv = 1.0;
-            for (int k = 1; k <= s; ++k) {
-                vsh[k] = cdiv(col[q + k], v0);
-                vv += vsh[k].x * vsh[k].x + vsh[k].y * vsh[k].y;
-            }
-            t = 2.0 / vv;
-        } else {
-            for (int k = 1; k <= s; ++k) vsh[k] = make_double2(0.0, 0.0);
+            v0 = csub(alpha, beta);          // = ph (aa + nrm)
         }
-        if (!(isfinite(beta.x) && isfinite(beta.y) && isfinite(t))) ok_sh = 0;
-        col[q] = beta;
-        red[0] = make_double2(t, 0.0);
-    }
-    __syncthreads();
-    {
+        double vv = 0.0;
+        double2 vk[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            vk[r] = sg > 0.0 ? cdiv(xs[r], v0) : make_double2(0.0, 0.0);
+            vv += vk[r].x * vk[r].x + vk[r].y * vk[r].y;
+        }
+        for (int o = 16; o; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
+        if (sg > 0.0) t = 2.0 / (1.0 + vv);
+        if (!(isfinite(beta.x) && isfinite(beta.y) && isfinite(t))) ok = false;
         double2 *v = a.Vh + (size_t)q * (s + 1);
-        for (int k = tid; k <= s; k += kLsThreads) v[k] = vsh[k];
-        if (tid == 0) a.tau[q] = red[0].x;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int k = lane + 32 * r;
+            if (k == 0) v[0] = make_double2(1.0, 0.0);
+            else if (k <= s) v[k] = vk[r];
+        }
+        if (lane == 0) {
+            a.tau[q] = t;
+            col[q] = beta;
+        }
+        __syncwarp();
         // the column of the triangular factor: rows 0 .. q
-        for (int i = tid; i < rows; i += kLsThreads)
-            hcol[i] = i <= q ? col[i] : make_double2(0.0, 0.0);
+        for (int i = lane; i < rows; i += kLsThreads) hcol[i] = i <= q ? col[i] : make_double2(0.0, 0.0);
         __threadfence();
-        __syncthreads();
-        if (tid == 0) *(volatile int *)(a.pub + q) = a.epoch;
+        __syncwarp();
+        if (lane == 0) *(volatile int *)(a.pub + q) = a.epoch;
     }
     // source c: this block's reflectors on its right-hand side
     double2 *gcol = a.g + (size_t)c * a.ldh;
-    for (int i = tid; i < rows; i += kLsThreads) col[i] = gcol[i];
-    __syncthreads();
-    for (int cc = 0; cc < s; ++cc) {
+    for (int i = lane; i < rows; i += kLsThreads) col[i] = gcol[i];
+    __syncwarp();
+    for (int cc = 0; cc < s && ok; ++cc) {
         const int qq = a.j * s + cc;
-        if (tid == 0 && ok_sh && !wait_flag(a.pub + qq, a.epoch)) ok_sh = 0;
-        __syncthreads();
-        if (!ok_sh) break;
-        const double2 *v = a.Vh + (size_t)qq * (s + 1);
-        for (int k = tid; k <= s; k += kLsThreads) vsh[k] = __ldcg(v + k);
-        const double tq = __ldcg(a.tau + qq);
-        __syncthreads();
-        apply_refl(vsh, tq, col + qq, s, red);
+        if (cc != c) ok = warp_wait_flag(a.pub + qq, a.epoch);
+        if (!ok) break;
+        double2 vr[3];
+        load_refl(a.Vh + (size_t)qq * (s + 1), s, true, vr);
+        warp_refl(vr, __ldcg(a.tau + qq), col + qq, s);
     }
-    for (int i = tid; i < rows; i += kLsThreads) gcol[i] = col[i];
-    __syncthreads();
-    if (tid == 0) {
-        double e = 0.0;
-        for (int i = (a.j + 1) * s; i < rows; ++i) e += col[i].x * col[i].x + col[i].y * col[i].y;
+    for (int i = lane; i < rows; i += kLsThreads) gcol[i] = col[i];
+    double e = 0.0;
+    for (int i = (a.j + 1) * s + lane; i < rows; i += kLsThreads) e += col[i].x * col[i].x + col[i].y * col[i].y;
+    for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) {
         e = sqrt(e);
-        if (!ok_sh || !isfinite(e)) {
+        if (!ok || !isfinite(e)) {
             e = qnan();
             atomicOr(a.bad, 1);
         }
@@ -714,7 +782,7 @@ void set_attrs() {
         cudaFuncSetAttribute(k_bgram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcStages));
         cudaFuncSetAttribute(k_bcomb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcStages));
         cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(3 * kBS * kBS * sizeof(double2)));
+                             (int)(2 * kBS * kBS * sizeof(float2)));
         cudaFuncSetAttribute(k_bls, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kMaxRows * sizeof(double2)));
         cudaFuncSetAttribute(k_bbacksolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -760,8 +828,10 @@ void launch_bgram(const float2 *V, size_t sv, int nv, const float2 *W, size_t sw
     count_launch();
     if (prof_on())
         prof_end("block_gram_tc", st, ((double)nv + s) * Np * 8.0 + (double)nkc * nv * 512.0, 0.0);
+    prof_begin(st);
     k_bgram_sum<<<nv, kBS, 0, st>>>(part, nkc, nv, s, G, ldg, hacc, ldh, add);
     count_launch();
+    prof_end("block_gram_sum", st, (double)nkc * nv * 512.0, 0.0);
 }
 
 // out = alpha win + V (sign C), C: nv x s complex128 row-major (ldc)
@@ -831,10 +901,12 @@ void block_cholqr(helm_grid *g, float2 *W, float2 *out, int s, size_t Np) {
     const size_t N = g->N;
     for (int pass = 0; pass < 2; ++pass) {
         launch_bgram(W, Np, s, W, Np, s, Np, g->bpart.as<float>(), g->bG.as<double2>(), s, nullptr, 0, 0, st);
-        k_bchol<<<1, kCh, 3 * kBS * kBS * sizeof(double2), st>>>(g->bG.as<double2>(), s, pass == 0 ? 1e-5 : 0.0,
+        prof_begin(st);
+        k_bchol<<<1, kCh, 2 * kBS * kBS * sizeof(float2), st>>>(g->bG.as<double2>(), s, pass == 0 ? 1e-5 : 0.0,
                                                                  g->bRinv.as<double2>(), g->bR.as<double2>(),
                                                                  pass == 0);
         count_launch();
+        prof_end("block_cholesky", st, 0.0, 0.0);
         launch_bcomb(W, Np, s, g->bRinv.as<double2>(), s, 1.0, g->bimg.as<float>(), W, Np, 0.f,
                      pass == 0 ? W : out, Np, s, N, Np, st);
     }
@@ -903,7 +975,10 @@ helm_status solve_block_group(helm_grid *g, int s, const double2 *f, double tol,
             launch_stencil<double, float2, float2>(ST_APPLY, L0, shift_H(g), Zj, Np, (const float2 *)nullptr, 0, W,
                                                    Np, s, 0.0, nullptr, st);
             double2 *hcol = Hb + (size_t)j * s * ldh;
-            for (int pass = 0; pass < 2; ++pass) {
+            // block classical Gram-Schmidt twice (one pass loses orthogonality
+            // in the complex64 basis: about 1.7x the block steps, measured)
+            const int passes = 2;
+            for (int pass = 0; pass < passes; ++pass) {
                 launch_bgram(V, Np, nv, W, Np, s, Np, g->bpart.as<float>(), g->bG.as<double2>(), s, hcol, ldh,
                              pass, st);
                 launch_bcomb(V, Np, nv, g->bG.as<double2>(), s, -1.0, g->bimg.as<float>(), W, Np, 1.f, W, Np, s, N,
@@ -934,10 +1009,12 @@ helm_status solve_block_group(helm_grid *g, int s, const double2 *f, double tol,
             a.tol = tol;
             *(volatile int *)g->bhflag = 1;
             void *args[] = {&a};
+            prof_begin(st);
             cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_bls, dim3(s), dim3(kLsThreads), args,
                                                         (size_t)(j + 2) * s * sizeof(double2), st);
             if (e != cudaSuccess) return fail(HELM_ERR_CUDA, "least-squares update: %s", cudaGetErrorString(e));
             count_launch();
+            prof_end("block_least_squares", st, 0.0, 0.0);
             ++steps;
             k = j + 1;
             if ((s_ = sync_stream(g, "block step"))) return s_;
@@ -945,8 +1022,10 @@ helm_status solve_block_group(helm_grid *g, int s, const double2 *f, double tol,
         }
         // u += Z Y, Y = R^-1 g over the k block steps of the cycle
         const int K = k * s;
+        prof_begin(st);
         k_bbacksolve<<<s, 256, (size_t)K * sizeof(double2), st>>>(Hb, ldh, gl, K, s, g->bY.as<double2>());
         count_launch();
+        prof_end("block_backsolve", st, 0.0, 0.0);
         launch_bcomb(Z, Np, K, g->bY.as<double2>(), s, 1.0, g->bimg.as<float>(), W, Np, 0.f, W, Np, s, N, Np, st);
         k_badd<<<dim3((unsigned)std::min<size_t>((N + 255) / 256, 4096), s), 256, 0, st>>>(W, Np, u, N, s);
         count_launch();
