@@ -17,7 +17,10 @@ Helmholtz equation, part 1: Data modelling"):
                      flexible variant that stores the preconditioned vectors,
                      optionally from an initial guess; GMRES on the
                      split-preconditioned system of Eq. 5; block flexible
-                     GMRES (many sources sharing one block Krylov space).
+                     GMRES (many sources sharing one block Krylov space);
+                     GCRO-DR (restarted GMRES with a recycled, deflating
+                     subspace kept across restarts and across the systems of
+                     a frequency sweep).
 * ``multigrid``   -- the geometric V-cycle used on the GPU to apply the
                      inverse of the shifted Laplacian, written out step by
                      step (Jacobi, residual, full weighting, bilinear

@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["givens", "arnoldi", "gmres_right", "gmres_split", "block_fgmres"]
+__all__ = ["givens", "arnoldi", "gmres_right", "gmres_split", "block_fgmres", "gcrodr"]
 
 
 def givens(a: complex, b: complex):
@@ -292,4 +292,155 @@ def block_fgmres(A, F, tol, restart, maxiter, Pinv=None):
             break
     out["X"] = X
     out["iterations"] = its
+    return out
+
+
+def _recycle_space(Ghat, What_Zhat, k):
+    """Harmonic Ritz subspace for GCRO-DR: with A Zhat = What Ghat (What with
+    orthonormal columns), the harmonic Ritz pairs (theta, p) of A over
+    span(Zhat) solve Ghat^H Ghat p = theta Ghat^H (What^H Zhat) p. Returns an
+    orthonormal n x k basis P of the eigenvectors of the k smallest |theta|
+    (only the span matters) and those theta."""
+    A1 = Ghat.conj().T @ Ghat
+    A2 = Ghat.conj().T @ What_Zhat
+    theta, Y = np.linalg.eig(np.linalg.solve(A2, A1))
+    idx = np.argsort(np.abs(theta))[:k]
+    P, _ = np.linalg.qr(Y[:, idx])
+    return P, theta[idx]
+
+
+def gcrodr(A, f, tol, restart, k, maxiter, Pinv=None, x0=None, recycle=None):
+    """Restarted GMRES with a recycled subspace (GCRO-DR; Parks, de Sturler et
+    al.), right-preconditioned as in Eq. 7, for one system of a sequence.
+
+    The recycled space is kept in the preconditioned variable z: Ut (k columns)
+    with U = Pinv(Ut) in the solution space and C = A U orthonormal. Arnoldi
+    runs on (I - C C^H) A Pinv from a residual orthogonal to C, so the relation
+    A [U, Z_m] = [C, V_{m+1}] Ghat with Ghat = [[I, B_m], [0, Hbar_m]] holds;
+    each cycle minimises ||r|| over x + span([U, Z_m]) (y_z from the usual
+    least squares, y_u = -B_m y_z). After a cycle that did not converge the
+    recycled space becomes the k harmonic Ritz vectors of A over
+    span([Ut, V_m]) with the smallest |theta| (GMRES-DR in the first cycle,
+    when there is no recycled space yet), recombined so that C stays
+    orthonormal. Pinv must be a fixed linear map.
+
+    recycle: the Ut (N x k) returned by the previous system of the sequence
+    (None: none). For the new operator, U = Pinv(Ut), C = A U is
+    orthonormalised (the same column operations on U and Ut), and the initial
+    guess gains U C^H r0. Returns a dict with x, iterations, restarts,
+    true_residuals, converged and "recycle" (Ut for the next system).
+    """
+    f = np.asarray(f, dtype=np.complex128).ravel()
+    N = f.shape[0]
+    if Pinv is None:
+        Pinv = lambda v: v.copy()  # noqa: E731
+    x = np.zeros(N, dtype=np.complex128) if x0 is None else np.array(x0, np.complex128).ravel()
+    fnorm = np.linalg.norm(f)
+    out = {"true_residuals": [], "iterations": 0, "restarts": 0, "converged": False, "recycle": None}
+    if fnorm == 0.0:
+        out.update(x=np.zeros(N, dtype=np.complex128), converged=True, recycle=recycle)
+        return out
+
+    def orthonormalise(Ct, U, Ut):
+        # thin QR of Ct by modified Gram-Schmidt (twice), the same column
+        # operations applied to U and Ut so that A U = C still holds
+        Ct, U, Ut = Ct.copy(), U.copy(), Ut.copy()
+        kk = Ct.shape[1]
+        for i in range(kk):
+            for _ in range(2):
+                for l in range(i):
+                    c = np.vdot(Ct[:, l], Ct[:, i])
+                    Ct[:, i] -= c * Ct[:, l]
+                    U[:, i] -= c * U[:, l]
+                    Ut[:, i] -= c * Ut[:, l]
+            nrm = np.linalg.norm(Ct[:, i])
+            Ct[:, i] /= nrm
+            U[:, i] /= nrm
+            Ut[:, i] /= nrm
+        return Ct, U, Ut
+
+    r = f - A(x)
+    C = U = Ut = None
+    if recycle is not None and recycle.shape[1] > 0:
+        Ut = np.array(recycle, dtype=np.complex128)
+        U = np.column_stack([Pinv(Ut[:, i]) for i in range(Ut.shape[1])])
+        Ct = np.column_stack([A(U[:, i]) for i in range(U.shape[1])])
+        C, U, Ut = orthonormalise(Ct, U, Ut)
+        c = C.conj().T @ r
+        x = x + U @ c
+        r = r - C @ c
+    its = 0
+    while its < maxiter:
+        beta = np.linalg.norm(r)
+        if beta <= tol * fnorm:
+            out["converged"] = True
+            break
+        kc = 0 if C is None else C.shape[1]
+        m = restart
+        V = np.zeros((N, m + 1), dtype=np.complex128)
+        Z = np.zeros((N, m), dtype=np.complex128)
+        Hb = np.zeros((m + 1, m), dtype=np.complex128)
+        B = np.zeros((kc, m), dtype=np.complex128)
+        V[:, 0] = r / beta
+        steps = 0
+        y = None
+        for j in range(m):
+            Z[:, j] = Pinv(V[:, j])
+            w = A(Z[:, j])
+            if kc:
+                B[:, j] = C.conj().T @ w
+                w = w - C @ B[:, j]
+            for i in range(j + 1):
+                Hb[i, j] = np.vdot(V[:, i], w)
+                w = w - Hb[i, j] * V[:, i]
+            Hb[j + 1, j] = np.linalg.norm(w)
+            V[:, j + 1] = w / Hb[j + 1, j]
+            its += 1
+            steps = j + 1
+            e1 = np.zeros(j + 2, dtype=np.complex128)
+            e1[0] = beta
+            y = np.linalg.lstsq(Hb[:j + 2, :j + 1], e1, rcond=None)[0]
+            est = np.linalg.norm(e1 - Hb[:j + 2, :j + 1] @ y)
+            if est <= tol * fnorm or its >= maxiter:
+                break
+        x = x + Z[:, :steps] @ y
+        if kc:
+            x = x - U @ (B[:, :steps] @ y)
+        r = f - A(x)
+        out["restarts"] += 1
+        out["true_residuals"].append(np.linalg.norm(r) / fnorm)
+        if np.linalg.norm(r) <= tol * fnorm:
+            out["converged"] = True
+            break
+        if k > 0 and steps == m:
+            # harmonic Ritz vectors over span([Ut, V_m]) (z variable) and their
+            # images: Zhat = [U, Z_m] (solution), What = [C, V_{m+1}]
+            n = kc + m
+            Ghat = np.zeros((n + 1, n), dtype=np.complex128)
+            Ghat[:kc, :kc] = np.eye(kc)
+            Ghat[:kc, kc:] = B
+            Ghat[kc:, kc:] = Hb
+            Wt = np.zeros((n + 1, n), dtype=np.complex128)   # What^H [Ut, V_m]
+            if kc:
+                Wt[:kc, :kc] = C.conj().T @ Ut
+                Wt[kc:, :kc] = V.conj().T @ Ut
+            Wt[kc:kc + m, kc:] = np.eye(m)
+            P, _ = _recycle_space(Ghat, Wt, min(k, n))
+            Zz = np.hstack([Ut, V[:, :m]]) if kc else V[:, :m]
+            Zu = np.hstack([U, Z]) if kc else Z
+            Wh = np.hstack([C, V]) if kc else V
+            Q = Ghat @ P
+            # C = What Q R^-1 with R from Q^H Q (What has orthonormal columns)
+            R = np.linalg.cholesky(Q.conj().T @ Q).conj().T
+            Rinv = np.linalg.inv(R)
+            C = Wh @ (Q @ Rinv)
+            U = Zu @ (P @ Rinv)
+            Ut = Zz @ (P @ Rinv)
+            c = C.conj().T @ r
+            x = x + U @ c
+            r = r - C @ c
+    out["x"] = x
+    out["iterations"] = its
+    out["recycle"] = Ut
+    out["U"], out["C"] = U, C
     return out
