@@ -163,7 +163,8 @@ def cpu_baseline(w, budget_s=12.0):
             "_u": np.asarray(u_lu).ravel()}
 
 
-def oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, plain_keep, extra_keep, variants, rho):
+def oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, U2r_keep, plain_keep, extra_keep, variants, rho,
+                  sweep401):
     """Relative L2 error of every reported GPU result against the oracle's
     sparse-LU solution (factor once per operator, then triangular solves),
     and the strong CPU baseline of the 801x401 workload: one factorisation per
@@ -182,6 +183,9 @@ def oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, plain_keep, extra_keep, v
     u_lu = lu.solve(w.rhs().ravel())
     for side in ("left", "split"):
         out[side] = err(variants[side].pop("_u"), u_lu)
+    lu_f = direct.lu_factor_H(w.n, w.h, m, 2 * np.pi * sweep401["frequencies_hz"][-1], w.alpha)
+    for name, Us in sweep401.pop("_keep").items():
+        out[f"sweep401_{name}"] = max(err(Us[i], lu_f.solve(F[k])) for i, k in enumerate((0, 31, 63)))
     Hr = density.assemble_H_rho(w.n, w.h, m, rho, w.omega(), w.alpha)
     out["density"] = err(variants["density"].pop("_u"), direct.spla.splu(Hr.tocsc()).solve(w.rhs().ravel()))
     wx, Ux = extra_keep["1d_well"]
@@ -189,7 +193,7 @@ def oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, plain_keep, extra_keep, v
     out["1d_well"] = max(err(Ux[k], lu1.solve(wx.rhs(k).ravel())) for k in range(Ux.shape[0]))
     # 801x401: per frequency, the sampled batched sources and the plain sample
     m2 = wb.slowness()
-    per_f, per_fb, plain, cpu = [], [], [], None
+    per_f, per_fb, per_fr, plain, cpu = [], [], [], [], None
     for fi, fq in enumerate(wb.freqs):
         t = time.perf_counter()
         lu2 = direct.lu_factor_H(wb.n, wb.h, m2, wb.omega(fi), wb.alpha)
@@ -197,6 +201,7 @@ def oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, plain_keep, extra_keep, v
         ref = {k: lu2.solve(wb.rhs(k).ravel()) for k in LU_SAMPLE}
         per_f.append(max(err(U2_keep[fi][i], ref[k]) for i, k in enumerate(LU_SAMPLE)))
         per_fb.append(max(err(U2b_keep[fi][i], ref[k]) for i, k in enumerate(LU_SAMPLE)))
+        per_fr.append(max(err(U2r_keep[fi][i], ref[k]) for i, k in enumerate(LU_SAMPLE)))
         plain += [err(plain_keep[(fi, k)], lu2.solve(wb.rhs(k).ravel())) for k in PLAIN_SAMPLE]
         if fq == 10.0:
             Fb = np.stack([wb.rhs(k).ravel() for k in range(len(wb.sources))]).T
@@ -210,6 +215,7 @@ def oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, plain_keep, extra_keep, v
                              f"single-threaded"}
     out["batched_801x401_per_frequency"] = per_f
     out["block_801x401_per_frequency"] = per_fb
+    out["recycle_801x401_per_frequency"] = per_fr
     out["plain_801x401_sample"] = max(plain)
     return out, cpu
 
@@ -659,6 +665,38 @@ def main():
         U2b_keep[fi] = U2[list(LU_SAMPLE)].cpu().numpy()
     t_blk = time.perf_counter() - t_blk
     del gk
+    # a frequency sweep with each source's solution carried to the next
+    # frequency as its initial guess (warm start), without and with GCRO-DR
+    # recycling (8 recycled vectors per source kept across restarts and
+    # frequencies); complex64 V-cycle, complex128 basis (recycling needs it)
+    sweep = {}
+    U2r_keep = {}
+    for name, rk in (("warm_start", 0), ("recycle_k8", 8)):
+        gs = helm.Grid(wb.n, wb.h, restart=wb.restart, precond="mg", precision="mixed", recycle=rk)
+        gs.set_stream(stream.cuda_stream)
+        gs.set_model(m2, wb.omega(0), wb.alpha)
+        gs.set_shift(*wb.beta)
+        for lev, (dn, up) in enumerate(tiles2):
+            gs.set_tiles(lev, dn, up)
+        U2.zero_()
+        rows = []
+        torch.cuda.synchronize()
+        t_sw = time.perf_counter()
+        for fi, fq in enumerate(wb.freqs):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            gs.set_model(m2, wb.omega(fi), wb.alpha)
+            gs.set_shift(*wb.beta)
+            e0.record(stream)
+            _, its_s, rr_s = gs.solve_batch(len(wb.sources), F2, wb.tol, U2, warm=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rows.append({"freq_hz": fq, "solve_ms": e0.elapsed_time(e1), "iterations_max": int(its_s.max()),
+                         "iterations_mean": float(its_s.mean()), "true_rel_residual_max": float(rr_s.max())})
+            if rk:
+                U2r_keep[fi] = U2[list(LU_SAMPLE)].cpu().numpy()
+        t_sw = time.perf_counter() - t_sw
+        sweep[name] = {"wall_s": t_sw, "solves_per_s": world * nsol / t_sw, "per_frequency": rows}
+        del gs
     # the plain one-at-a-time complex128 path on the same workload: a sample
     # of sources per frequency, each one helm_solve (FGMRES(30), complex128
     # V-cycle and basis), timed with CUDA events around each solve
@@ -696,7 +734,8 @@ def main():
                      "batched_vs_plain": (world * nsol / t_all) / plain_rate,
                      "block_fgmres": {"solves": nsol, "wall_s": t_blk, "solves_per_s": world * nsol / t_blk,
                                       "per_frequency": blk_f, "vs_plain": (world * nsol / t_blk) / plain_rate,
-                                      "vs_lockstep": t_all / t_blk}}
+                                      "vs_lockstep": t_all / t_blk},
+                     "sweep_recycling": sweep}
     del F2, U2
 
     serving = serving_run(helm)
@@ -772,6 +811,40 @@ def main():
     variants["left"]["stop"] = variants["split"]["stop"] = (
         "preconditioned residual ||M^-1 (f - H u)|| <= 1e-8 ||M^-1 f||")
 
+    # ---- a fine frequency sweep on 401x201 (the 64 sources, 10.0 .. 10.5 Hz):
+    # each source starts from its solution at the previous frequency, without
+    # and with GCRO-DR recycling (8 vectors per source, kept across restarts
+    # and frequencies); complex64 V-cycle, complex128 basis
+    fine = [10.0 + 0.1 * i for i in range(6)]
+    sweep401 = {"frequencies_hz": fine, "sources": BATCH_SOURCES, "_keep": {}}
+    for name, rk in (("warm_start", 0), ("recycle_k8", 8)):
+        gs = helm.Grid(w.n, w.h, restart=w.restart, precond="mg", precision="mixed", recycle=rk)
+        gs.set_stream(stream.cuda_stream)
+        gs.set_model(md, 2 * math.pi * fine[0], w.alpha)
+        gs.set_shift(*w.beta)
+        for lev, (dn, up) in enumerate(tuned["tiles"]):
+            gs.set_tiles(lev, dn, up)
+        gs.set_options(nu1=tuned["nu"][0], nu2=tuned["nu"][1])
+        Ud.zero_()
+        rows = []
+        for fq in fine:
+            gs.set_model(md, 2 * math.pi * fq, w.alpha)
+            gs.set_shift(*w.beta)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, its_s, rr_s = gs.solve_batch(BATCH_SOURCES, Fd, w.tol, Ud, warm=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rows.append({"freq_hz": round(fq, 2), "solve_ms": e0.elapsed_time(e1),
+                         "iterations_max": int(its_s.max()), "iterations_mean": float(its_s.mean()),
+                         "true_rel_residual_max": float(rr_s.max())})
+        sweep401[name] = {"ms_total": sum(r["solve_ms"] for r in rows),
+                          "iterations_mean_total": sum(r["iterations_mean"] for r in rows),
+                          "per_frequency": rows}
+        sweep401["_keep"][name] = Ud[[0, 31, 63]].cpu().numpy()
+        del gs
+    sweep401["recycle_vs_warm_time"] = sweep401["warm_start"]["ms_total"] / sweep401["recycle_k8"]["ms_total"]
+
     cpu = None
     rel_err_lu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -781,14 +854,20 @@ def main():
         u_gpu = ud.cpu().numpy().ravel()
         rel_err_lu = float(np.linalg.norm(u_gpu - u_lu) / np.linalg.norm(u_lu))
         cpu["host_cores"] = os.cpu_count()
-        errs, cpu_801 = oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, plain_keep, extra_keep, variants,
-                                      rho)
+        errs, cpu_801 = oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, U2r_keep, plain_keep, extra_keep,
+                                      variants, rho, sweep401)
+        for name in ("warm_start", "recycle_k8"):
+            sweep401[name]["rel_err_vs_oracle_lu_last_freq"] = errs[f"sweep401_{name}"]
+        sweep401["rel_err_sources"] = [0, 31, 63]
         batched["rel_err_vs_oracle_lu_max"] = errs["batched_mixed_ds"]
         batched["complex128_arnoldi_basis"]["rel_err_vs_oracle_lu_max"] = errs["batched_mixed"]
         batched["block_fgmres"]["rel_err_vs_oracle_lu_max"] = errs["batched_block"]
         for pf, e in zip(batched_multi["block_fgmres"]["per_frequency"], errs["block_801x401_per_frequency"]):
             pf["rel_err_vs_oracle_lu_max"] = e
             pf["rel_err_sources"] = list(LU_SAMPLE)
+        for pf, e in zip(batched_multi["sweep_recycling"]["recycle_k8"]["per_frequency"],
+                         errs["recycle_801x401_per_frequency"]):
+            pf["rel_err_vs_oracle_lu_max"] = e
         for pf, e in zip(batched_multi["per_frequency"], errs["batched_801x401_per_frequency"]):
             pf["rel_err_vs_oracle_lu_max"] = e
             pf["rel_err_sources"] = list(LU_SAMPLE)
@@ -802,6 +881,7 @@ def main():
             variants[vname]["rel_err_vs_oracle_lu"] = errs[vname]
     for v in variants.values():
         v.pop("_u", None)
+    sweep401.pop("_keep", None)
 
     if rank == 0:
         line = {
@@ -831,6 +911,7 @@ def main():
             "serving": serving,
             "other_workloads": extra,
             "variants_401x201": variants,
+            "sweep_401x201_10.0-10.5Hz": sweep401,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -109,6 +109,9 @@ typedef struct {
                              /*    recurrences in lock-step (default); 1: block FGMRES */
                              /*    -- up to 64 sources share one block Krylov space    */
                              /*    (see helm_solve_batch)                              */
+    int recycle;             /* k = 0 (default): none; 1..16: GCRO-DR, k recycled      */
+                             /*    vectors per right-hand side kept across restarts   */
+                             /*    and across solves (see helm_solve_batch)            */
 } helm_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -195,7 +198,22 @@ helm_status helm_solve(helm_grid *g, const helm_c128 *f, double tol, helm_c128 *
  * solution and the true residual stay complex128, and a group restarts until
  * every true residual is <= tol. iterations then counts block steps. Needs
  * precision HELM_PREC_MIXED, precond MG or EXACT, side RIGHT and restart <= 32
- * (HELM_ERR_UNSUPPORTED otherwise, from helm_set_options). */
+ * (HELM_ERR_UNSUPPORTED otherwise, from helm_set_options).
+ *
+ * With options.recycle = k > 0 each right-hand side runs GCRO-DR: restarted
+ * GMRES (Eq. 7) that keeps k recycled vectors U (with C = H U orthonormal)
+ * and orthogonalises every Krylov vector against C as well. A cycle that
+ * ends unconverged replaces them by the k harmonic Ritz vectors of the
+ * smallest magnitude over the recycled and the new Krylov vectors, so slowly
+ * converging directions are deflated across restarts. The recycled vectors
+ * stay in the grid after the call: the next call with the same nrhs (e.g. the
+ * next frequency of a sweep, after helm_set_model) rebuilds U and C for the
+ * new H and M and starts with them, the initial guess gaining the part of
+ * the solution they carry. A change of nrhs, restart, k or precision starts
+ * empty; a right-hand side whose solve never ran a full cycle of restart
+ * steps has none yet. Each right-hand side's result is the same alone and in
+ * any batch. Needs precision HELM_PREC_F64 or HELM_PREC_MIXED, precond MG or
+ * EXACT, side RIGHT, reorth 0, block 0, k <= restart <= 40. */
 helm_status helm_solve_batch(helm_grid *g, int nrhs, const helm_c128 *f, double tol,
                              helm_c128 *u, int *iterations, double *true_rel_residual);
 

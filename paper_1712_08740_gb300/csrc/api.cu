@@ -229,6 +229,7 @@ void helm_default_options(helm_options *o) {
     o->graphs = 1;
     o->side = HELM_SIDE_RIGHT;
     o->block = 0;
+    o->recycle = 0;
 }
 
 const char *helm_last_error(void) { return helm::last_error(); }
@@ -317,6 +318,13 @@ helm_status helm_set_options(helm_grid *g, const helm_options *o) {
     if (o->reorth < 0 || o->reorth > 2) return fail(HELM_ERR_ARG, "reorth must be 0, 1 or 2");
     if (o->side < 0 || o->side > 2) return fail(HELM_ERR_ARG, "side must be 0, 1 or 2");
     if (o->block < 0 || o->block > 1) return fail(HELM_ERR_ARG, "block must be 0 or 1");
+    if (o->recycle < 0 || o->recycle > 16) return fail(HELM_ERR_ARG, "recycle must be 0..16");
+    if (o->recycle &&
+        (o->precision == HELM_PREC_MIXED_DS || o->precond == HELM_PRECOND_NONE || o->side != HELM_SIDE_RIGHT ||
+         o->reorth != 0 || o->block || o->restart > 40 || o->restart < o->recycle))
+        return fail(HELM_ERR_UNSUPPORTED,
+                    "recycling needs precision HELM_PREC_F64 or HELM_PREC_MIXED, a preconditioner, side RIGHT, "
+                    "reorth 0, block 0 and recycle <= restart <= 40");
     if (o->block &&
         (o->precision != HELM_PREC_MIXED || o->precond == HELM_PRECOND_NONE || o->side != HELM_SIDE_RIGHT ||
          o->restart > 32))
@@ -365,6 +373,7 @@ helm_status helm_set_model(helm_grid *g, const double *m, double omega, double a
     g->has_model = false;
     g->ready = false;
     g->hdiag_ok = false;
+    g->rec_stale = true;
     if (bad) return fail(HELM_ERR_NONFINITE, "slowness must be finite and > 0 at every node");
     g->omega = omega;
     g->alpha = alpha;
@@ -378,6 +387,7 @@ helm_status helm_set_density(helm_grid *g, const double *rho) {
     if (!rho) {
         g->has_rho = false;
         g->ready = false;
+        g->rec_stale = true;
         return HELM_OK;
     }
     if (g->opt.precision == HELM_PREC_MIXED_DS)
@@ -393,6 +403,7 @@ helm_status helm_set_density(helm_grid *g, const double *rho) {
     cudaMemcpyAsync(&bad, g->flag.p, sizeof(int), cudaMemcpyDeviceToHost, g->st);
     if ((s = sync_stream(g, "helm_set_density"))) return s;
     g->ready = false;
+    g->rec_stale = true;
     if (bad) {
         g->has_rho = false;
         return fail(HELM_ERR_NONFINITE, "rho must be finite and > 0 at every node");
@@ -409,6 +420,7 @@ helm_status helm_set_shift(helm_grid *g, double beta1, double beta2) {
     g->beta1 = beta1;
     g->beta2 = beta2;
     g->ready = false;
+    g->rec_stale = true;
     helm_status s = build_hierarchy(g);
     if (s) return s;
     return sync_stream(g, "helm_set_shift");

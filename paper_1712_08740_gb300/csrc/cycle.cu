@@ -346,6 +346,7 @@ void launch_givens_scale(const CycleState &S, int j, const double2 *hb, int hstr
     if (nrhs > 1 && nbs > cap) nbs = cap;
     if (nbs < 1) nbs = 1;
     if (nbs > 65535) nbs = 65535;
+    if (!w) nbs = 0;   // least-squares blocks only: the caller scales w itself
     prof_begin(st);
     k_givens_scale<SV><<<dim3(1 + (unsigned)nbs, nrhs), kGivensThreads, sm, st>>>(
         S, j, hb, hstride, two, nrm2, nrhs, tol, max_iters, host_flag, qs ? 1 : 0, w, sw, N);

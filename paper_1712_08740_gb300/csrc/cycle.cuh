@@ -32,7 +32,10 @@ void prepare_cycle_kernels();   // shared-memory attributes; call outside graph 
 void launch_cycle_init(const CycleState &S, const double *nrm2, int nrhs, int *host_flag,
                        cudaStream_t st);
 // least-squares update of step j and v_{j+1} = w / ||w|| in one launch;
-// SV: basis type (double2, or float4 for the double-single basis)
+// SV: basis type (double2, or float4 for the double-single basis). The
+// scaling of a right-hand side that stops at this step may be skipped (its
+// v_{j+1} is never read again by FGMRES); w = nullptr launches the
+// least-squares part only, for a caller that scales w itself.
 template <typename SV>
 void launch_givens_scale(const CycleState &S, int j, const double2 *hb, int hstride, int two,
                          const double *nrm2, int nrhs, double tol, int max_iters, int *host_flag,

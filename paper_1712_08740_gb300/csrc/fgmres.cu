@@ -399,6 +399,7 @@ helm_status workspace_for(helm_grid *g, int nrhs) { return ensure_workspace(g, n
 helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, double2 *u,
                          int *iterations, double *relres_out, bool warm) {
     if (g->opt.block) return solve_block_device(g, nrhs, f, tol, u, iterations, relres_out, warm);
+    if (g->opt.recycle) return solve_recycle_device(g, nrhs, f, tol, u, iterations, relres_out, warm);
     helm_status s;
     if ((s = ensure_ready(g))) return s;
     if ((s = ensure_workspace(g, nrhs))) return s;

@@ -84,6 +84,14 @@ struct helm_grid {
     int bls_epoch = 0;
     int *bhflag = nullptr;              // host-mapped "cycle goes on" flag
 
+    // Krylov recycling (helm_options.recycle): [C | V] per right-hand side,
+    // U and Ut, Z, Ritz scratch; kept across solves while the shape stays
+    helm::DevBuf rCV, rU, rUt, rZ, rNew, rRes, rH, rB, rWt, rcC, rcU, rScr, rhb, rc, rpart, rcnt, rbad;
+    helm::DevBuf rupd, rhas;            // per right-hand side: update now / holds a recycled space
+    int rec_nrhs = 0, rec_k = 0, rec_m = 0, rec_prec = -1;
+    bool rec_any = false;               // some right-hand side holds a recycled space
+    bool rec_stale = false;             // the operator changed: rebuild U and C from Ut
+
     // CUDA graphs of one Arnoldi step per j, valid for graph_key
     std::vector<cudaGraphExec_t> step_graphs;
     std::vector<uint64_t> step_launches;                           // kernels per step graph

@@ -29,6 +29,9 @@ helm_status workspace_for(helm_grid *g, int nrhs);
 helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, double2 *u,
                          int *iterations, double *relres_out, bool warm = false);
 const char *last_error();
+// GCRO-DR with a recycled subspace kept across restarts and solves (helm_options.recycle)
+helm_status solve_recycle_device(helm_grid *g, int nrhs, const double2 *f, double tol, double2 *u,
+                                 int *iterations, double *relres_out, bool warm);
 // block FGMRES (helm_options.block): nrhs sources in blocks of at most 64
 helm_status solve_block_device(helm_grid *g, int nrhs, const double2 *f, double tol, double2 *u,
                                int *iterations, double *relres_out, bool warm);

@@ -44,7 +44,7 @@ class helm_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega_jacobi", ctypes.c_double), ("coarse_max", ctypes.c_int),
                 ("reorth", ctypes.c_int), ("graphs", ctypes.c_int), ("side", ctypes.c_int),
-                ("block", ctypes.c_int)]
+                ("block", ctypes.c_int), ("recycle", ctypes.c_int)]
 
 
 class helm_server_config(ctypes.Structure):
@@ -415,7 +415,7 @@ class Grid:
 
     def __init__(self, n, h, *, restart=30, precond="mg", precision="f64", nu1=1, nu2=1,
                  omega_jacobi=0.8, coarse_max=1500, reorth=0, max_iters=5000, graphs=True,
-                 side="right", block=False):
+                 side="right", block=False, recycle=0):
         self.n = tuple(int(k) for k in n)
         self.N = int(np.prod(self.n))
         self.h = float(h)
@@ -423,7 +423,8 @@ class Grid:
         _live.add(self)
         self.set_options(restart=restart, precond=precond, precision=precision, nu1=nu1,
                          nu2=nu2, omega_jacobi=omega_jacobi, coarse_max=coarse_max,
-                         reorth=reorth, max_iters=max_iters, graphs=graphs, side=side, block=block)
+                         reorth=reorth, max_iters=max_iters, graphs=graphs, side=side, block=block,
+                         recycle=recycle)
 
     def set_options(self, **kw):
         o = helm_get_options(self._g)
