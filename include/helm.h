@@ -71,10 +71,16 @@ typedef enum {
     HELM_PREC_F64 = 0,       /* V-cycle and Arnoldi in complex128                      */
     HELM_PREC_MIXED = 1,     /* V-cycle in complex64 (z stored in complex64), Arnoldi   */
                              /* orthogonalisation in complex128                        */
-    HELM_PREC_MIXED_DS = 2   /* as MIXED, but the Arnoldi basis is stored and           */
+    HELM_PREC_MIXED_DS = 2,  /* as MIXED, but the Arnoldi basis is stored and           */
                              /* orthogonalised in double-single arithmetic (pairs of   */
                              /* FP32 values, ~48-bit significands, FP32 pipe); H z,    */
                              /* Hessenberg, norms and the true residual in complex128  */
+    HELM_PREC_MIXED_C64 = 3  /* as MIXED_DS, but the basis vectors are stored in        */
+                             /* complex64 (half the bytes the Gram-Schmidt passes      */
+                             /* stream); w = H z and its orthogonalisation stay        */
+                             /* double-single until v_{j+1} = w / ||w|| is rounded.     */
+                             /* Needs side RIGHT, reorth 0, precond MG or EXACT and a  */
+                             /* constant density                                       */
 } helm_precision;
 
 /* Where M^-1 enters the Krylov operator (Eq. 5: Ml^-1 H Mr^-1 z = Ml^-1 f,
@@ -155,8 +161,8 @@ helm_status helm_set_model(helm_grid *g, const double *m, double omega, double a
  * keeps the same -div(rho grad) and boundary rows (Eq. 6 with rho), so H - M
  * stays diagonal; coarser levels inject rho like the slowness. With a density
  * the V-cycle runs the general (unfused) level kernels, and the
- * HELM_PREC_MIXED_DS basis, helm_apply_H_ds and helm_true_residual_noalloc
- * are not available (HELM_ERR_UNSUPPORTED). Invalidates the preconditioner.
+ * HELM_PREC_MIXED_DS and HELM_PREC_MIXED_C64 bases, helm_apply_H_ds and
+ * helm_true_residual_noalloc are not available (HELM_ERR_UNSUPPORTED). Invalidates the preconditioner.
  * Errors: HELM_ERR_ARG, HELM_ERR_NONFINITE, HELM_ERR_UNSUPPORTED,
  * HELM_ERR_NOMEM, HELM_ERR_CUDA. */
 helm_status helm_set_density(helm_grid *g, const double *rho);

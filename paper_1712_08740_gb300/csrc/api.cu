@@ -309,7 +309,7 @@ helm_status helm_set_options(helm_grid *g, const helm_options *o) {
     if (o->restart < 1 || o->restart > 256) return fail(HELM_ERR_ARG, "restart must be 1..256");
     if (o->max_iters < 1) return fail(HELM_ERR_ARG, "max_iters must be >= 1");
     if (o->precond < 0 || o->precond > 2) return fail(HELM_ERR_ARG, "bad precond");
-    if (o->precision < 0 || o->precision > 2) return fail(HELM_ERR_ARG, "bad precision");
+    if (o->precision < 0 || o->precision > 3) return fail(HELM_ERR_ARG, "bad precision");
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 > 16 || o->nu2 > 16)
         return fail(HELM_ERR_ARG, "nu1, nu2 must be 0..16");
     if (!(o->omega_jacobi > 0.0 && o->omega_jacobi <= 1.0))
@@ -320,8 +320,8 @@ helm_status helm_set_options(helm_grid *g, const helm_options *o) {
     if (o->block < 0 || o->block > 1) return fail(HELM_ERR_ARG, "block must be 0 or 1");
     if (o->recycle < 0 || o->recycle > 16) return fail(HELM_ERR_ARG, "recycle must be 0..16");
     if (o->recycle &&
-        (o->precision == HELM_PREC_MIXED_DS || o->precond == HELM_PRECOND_NONE || o->side != HELM_SIDE_RIGHT ||
-         o->reorth != 0 || o->block || o->restart > 40 || o->restart < o->recycle))
+        ((o->precision != HELM_PREC_F64 && o->precision != HELM_PREC_MIXED) || o->precond == HELM_PRECOND_NONE ||
+         o->side != HELM_SIDE_RIGHT || o->reorth != 0 || o->block || o->restart > 40 || o->restart < o->recycle))
         return fail(HELM_ERR_UNSUPPORTED,
                     "recycling needs precision HELM_PREC_F64 or HELM_PREC_MIXED, a preconditioner, side RIGHT, "
                     "reorth 0, block 0 and recycle <= restart <= 40");
@@ -331,6 +331,12 @@ helm_status helm_set_options(helm_grid *g, const helm_options *o) {
         return fail(HELM_ERR_UNSUPPORTED,
                     "block FGMRES needs precision HELM_PREC_MIXED, a preconditioner, side RIGHT and "
                     "restart <= 32");
+    if (o->precision == HELM_PREC_MIXED_C64 &&
+        (o->side != HELM_SIDE_RIGHT || o->reorth != 0 || o->precond == HELM_PRECOND_NONE))
+        return fail(HELM_ERR_UNSUPPORTED,
+                    "a complex64 Arnoldi basis needs side RIGHT, reorth 0 and a preconditioner");
+    if (g->has_rho && o->precision == HELM_PREC_MIXED_C64)
+        return fail(HELM_ERR_UNSUPPORTED, "a variable density needs precision HELM_PREC_F64 or HELM_PREC_MIXED");
     if (g->has_rho && o->precision == HELM_PREC_MIXED_DS)
         return fail(HELM_ERR_UNSUPPORTED, "a variable density needs precision HELM_PREC_F64 or HELM_PREC_MIXED");
     if (o->side != HELM_SIDE_RIGHT && o->precond != HELM_PRECOND_NONE &&
@@ -390,7 +396,7 @@ helm_status helm_set_density(helm_grid *g, const double *rho) {
         g->rec_stale = true;
         return HELM_OK;
     }
-    if (g->opt.precision == HELM_PREC_MIXED_DS)
+    if (g->opt.precision == HELM_PREC_MIXED_DS || g->opt.precision == HELM_PREC_MIXED_C64)
         return fail(HELM_ERR_UNSUPPORTED, "a variable density needs precision HELM_PREC_F64 or HELM_PREC_MIXED");
     MGLevel &L = g->lv[0];
     helm_status s;

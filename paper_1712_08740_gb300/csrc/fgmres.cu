@@ -53,14 +53,17 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
     const size_t N = g->N;
     helm_status s;
     const size_t zsz = (prec == HELM_PREC_F64) ? sizeof(double2) : sizeof(float2);
-    if ((s = g->V.ensure((size_t)nrhs * (m + 1) * N * sizeof(double2)))) return s;
+    const size_t vbytes = (prec == HELM_PREC_MIXED_C64) ? (size_t)nrhs * (m + 1) * c64_stride(N) * sizeof(float2)
+                                                        : (size_t)nrhs * (m + 1) * N * sizeof(double2);
+    if ((s = g->V.ensure(vbytes))) return s;
     if (pc != HELM_PRECOND_NONE) {
         if ((s = g->Z.ensure((size_t)nrhs * m * N * zsz))) return s;
 
     }
     const int nv = m + 1;
     const size_t R = (size_t)nrhs;
-    if (prec == HELM_PREC_MIXED_DS && ((s = g->rbuf.ensure(R * N * sizeof(double2))) ||
+    if ((prec == HELM_PREC_MIXED_DS || prec == HELM_PREC_MIXED_C64) &&
+        ((s = g->rbuf.ensure(R * N * sizeof(double2))) ||
                                        (s = g->hdiag.ensure(N * sizeof(float4)))))
         return s;
     if (left_side(g) && ((s = g->rbuf.ensure(R * N * sizeof(double2))) ||
@@ -70,7 +73,8 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
     if ((s = g->nrm.ensure(R * sizeof(double)))) return s;
     if ((s = g->yv.ensure(R * m * sizeof(double2)))) return s;
     size_t per_rhs = (size_t)kMaxBlocks * nv;
-    if (prec == HELM_PREC_MIXED_DS) per_rhs = std::max(per_rhs, ds_partial_per_rhs(N, nv));
+    if (prec == HELM_PREC_MIXED_DS || prec == HELM_PREC_MIXED_C64)
+        per_rhs = std::max(per_rhs, ds_partial_per_rhs(N, nv));
     if ((s = g->partial.ensure(R * per_rhs * sizeof(double2)))) return s;
     if ((s = g->counter.ensure(R * sizeof(unsigned)))) return s;
     cudaMemsetAsync(g->counter.p, 0, R * sizeof(unsigned), g->st);
@@ -148,6 +152,9 @@ void apply_precond_j(helm_grid *g, int j, int nrhs, const int *act) {
         vcycle<double, double2>(g, vj, sV, g->Z.as<double2>() + (size_t)j * N, sZ, nrhs, act);
     else if (g->opt.precision == HELM_PREC_MIXED)
         vcycle<float, double2>(g, vj, sV, g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act);
+    else if (g->opt.precision == HELM_PREC_MIXED_C64)
+        vcycle<float, float2>(g, g->V.as<float2>() + (size_t)j * c64_stride(N), (size_t)(m + 1) * c64_stride(N),
+                              g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act);
     else
         vcycle<float, float4>(g, g->V.as<float4>() + (size_t)j * N, sV,
                               g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act);
@@ -243,6 +250,22 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
     const bool left = left_side(g);
     if (g->opt.precond != HELM_PRECOND_NONE && !(left && g->opt.side == HELM_SIDE_LEFT))
         apply_precond_j(g, j, nrhs, act);
+    if (g->opt.precision == HELM_PREC_MIXED_C64) {
+        // w = H z_j (double-single, in the residual buffer), orthogonalised
+        // against the complex64 basis, then v_{j+1} = w / ||w|| rounded
+        float2 *Vc = g->V.as<float2>();
+        float4 *wd = g->rbuf.as<float4>();
+        const size_t Nv = c64_stride(N), sVc = (size_t)nv * Nv;
+        const LevelView<double> Lv = level_view<double>(g, 0);
+        launch_apply_H_ds(Lv, g->hdiag.as<float4>(), g->Z.as<float2>() + (size_t)j * N, (size_t)m * N, wd, N,
+                          nrhs, act, st);
+        launch_multidot_sb(Vc, sVc, Nv, j + 1, wd, N, N, hb, 2 * nv, nrhs, act, ks, st);
+        launch_multiaxpy_sb(Vc, sVc, Nv, j + 1, hb, 2 * nv, wd, N, N, nrm, nrhs, act, ks, st);
+        launch_scale_c64(wd, N, nrm, Vc + (size_t)(j + 1) * Nv, sVc, N, nrhs, act, st);
+        launch_givens_scale<double2>(cycle_state(g), j, hb, 2 * nv, 0, nrm, nrhs, tol, g->opt.max_iters, g->hflag,
+                                     (double2 *)nullptr, sV, N, st);
+        return;
+    }
     double2 *w = V + (size_t)(j + 1) * N;
     const int nvec = j + 1;
     const int mode = g->opt.reorth;      // 0: CGS once, 1: CGS twice, 2: twice only when needed
@@ -412,7 +435,7 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
     double *nrm = g->nrm.as<double>();
     const CycleState S = cycle_state(g);
     const LevelView<double> L0 = level_view<double>(g, 0);
-    if (g->opt.precision == HELM_PREC_MIXED_DS && !g->hdiag_ok) {
+    if ((g->opt.precision == HELM_PREC_MIXED_DS || g->opt.precision == HELM_PREC_MIXED_C64) && !g->hdiag_ok) {
         launch_make_hdiag_ds(level_view<double>(g, 0), shift_H(g), g->hdiag.as<float4>(), g->st);
         g->hdiag_ok = true;
     }
@@ -430,9 +453,10 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         cudaMemsetAsync(u, 0, (size_t)nrhs * N * sizeof(double2), st);
     // r_0: into basis slot 0 (complex128 basis) or the residual buffer (double-single basis)
     const bool ds = g->opt.precision == HELM_PREC_MIXED_DS;
+    const bool c64 = g->opt.precision == HELM_PREC_MIXED_C64;
     const bool left = left_side(g);
-    double2 *rvec = ds ? g->rbuf.as<double2>() : V;
-    const size_t sr = ds ? N : sV;
+    double2 *rvec = (ds || c64) ? g->rbuf.as<double2>() : V;
+    const size_t sr = (ds || c64) ? N : sV;
     if (left) {
         // preconditioned system: ||M^-1 f|| is the reference of every test;
         // M^-1 f is r_0 from x0 = 0
@@ -472,6 +496,9 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         // v_0 = r / ||r|| (||r||^2 in nrm)
         if (ds)
             launch_scale_ds<double2>(rvec, sr, nrm, g->V.as<float4>(), sV, N, nrhs, S.act_cy, st);
+        else if (c64)
+            launch_scale<float2>(rvec, sr, nrm, g->V.as<float2>(), (size_t)(m + 1) * c64_stride(N), N, nrhs,
+                                 S.act_cy, st);
         else
             launch_scale<double2>(V, sV, nrm, V, sV, N, nrhs, S.act_cy, st);
         for (int j = 0; j < m; ++j) {
@@ -505,7 +532,7 @@ helm_status solve_device(helm_grid *g, int nrhs, const double2 *f, double tol, d
         else if (g->opt.precision == HELM_PREC_F64)
             launch_update<double2>(g->Z.as<double2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u,
                                    N, N, nrhs, S.act_cy, st, S.k);
-        else if (ds)
+        else if (ds || c64)
             launch_update_zds(g->Z.as<float2>(), (size_t)m * N, m, g->yv.as<double2>(), m, u, N, N,
                               nrhs, S.act_cy, st, S.k);
         else
@@ -807,8 +834,21 @@ extern "C" helm_status helm_time_kernel(helm_grid *g, const char *kernel, int j,
     double b = 0.0, fl = 0.0;
     auto one = [&]() -> bool {
         const bool dsb = g->opt.precision == HELM_PREC_MIXED_DS;
+        const bool c64b = g->opt.precision == HELM_PREC_MIXED_C64;
         float4 *Vd = g->V.as<float4>();
-        if (name == "multidot" && dsb) {
+        if (c64b && (name == "multidot" || name == "multiaxpy")) {
+            float2 *Vc = g->V.as<float2>();
+            float4 *wd = g->rbuf.as<float4>();
+            const size_t Nv = c64_stride(N);
+            if (name == "multidot") {
+                launch_multidot_sb(Vc, nv * Nv, Nv, nvec, wd, N, N, hb, 2 * nv, nrhs, nullptr, ks, g->st);
+                b = (nvec * 8.0 + 16.0) * N * nrhs;
+            } else {
+                launch_multiaxpy_sb(Vc, nv * Nv, Nv, nvec, hb, 2 * nv, wd, N, N, nrm, nrhs, nullptr, ks, g->st);
+                b = (nvec * 8.0 + 32.0) * N * nrhs;
+            }
+            fl = 0.0;
+        } else if (name == "multidot" && dsb) {
             launch_multidot_ds(Vd, sV, nvec, Vd + (size_t)(j + 1) * N, sV, N, hb, 2 * nv, nrhs, nullptr, ks,
                                g->st);
             b = (nvec + 1.0) * N * 16.0 * nrhs;

@@ -345,6 +345,22 @@ void launch_update_ds(const float4 *Z, size_t sZ, int nvec, const double2 *y, si
                       double2 *x, size_t sx, size_t N, int nrhs, const int *active, cudaStream_t st,
                       const int *kcount = nullptr);
 
+// ---- complex64 basis (precision HELM_PREC_MIXED_C64): v_i stored as float2 at
+// a per-vector stride Nv = c64_stride(N) (N rounded up to even, so that every
+// vector starts on a 16-byte boundary), the vector being orthogonalised as
+// double-single float4 (stride sw), coefficients complex128; partial sums as
+// the double-single kernels (ds_partial_per_rhs)
+inline size_t c64_stride(size_t N) { return (N + 1) & ~(size_t)1; }
+void launch_multidot_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const float4 *w, size_t sw, size_t N,
+                        double2 *out, size_t out_stride, int nrhs, const int *active, KrylovScratch &ks,
+                        cudaStream_t st);
+void launch_multiaxpy_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const double2 *c, size_t c_stride,
+                         float4 *w, size_t sw, size_t N, double *norm2, int nrhs, const int *active,
+                         KrylovScratch &ks, cudaStream_t st);
+// v = w / sqrt(norm2[k]) rounded to complex64
+void launch_scale_c64(const float4 *w, size_t sw, const double *norm2, float2 *v, size_t sv, size_t N, int nrhs,
+                      const int *active, cudaStream_t st);
+
 // diagonal of H on the fine grid as double-single pairs, and w = H z in
 // double-single arithmetic (z complex64, w double-single)
 void launch_make_hdiag_ds(const LevelView<double> &L, OpShift<double> s, float4 *hd, cudaStream_t st);

@@ -405,6 +405,237 @@ k_multiaxpy_ds(const float4 *__restrict__ V, size_t sV, int nvec, const double2 
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- complex64 basis
+// The same streamed multi-dot and multi-axpy for a basis stored in complex64
+// (precision HELM_PREC_MIXED_C64): the vector w being orthogonalised is still
+// double-single, the basis tiles are float2 and half the bytes. Each basis
+// vector starts at a multiple of Nv elements, Nv = N rounded up to even, so
+// every bulk copy starts on a 16-byte boundary and moves a multiple of 16
+// bytes (a ragged last tile copies one padding element, which no consumer
+// reads).
+struct DotSmemSB {
+    float4 w[kDotStages][kDotTile];
+    float2 v[kDotStages][kGroup][kDotTile];
+    uint64_t full[kDotStages], empty[kDotStages];
+    int abort;
+};
+
+// as k_multidot_ds; the products and each thread's sums over its nodes are
+// plain FP32 against the high part of w (the coefficients only set how
+// orthogonal the new vector comes out: the update below subtracts the same h
+// that enter the Hessenberg, in double-single), the warp, block and chunk
+// sums double-single and FP64
+__global__ void __launch_bounds__(kPipeThreads, kDotBlocksPerSM)
+k_multidot_sb(const float2 *__restrict__ V, size_t sV, size_t Nv, int nvec, const float4 *__restrict__ w,
+              size_t sw, size_t N, double2 *__restrict__ partial, int nvec_max, int nrhs,
+              const int *__restrict__ active) {
+    extern __shared__ __align__(128) unsigned char pipe_raw[];
+    DotSmemSB &S = *reinterpret_cast<DotSmemSB *>(pipe_raw);
+    ring_init(S.full, S.empty, S.abort);
+    const int ntiles = ceil_div(N, kDotTile), nch = ceil_div(ntiles, kDotTpi);
+    const int items = nrhs * nch;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned k = 0;
+    if (warp == kConsWarps) {
+        if (lane == 0) {
+            unsigned issued = 0;
+            for (int it = blockIdx.x; it < items; it += gridDim.x) {
+                const int r = it / nch, c = it % nch;
+                if (active && !active[r]) continue;
+                const int t0 = c * kDotTpi, t1 = min(t0 + kDotTpi, ntiles);
+                const float2 *Vr = V + r * sV;
+                const float4 *wr = w + r * sw;
+                for (int i0 = 0; i0 < nvec; i0 += kGroup) {
+                    const int nq = min(kGroup, nvec - i0);
+                    for (int tl = t0; tl < t1; ++tl, ++k) {
+                        const size_t p0 = (size_t)tl * kDotTile;
+                        const unsigned nodes = (unsigned)min((size_t)kDotTile, N - p0);
+                        const unsigned bw = nodes * 16u, bv = ((nodes + 1u) & ~1u) * 8u;
+                        const int s = (int)(k % kDotStages);
+                        if (!pipe::mbar_wait(&S.empty[s], ((k / kDotStages) & 1u) ^ 1u, &S.abort) ||
+                            aborted(S.abort))
+                            continue;
+                        pipe::mbar_arrive_expect_tx(&S.full[s], bw + bv * nq);
+                        pipe::bulk_load(&S.w[s][0], wr + p0, bw, &S.full[s]);
+                        for (int q = 0; q < nq; ++q)
+                            pipe::bulk_load(&S.v[s][q][0], Vr + (size_t)(i0 + q) * Nv + p0, bv, &S.full[s]);
+                        issued = k + 1;
+                    }
+                }
+            }
+            ring_drain(S.full, issued);
+        }
+        __syncwarp();
+        __syncthreads();
+        return;
+    }
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 zero2 = make_float2(0.f, 0.f);
+    const int t = threadIdx.x;
+    const unsigned long long wait_ns = g_cons_wait_ns;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int r = it / nch, c = it % nch;
+        if (active && !active[r]) continue;
+        const int t0 = c * kDotTpi, t1 = min(t0 + kDotTpi, ntiles);
+        for (int i0 = 0; i0 < nvec; i0 += kGroup) {
+            const int nq = min(kGroup, nvec - i0);
+            float h[16], l[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) h[q] = l[q] = 0.f;
+            for (int tl = t0; tl < t1; ++tl, ++k) {
+                const int nodes = (int)min((size_t)kDotTile, N - (size_t)tl * kDotTile);
+                const int s = (int)(k % kDotStages);
+                const bool ok = pipe::mbar_wait(&S.full[s], (k / kDotStages) & 1u, &S.abort, wait_ns);
+                const bool in = ok && t < nodes;
+                const float4 x = in ? S.w[s][t] : zero4;
+                float2 v[kGroup];
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) v[q] = (in && q < nq) ? S.v[s][q][t] : zero2;
+                __syncwarp();
+                if (lane == 0) pipe::mbar_arrive(&S.empty[s]);
+#pragma unroll
+                for (int q = 0; q < kGroup; ++q) {
+                    // conj(v) x: re = vr xr + vi xi, im = vr xi - vi xr
+                    h[2 * q] = fmaf(v[q].x, x.x, h[2 * q]);
+                    h[2 * q] = fmaf(v[q].y, x.z, h[2 * q]);
+                    h[2 * q + 1] = fmaf(v[q].x, x.z, h[2 * q + 1]);
+                    h[2 * q + 1] = fmaf(-v[q].y, x.x, h[2 * q + 1]);
+                }
+            }
+            float oh, ol;
+            warp_reduce16_ds(h, l, oh, ol);
+            const int comp = (lane >> 1) & 15;
+            if ((lane & 1) == 0 && (comp >> 1) < nq) {
+                double *dst = reinterpret_cast<double *>(
+                    partial + (((size_t)r * nvec_max + i0 + (comp >> 1)) * nch + c) * kConsWarps + warp);
+                dst[comp & 1] = S.abort ? qnan() : ds_join(oh, ol);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// as k_multiaxpy_ds with complex64 basis tiles (in the same ring slots): w
+// stays double-single, each product of a basis entry with the double-single
+// coefficient is exact as p + e
+__global__ void __launch_bounds__(kPipeThreads, kAxpyBlocksPerSM)
+k_multiaxpy_sb(const float2 *__restrict__ V, size_t sV, size_t Nv, int nvec, const double2 *__restrict__ c,
+               size_t cstride, float4 *__restrict__ w, size_t sw, size_t N, double *__restrict__ partial_d,
+               int nrhs, const int *__restrict__ active) {
+    constexpr int NPT = kAxpyTile / kCons;
+    extern __shared__ __align__(128) unsigned char pipe_raw[];
+    AxpySmem &S = *reinterpret_cast<AxpySmem *>(pipe_raw);
+    float4 *cs = reinterpret_cast<float4 *>(pipe_raw + sizeof(AxpySmem)) + (threadIdx.x >> 5) * nvec;
+    ring_init(S.full, S.empty, S.abort);
+    const int ntiles = ceil_div(N, kAxpyTile);
+    const int items = nrhs * ntiles;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned k = 0;
+    if (warp == kConsWarps) {
+        if (lane == 0) {
+            unsigned issued = 0;
+            for (int it = blockIdx.x; it < items; it += gridDim.x) {
+                const int r = it / ntiles, tl = it % ntiles;
+                if (active && !active[r]) continue;
+                const size_t p0 = (size_t)tl * kAxpyTile;
+                const unsigned nodes = (unsigned)min((size_t)kAxpyTile, N - p0);
+                const float2 *Vr = V + r * sV;
+                const float4 *wr = w + r * sw;
+                for (int i = -1; i < nvec; ++i, ++k) {
+                    const int s = (int)(k % kAxpyStages);
+                    if (!pipe::mbar_wait(&S.empty[s], ((k / kAxpyStages) & 1u) ^ 1u, &S.abort) ||
+                        aborted(S.abort))
+                        continue;
+                    const unsigned bytes = i < 0 ? nodes * 16u : ((nodes + 1u) & ~1u) * 8u;
+                    pipe::mbar_arrive_expect_tx(&S.full[s], bytes);
+                    if (i < 0)
+                        pipe::bulk_load(&S.slot[s][0], wr + p0, bytes, &S.full[s]);
+                    else
+                        pipe::bulk_load(&S.slot[s][0], Vr + (size_t)i * Nv + p0, bytes, &S.full[s]);
+                    issued = k + 1;
+                }
+            }
+            ring_drain(S.full, issued);
+        }
+        __syncwarp();
+        __syncthreads();
+        return;
+    }
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 zero2 = make_float2(0.f, 0.f);
+    const int t = threadIdx.x;
+    const unsigned long long wait_ns = g_cons_wait_ns;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int r = it / ntiles, tl = it % ntiles;
+        if (active && !active[r]) continue;
+        const size_t p0 = (size_t)tl * kAxpyTile;
+        const int nodes = (int)min((size_t)kAxpyTile, N - p0);
+        float4 *wr = w + r * sw;
+        for (int i = lane; i < nvec; i += 32) {
+            const double2 ci = c[r * cstride + i];
+            cs[i] = cvt<float4>(make_double2(-ci.x, -ci.y));   // (re_hi, re_lo, im_hi, im_lo) of -c_i
+        }
+        __syncwarp();
+        float rh[NPT], rl[NPT], ih[NPT], il[NPT];
+        {
+            const int s = (int)(k % kAxpyStages);
+            const bool ok = pipe::mbar_wait(&S.full[s], (k / kAxpyStages) & 1u, &S.abort, wait_ns);
+#pragma unroll
+            for (int m = 0; m < NPT; ++m) {
+                const float4 a = (ok && t + m * kCons < nodes) ? S.slot[s][t + m * kCons] : zero4;
+                rh[m] = a.x;
+                rl[m] = a.y;
+                ih[m] = a.z;
+                il[m] = a.w;
+            }
+            __syncwarp();
+            if (lane == 0) pipe::mbar_arrive(&S.empty[s]);
+            ++k;
+        }
+        for (int i = 0; i < nvec; ++i) {
+            const int s = (int)(k % kAxpyStages);
+            const bool ok = pipe::mbar_wait(&S.full[s], (k / kAxpyStages) & 1u, &S.abort, wait_ns);
+            const float2 *vs = reinterpret_cast<const float2 *>(&S.slot[s][0]);
+            float2 v[NPT];
+#pragma unroll
+            for (int m = 0; m < NPT; ++m) v[m] = (ok && t + m * kCons < nodes) ? vs[t + m * kCons] : zero2;
+            __syncwarp();
+            if (lane == 0) pipe::mbar_arrive(&S.empty[s]);
+            ++k;
+            const float4 mc = cs[i];   // -c_i
+#pragma unroll
+            for (int m = 0; m < NPT; ++m) {
+                // w += v * (-c): re = vr mr - vi mi, im = vr mi + vi mr
+                ds_fma(rh[m], rl[m], v[m].x, 0.f, mc.x, mc.y);
+                ds_fma(rh[m], rl[m], -v[m].y, 0.f, mc.z, mc.w);
+                ds_fma(ih[m], il[m], v[m].x, 0.f, mc.z, mc.w);
+                ds_fma(ih[m], il[m], v[m].y, 0.f, mc.x, mc.y);
+            }
+        }
+        float nh = 0.f, nl = 0.f;
+#pragma unroll
+        for (int m = 0; m < NPT; ++m) {
+            float th = rh[m] + rl[m];
+            rl[m] = rl[m] - (th - rh[m]);
+            rh[m] = th;
+            th = ih[m] + il[m];
+            il[m] = il[m] - (th - ih[m]);
+            ih[m] = th;
+            if (t + m * kCons < nodes) {
+                wr[p0 + t + m * kCons] = make_float4(rh[m], rl[m], ih[m], il[m]);
+                ds_fma(nh, nl, rh[m], rl[m], rh[m], rl[m]);
+                ds_fma(nh, nl, ih[m], il[m], ih[m], il[m]);
+            }
+        }
+        if (partial_d) {
+            const double v = warp_sum(ds_join(nh, nl));
+            if (lane == 0) partial_d[((size_t)r * ntiles + tl) * kConsWarps + warp] = S.abort ? qnan() : v;
+        }
+        __syncwarp();   // this warp's cs is rewritten by the next item
+    }
+    __syncthreads();
+}
+
 // norm2[r] = sum of the n partials of r (fixed order, as k_dot_finalize)
 __global__ void __launch_bounds__(256)
 k_norm_finalize(const double *__restrict__ partial_d, int n, double *__restrict__ norm2,
@@ -569,6 +800,9 @@ void set_pipe_attrs() {
         cudaFuncSetAttribute(k_multidot_ds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DotSmem));
         cudaFuncSetAttribute(k_multiaxpy_ds, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(AxpySmem) + kConsWarps * kMaxVec * sizeof(float4)));
+        cudaFuncSetAttribute(k_multidot_sb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DotSmemSB));
+        cudaFuncSetAttribute(k_multiaxpy_sb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(AxpySmem) + kConsWarps * kMaxVec * sizeof(float4)));
         return 1;
     }();
     (void)once;
@@ -660,5 +894,38 @@ template void launch_scale_ds<double2>(const double2 *, size_t, const double *, 
                                        size_t, int, const int *, cudaStream_t);
 template void launch_scale_ds<float4>(const float4 *, size_t, const double *, float4 *, size_t,
                                       size_t, int, const int *, cudaStream_t);
+
+void launch_multidot_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const float4 *w, size_t sw, size_t N,
+                        double2 *out, size_t out_stride, int nrhs, const int *active, KrylovScratch &ks,
+                        cudaStream_t st) {
+    set_pipe_attrs();
+    const int nch = ceil_div(ceil_div(N, kDotTile), kDotTpi);
+    const int nb = pipe_grid(nrhs * nch, kDotBlocksPerSM);
+    prof_begin(st);
+    k_multidot_sb<<<nb, kPipeThreads, sizeof(DotSmemSB), st>>>(V, sV, Nv, nvec, w, sw, N, ks.partial, ks.nvec_max,
+                                                              nrhs, active);
+    k_dot_finalize<<<dim3(nvec, nrhs), 256, 0, st>>>(ks.partial, ks.nvec_max, nch * kConsWarps, out, out_stride,
+                                                     active);
+    count_launch(2);
+    if (prof_on()) prof_end("multidot_c64", st, (nvec * 8.0 + 16.0) * N * nrhs, 0.0);
+}
+
+void launch_multiaxpy_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const double2 *c, size_t c_stride,
+                         float4 *w, size_t sw, size_t N, double *norm2, int nrhs, const int *active,
+                         KrylovScratch &ks, cudaStream_t st) {
+    set_pipe_attrs();
+    const int ntiles = ceil_div(N, kAxpyTile);
+    const int nb = pipe_grid(nrhs * ntiles, kAxpyBlocksPerSM);
+    double *pd = norm2 ? (double *)ks.partial : nullptr;
+    prof_begin(st);
+    k_multiaxpy_sb<<<nb, kPipeThreads, sizeof(AxpySmem) + kConsWarps * nvec * sizeof(float4), st>>>(
+        V, sV, Nv, nvec, c, c_stride, w, sw, N, pd, nrhs, active);
+    count_launch();
+    if (norm2) {
+        k_norm_finalize<<<nrhs, 256, 0, st>>>(pd, ntiles * kConsWarps, norm2, active);
+        count_launch();
+    }
+    if (prof_on()) prof_end("multiaxpy_c64", st, (nvec * 8.0 + 32.0) * N * nrhs, 0.0);
+}
 
 }  // namespace helm

@@ -111,7 +111,7 @@ size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o)
         add(ldh * S * 16.0 + nv * (S + 1) * 16.0 + 2.0 * nv * S * 16.0);
         add(S * N * 16.0);                               // complex128 residual block
     } else {
-        add(nrhs * (m + 1.0) * N * 16.0);                // basis V
+        add(nrhs * (m + 1.0) * N * (o.precision == HELM_PREC_MIXED_C64 ? 8.0 : 16.0));   // basis V
         if (zsz > 0.0) add(nrhs * (double)m * N * zsz);  // preconditioned vectors Z
     }
     for (int l = 0; l < nlev; ++l) {                     // per level of the hierarchy
@@ -136,7 +136,7 @@ size_t solve_footprint(int dim, const int n[3], int nrhs, const helm_options &o)
     }
     add(nrhs * N * 16.0);                                // staging of host f
     add(nrhs * N * 16.0);                                // staging of host u
-    if (o.precision == HELM_PREC_MIXED_DS) {
+    if (o.precision == HELM_PREC_MIXED_DS || o.precision == HELM_PREC_MIXED_C64) {
         add(nrhs * N * 16.0);                            // complex128 residuals
         add(N * 16.0);                                   // diagonal of H, double-single
     } else if (o.side != HELM_SIDE_RIGHT && o.precond != HELM_PRECOND_NONE) {

@@ -73,7 +73,7 @@ helm_status tune_tiles(helm_grid *g, int nrhs, helm_tune_report *rep) {
     const CB0 *b0 = g->V.as<CB0>();
     cudaStream_t st = g->st;
     // defined contents for the timed kernels (values do not affect timing)
-    cudaMemsetAsync(g->V.p, 0, (size_t)nrhs * sV * sizeof(double2), st);
+    cudaMemsetAsync(g->V.p, 0, (size_t)nrhs * sV * sizeof(CB0), st);
     for (int l = 0; l < L; ++l) {
         const size_t b = g->lv[l].N * sizeof(C) * (size_t)nrhs;
         cudaMemsetAsync(g->lv[l].u.p, 0, b, st);
@@ -200,6 +200,7 @@ helm_status helm_autotune(helm_grid *g, int nrhs, const helm_c128 *f, double tol
     if ((flags & HELM_TUNE_TILES) && g->dim >= 2 && g->lv.size() > 1 && !g->has_rho) {
         if (g->opt.precision == HELM_PREC_F64) s = tune_tiles<double, double2>(g, nrhs, rep);
         else if (g->opt.precision == HELM_PREC_MIXED) s = tune_tiles<float, double2>(g, nrhs, rep);
+        else if (g->opt.precision == HELM_PREC_MIXED_C64) s = tune_tiles<float, float2>(g, nrhs, rep);
         else s = tune_tiles<float, float4>(g, nrhs, rep);
         if (s) return s;
     }

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "HELM_OK", 1: "HELM_ERR_ARG", 2: "HELM_ERR_NOMEM", 3: "HELM_E
                 4: "HELM_ERR_NOT_CONVERGED", 5: "HELM_ERR_BREAKDOWN", 6: "HELM_ERR_NONFINITE",
                 7: "HELM_ERR_STATE", 8: "HELM_ERR_UNSUPPORTED"}
 PRECOND = {"mg": 0, "exact": 1, "none": 2}
-PRECISION = {"f64": 0, "mixed": 1, "mixed_ds": 2}
+PRECISION = {"f64": 0, "mixed": 1, "mixed_ds": 2, "mixed_c64": 3}
 SIDE = {"right": 0, "left": 1, "split": 2}
 
 EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "helm_set_stream",

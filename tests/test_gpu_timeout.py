@@ -31,10 +31,13 @@ def helm():
     return h
 
 
+@pytest.mark.parametrize("precision", ["mixed_ds", "mixed_c64"])
 @pytest.mark.parametrize("graphs", [True, False])
-def test_wait_timeout_reports_breakdown_and_grid_stays_usable(helm, graphs):
+def test_wait_timeout_reports_breakdown_and_grid_stays_usable(helm, graphs, precision):
+    """The double-single basis and the complex64 basis stream their tiles
+    through the same bounded-wait ring."""
     w = workload("2d_smooth_small")
-    g = helm.Grid(w.n, w.h, restart=30, precision="mixed_ds", graphs=graphs)
+    g = helm.Grid(w.n, w.h, restart=30, precision=precision, graphs=graphs)
     g.set_model(torch.from_numpy(w.slowness().ravel().copy()).to(DEV), w.omega(), w.alpha)
     g.set_shift(*w.beta)
     fd = torch.from_numpy(w.rhs().ravel().copy()).to(DEV)
