@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default="plain", choices=["plain", "batched", "3d", "block-tc", "block-ls"],
+    ap.add_argument("--profile", default="plain",
+                    choices=["plain", "batched", "3d", "block-tc", "block-ls", "batched-c64", "batched-ds"],
                     help="region bracketed by cudaProfilerStart/Stop for ncu --profile-from-start "
                          "off: the plain timed solves, or one extra (untimed) solve of the "
                          "64-source batch with the complex64 basis; block-tc / block-ls: only "
@@ -390,6 +391,32 @@ def profile_block(helm, dev, which):
     g.close()
 
 
+def profile_batched(helm, dev, precision):
+    """--profile batched-c64 / batched-ds: the 64-source 401x201 batch alone
+    (tiles tuned, graphs captured by a warm solve), one solve bracketed by
+    cudaProfilerStart/Stop for ncu --profile-from-start off."""
+    import torch
+    from workloads import point_sources, workload
+    w = workload("2d_smooth")
+    m = torch.from_numpy(w.slowness().ravel().copy()).to(dev)
+    xs = [int(math.floor((k + 0.5) * (w.n[0] - 1) / BATCH_SOURCES + 0.5)) for k in range(BATCH_SOURCES)]
+    F = torch.from_numpy(np.stack([point_sources(w.n, w.h, [(x, 2)]).ravel() for x in xs])).to(dev)
+    U = torch.empty_like(F)
+    g = helm.Grid(w.n, w.h, restart=w.restart, precond="mg", precision=precision)
+    g.set_model(m, w.omega(), w.alpha)
+    g.set_shift(*w.beta)
+    g.autotune(BATCH_SOURCES, None, w.tol, tiles=True, smoother=False)
+    g.solve_batch(BATCH_SOURCES, F, w.tol, U)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    _, its, rr = g.solve_batch(BATCH_SOURCES, F, w.tol, U)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"profile": precision, "iterations_max": int(its.max()), "true_rel_residual_max": float(rr.max())}),
+          flush=True)
+    g.close()
+
+
 def main():
     args = parse()
     from paper_1712_08740_gb300.replicas import max_over_ranks, rank_env, whole_job_rate
@@ -414,6 +441,9 @@ def main():
         return
     if args.profile in ("block-tc", "block-ls"):
         profile_block(helm, dev, args.profile)
+        return
+    if args.profile in ("batched-c64", "batched-ds"):
+        profile_batched(helm, dev, "mixed_c64" if args.profile == "batched-c64" else "mixed_ds")
         return
 
     w = workload("2d_smooth")

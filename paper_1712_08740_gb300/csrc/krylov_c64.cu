@@ -27,7 +27,19 @@ k_scale_c64(const float4 *__restrict__ w, size_t sw, const double *__restrict__ 
     }
     __syncthreads();
     const float sh = s_sh.x, sl = s_sh.y;
-    for (size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x; p < N; p += (size_t)gridDim.x * kThreads) {
+    // four nodes per thread and round, all loads issued first
+    const size_t stride = (size_t)gridDim.x * kThreads;
+    size_t p = (size_t)blockIdx.x * kThreads + threadIdx.x;
+    for (; p + 3 * stride < N; p += 4 * stride) {
+        float4 x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = w[p + q * stride];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            v[p + q * stride] = make_float2(fmaf(x[q].x, sh, fmaf(x[q].x, sl, x[q].y * sh)),
+                                            fmaf(x[q].z, sh, fmaf(x[q].z, sl, x[q].w * sh)));
+    }
+    for (; p < N; p += stride) {
         const float4 x = w[p];
         v[p] = make_float2(fmaf(x.x, sh, fmaf(x.x, sl, x.y * sh)), fmaf(x.z, sh, fmaf(x.z, sl, x.w * sh)));
     }
@@ -37,7 +49,8 @@ k_scale_c64(const float4 *__restrict__ w, size_t sw, const double *__restrict__ 
 
 void launch_scale_c64(const float4 *w, size_t sw, const double *norm2, float2 *v, size_t sv, size_t N, int nrhs,
                       const int *active, cudaStream_t st) {
-    const size_t want = (N + kThreads - 1) / kThreads;
+    // about four nodes per thread; a whole number of blocks per SM over the batch
+    const size_t want = (N + 4 * kThreads - 1) / (4 * kThreads);
     const int nb = (int)(want < (size_t)(1 << 16) ? (want ? want : 1) : (1 << 16));
     prof_begin(st);
     k_scale_c64<<<dim3(nb, nrhs), kThreads, 0, st>>>(w, sw, norm2, v, sv, N, active);

@@ -38,6 +38,19 @@ __device__ __forceinline__ void ds_fma(float &h, float &l, float ah, float al, f
     l += err + e;
 }
 
+// acc += a * b with a exact in FP32 and b double-single (acc unnormalised):
+// the product a * b_hi is exact as p + e
+__device__ __forceinline__ void ds_fma1(float &h, float &l, float a, float bh, float bl) {
+    const float p = a * bh;
+    float e = fmaf(a, bh, -p);
+    e = fmaf(a, bl, e);
+    const float s = h + p;
+    const float bb = s - h;
+    const float err = (h - (s - bb)) + (p - bb);
+    h = s;
+    l += err + e;
+}
+
 // (h, l) = a * b for a fresh accumulator: the same bits as ds_fma into (0, 0)
 __device__ __forceinline__ void ds_init(float &h, float &l, float ah, float al, float bh, float bl) {
     const float p = ah * bh;
@@ -413,10 +426,14 @@ k_multiaxpy_ds(const float4 *__restrict__ V, size_t sV, int nvec, const double2 
 // every bulk copy starts on a 16-byte boundary and moves a multiple of 16
 // bytes (a ragged last tile copies one padding element, which no consumer
 // reads).
+// half-size stages, so the ring is deeper than the double-single one (more
+// bytes in flight per block)
+constexpr int kDotStagesSB = 5;
+
 struct DotSmemSB {
-    float4 w[kDotStages][kDotTile];
-    float2 v[kDotStages][kGroup][kDotTile];
-    uint64_t full[kDotStages], empty[kDotStages];
+    float4 w[kDotStagesSB][kDotTile];
+    float2 v[kDotStagesSB][kGroup][kDotTile];
+    uint64_t full[kDotStagesSB], empty[kDotStagesSB];
     int abort;
 };
 
@@ -451,8 +468,8 @@ k_multidot_sb(const float2 *__restrict__ V, size_t sV, size_t Nv, int nvec, cons
                         const size_t p0 = (size_t)tl * kDotTile;
                         const unsigned nodes = (unsigned)min((size_t)kDotTile, N - p0);
                         const unsigned bw = nodes * 16u, bv = ((nodes + 1u) & ~1u) * 8u;
-                        const int s = (int)(k % kDotStages);
-                        if (!pipe::mbar_wait(&S.empty[s], ((k / kDotStages) & 1u) ^ 1u, &S.abort) ||
+                        const int s = (int)(k % kDotStagesSB);
+                        if (!pipe::mbar_wait(&S.empty[s], ((k / kDotStagesSB) & 1u) ^ 1u, &S.abort) ||
                             aborted(S.abort))
                             continue;
                         pipe::mbar_arrive_expect_tx(&S.full[s], bw + bv * nq);
@@ -484,8 +501,8 @@ k_multidot_sb(const float2 *__restrict__ V, size_t sV, size_t Nv, int nvec, cons
             for (int q = 0; q < 16; ++q) h[q] = l[q] = 0.f;
             for (int tl = t0; tl < t1; ++tl, ++k) {
                 const int nodes = (int)min((size_t)kDotTile, N - (size_t)tl * kDotTile);
-                const int s = (int)(k % kDotStages);
-                const bool ok = pipe::mbar_wait(&S.full[s], (k / kDotStages) & 1u, &S.abort, wait_ns);
+                const int s = (int)(k % kDotStagesSB);
+                const bool ok = pipe::mbar_wait(&S.full[s], (k / kDotStagesSB) & 1u, &S.abort, wait_ns);
                 const bool in = ok && t < nodes;
                 const float4 x = in ? S.w[s][t] : zero4;
                 float2 v[kGroup];
@@ -606,10 +623,10 @@ k_multiaxpy_sb(const float2 *__restrict__ V, size_t sV, size_t Nv, int nvec, con
 #pragma unroll
             for (int m = 0; m < NPT; ++m) {
                 // w += v * (-c): re = vr mr - vi mi, im = vr mi + vi mr
-                ds_fma(rh[m], rl[m], v[m].x, 0.f, mc.x, mc.y);
-                ds_fma(rh[m], rl[m], -v[m].y, 0.f, mc.z, mc.w);
-                ds_fma(ih[m], il[m], v[m].x, 0.f, mc.z, mc.w);
-                ds_fma(ih[m], il[m], v[m].y, 0.f, mc.x, mc.y);
+                ds_fma1(rh[m], rl[m], v[m].x, mc.x, mc.y);
+                ds_fma1(rh[m], rl[m], -v[m].y, mc.z, mc.w);
+                ds_fma1(ih[m], il[m], v[m].x, mc.z, mc.w);
+                ds_fma1(ih[m], il[m], v[m].y, mc.x, mc.y);
             }
         }
         float nh = 0.f, nl = 0.f;
@@ -729,18 +746,6 @@ k_update_ds(const float4 *__restrict__ Z, size_t sZ, int nvec, const double2 *__
         }
         x[p] = acc;
     }
-}
-
-// acc += a * b with a exact in FP32 and b double-single (acc unnormalised)
-__device__ __forceinline__ void ds_fma1(float &h, float &l, float a, float bh, float bl) {
-    const float p = a * bh;
-    float e = fmaf(a, bh, -p);
-    e = fmaf(a, bl, e);
-    const float s = h + p;
-    const float bb = s - h;
-    const float err = (h - (s - bb)) + (p - bb);
-    h = s;
-    l += err + e;
 }
 
 // x += sum_i Z_i y_i for complex64 z_i (exact in FP32): the sum is formed in
