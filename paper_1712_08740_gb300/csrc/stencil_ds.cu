@@ -214,7 +214,9 @@ void launch_apply_H_ds(const LevelView<double> &L, const float4 *hd, const float
     // blocks of whole warps spanning a row's node pairs: 401 nodes -> 201 pairs -> 224 threads
     const int wpr = ((L.nx + 1) / 2 + 31) / 32, bpr = (wpr + 15) / 16;
     const int bx = 32 * ((wpr + bpr - 1) / bpr);
-    const dim3 g(bpr, rows < 65535 ? rows : 65535, nb);
+    // a block takes four rows (its y-stride loop); fewer, longer-lived blocks
+    const int ry = (rows + 3) / 4;
+    const dim3 g(bpr, ry < 65535 ? ry : 65535, nb);
     prof_begin(st);
     if (L.dim == 1) k_apply_H_ds<1><<<g, bx, 0, st>>>(L, hd, ihh, ihl, z, sz, w, sw, active);
     else if (L.dim == 2) k_apply_H_ds<2><<<g, bx, 0, st>>>(L, hd, ihh, ihl, z, sz, w, sw, active);
