@@ -49,7 +49,7 @@ def solve_alone(helm, r, precision, tol):
     return U
 
 
-@pytest.mark.parametrize("precision", ["mixed", "f64"])
+@pytest.mark.parametrize("precision", ["mixed", "f64", "mixed_c64"])
 def test_results_same_alone_and_in_the_mix(helm, precision):
     reqs = make_requests(8)
     tol = 1e-9
@@ -68,7 +68,7 @@ def test_results_same_alone_and_in_the_mix(helm, precision):
     assert np.linalg.norm(alone[1][0] - u_lu.ravel()) <= 1e-6 * np.linalg.norm(u_lu)
 
 
-@pytest.mark.parametrize("precision,nrhs", [("f64", 1), ("mixed", 4), ("mixed_ds", 8)])
+@pytest.mark.parametrize("precision,nrhs", [("f64", 1), ("mixed", 4), ("mixed_ds", 8), ("mixed_c64", 8)])
 def test_footprint_bounds_the_memory_a_solve_holds(helm, precision, nrhs):
     """Admission relies on helm_solve_footprint: it must not be below the
     device memory a grid actually holds after a batched solve (model,
