@@ -79,7 +79,7 @@ def test_footprint_bounds_the_memory_a_solve_holds(helm, precision, nrhs):
     m = (1.0 / smooth_random(n, h, seed=11)).ravel()
     F = np.stack([point_sources(n, h, [(20 + 25 * k, 2)]).ravel() for k in range(nrhs)])
     o = helm.helm_default_options()
-    o.precision = {"f64": 0, "mixed": 1, "mixed_ds": 2}[precision]
+    o.precision = helm.PRECISION[precision]
     fp = helm.helm_solve_footprint(2, n, nrhs, o)
     Fd = torch.from_numpy(F).cuda()
     Ud = torch.empty_like(Fd)
