@@ -557,13 +557,13 @@ __device__ __forceinline__ void warp_refl(const double2 (&v)[3], double tau, dou
 
 // bounded wait until flag == epoch (another block publishes it)
 __device__ __forceinline__ bool wait_flag(const int *flag, int epoch) {
-    const unsigned long long t0 = pipe::global_ns();
+    pipe::WaitClock clk;
     for (unsigned n = 0;; ++n) {
         if (*(volatile const int *)flag == epoch) {
             __threadfence();
             return true;
         }
-        if ((n & 15) == 15 && (pipe::global_ns() - t0 > kLsWaitNs || n > (1u << 28))) return false;
+        if ((n & 15) == 15 && (clk.over(kLsWaitNs) || n > (1u << 28))) return false;
         __nanosleep(64);
     }
 }

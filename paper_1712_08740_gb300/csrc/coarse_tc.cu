@@ -143,6 +143,14 @@ k_coarse_tc(const float *__restrict__ tiles, TcGeom G, const float2 *__restrict_
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // every warp reads the abort word (and later the barriers and the TMEM
+    // address) that thread 0 and warp 0 have just written: without this
+    // barrier a warp could read the word before it is cleared, i.e. whatever
+    // an earlier block, of any kernel, left at that shared-memory address,
+    // and skip staging its sources' slice
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
     static_assert(kN == 8 * (kThreads / 32) && kK == 32, "one source per four lanes, eight groups of four columns");
     const int src_j = jt * kN + 8 * warp + (lane >> 2);
     const bool use_j = src_j < nb && (!active || active[src_j]);

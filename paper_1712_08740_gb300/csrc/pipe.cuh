@@ -8,7 +8,7 @@
 // the slot. The copy engine keeps many tiles in flight while the consumers
 // compute, without a register per byte in flight.
 //
-// Every wait is bounded in time (globaltimer). A wait that runs out sets the
+// Every wait is bounded in time (globaltimer, through WaitClock). A wait that runs out sets the
 // block's abort word; from then on no wait of the block blocks again, the
 // kernel walks the rest of its control flow (every named barrier included)
 // without data and reports NaN, and the producer waits, again bounded, for
@@ -80,6 +80,26 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// Time spent in one wait, from %globaltimer read at each check. Only forward
+// steps below kStepCapNs count, so a reading behind the previous one (which a
+// plain unsigned now - start would turn into an instant timeout) or a leap
+// longer than a check interval can take adds nothing; the iteration caps of
+// the waits bound them whatever the timer does.
+constexpr unsigned long long kStepCapNs = 50ull * 1000 * 1000;   // 50 ms between two checks
+
+struct WaitClock {
+    unsigned long long prev, spent;
+    __device__ __forceinline__ WaitClock() : prev(global_ns()), spent(0) {}
+    // true once the counted time exceeds limit_ns
+    __device__ __forceinline__ bool over(unsigned long long limit_ns) {
+        const unsigned long long now = global_ns();
+        const long long d = (long long)(now - prev);
+        prev = now;
+        if (d > 0 && (unsigned long long)d < kStepCapNs) spent += (unsigned long long)d;
+        return spent > limit_ns;
+    }
+};
+
 // Wait until the phase of parity `parity` of barrier b has completed. Returns
 // false at once when *abort is set, and false (setting *abort) after limit_ns.
 // A limit below 1 us gives up at the first check that finds the phase
@@ -93,12 +113,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, volatile
         return false;
     }
     if (mbar_try_wait(b, parity)) return true;
-    const unsigned long long t0 = global_ns();
+    WaitClock clk;
     for (unsigned n = 1;; ++n) {
         if (mbar_try_wait(b, parity)) return true;
         if ((n & 31) == 0) {
             if (*abort) return false;
-            if (global_ns() - t0 > limit_ns || n > (1u << 30)) {
+            if (clk.over(limit_ns) || n > (1u << 30)) {
                 *abort = 1;
                 return false;
             }
@@ -108,10 +128,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, volatile
 
 // The same wait without the abort short-cut (teardown of copies in flight).
 __device__ __forceinline__ bool mbar_wait_drain(uint64_t *b, unsigned parity) {
-    const unsigned long long t0 = global_ns();
+    WaitClock clk;
     for (unsigned n = 0;; ++n) {
         if (mbar_try_wait(b, parity)) return true;
-        if ((n & 31) == 31 && (global_ns() - t0 > kWaitNs || n > (1u << 30))) return false;
+        if ((n & 31) == 31 && (clk.over(kWaitNs) || n > (1u << 30))) return false;
     }
 }
 
