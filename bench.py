@@ -241,7 +241,7 @@ def tune_summary(helm, dim, rep):
     return out
 
 
-def serving_run(helm, n_req=200, rate_hz=200.0, seed=0, workers=4):
+def serving_run(helm, n_req=200, rate_hz=200.0, seed=0, workers=4, coalesce=0, **opts):
     """Poisson stream of 2D solves through the serving loop (helm_server_*).
 
     Grids drawn from {257x129, 513x257, 1025x513, 1601x801}, h = 10 m, f = 15 Hz
@@ -258,7 +258,8 @@ def serving_run(helm, n_req=200, rate_hz=200.0, seed=0, workers=4):
     for r in reqs:
         F = np.stack([point_sources(r["n"], r["h"], [s]).ravel() for s in r["sources"]])
         payload.append((r, pool[(r["n"], r["model_seed"] % 4)].ravel(), F))
-    srv = helm.Server(workers=workers, memory_budget=96 << 30, precision="mixed_c64", restart=30)
+    opts = {"precision": "mixed_c64", "restart": 30, **opts}
+    srv = helm.Server(workers=workers, memory_budget=96 << 30, coalesce=coalesce, **opts)
     t0 = srv.clock()
     ids = []
     for r, m, F in payload:
@@ -284,7 +285,9 @@ def serving_run(helm, n_req=200, rate_hz=200.0, seed=0, workers=4):
                      # one worker's rate on this class (solves per second of service)
                      "solves_per_worker_s": v["solves"] / sum(v["service_s"])}
                  for k, v in sorted(classes.items())}
+    batches = len({round(x[1].t_admit, 9) for x in res})
     return {"requests": n_req, "solves": int(nsol), "arrival_rate_hz": rate_hz, "workers": workers,
+            "coalesce": coalesce, "batches": batches,
             "per_grid_class": per_class,
             "all_converged": bool(ok),
             "true_rel_residual_max": float(max(x[1].true_rel_residual_max for x in res)),
@@ -771,6 +774,9 @@ def main():
     del F2, U2
 
     serving = serving_run(helm)
+    # the same stream with coalescing: queued requests on the same grid, medium and
+    # frequency are merged into lock-step batches of up to 64 sources
+    serving["coalesced"] = serving_run(helm, coalesce=64)
 
     # ---- the 1D well case and the 3D case, each timed as one solve call
     extra = {}

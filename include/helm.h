@@ -392,7 +392,9 @@ const char *helm_last_error(void);
  * in arrival order (FIFO) to `workers` worker threads, each with its own CUDA
  * stream, when the device memory all admitted requests hold fits
  * `memory_budget` (footprints from helm_solve_footprint; idle workers drop
- * their cached grids to make room). Workers keep one grid resident between
+ * their cached grids to make room). With `coalesce` > 1 an admitted request
+ * takes along the queued requests of the same problem (see
+ * helm_server_config). Workers keep one grid resident between
  * requests of the same size. Requests on different workers run concurrently
  * and their kernels overlap on the device; each request's right-hand sides
  * are solved together by helm_solve_batch. The paper has no counterpart: it
@@ -404,6 +406,14 @@ typedef struct {
     size_t memory_budget;    /* device bytes all admitted requests may hold together  */
     helm_options options;    /* solver options for every request                      */
     double beta1, beta2;     /* shift of M (Eq. 6), as in helm_set_shift              */
+    int coalesce;            /* 0 or 1: every request is solved alone. k > 1: when a    */
+                             /* request is admitted, queued requests with the same     */
+                             /* grid, slowness values, omega, alpha and tol join it in */
+                             /* one helm_solve_batch of at most k right-hand sides     */
+                             /* (each keeps its own result: a member of a lock-step    */
+                             /* batch gets the bits of its solve alone). Ignored with  */
+                             /* options.block (a shared block space would change the   */
+                             /* results).                                              */
 } helm_server_config;
 
 typedef struct {

@@ -45,6 +45,7 @@ struct Req {
     std::vector<double2> f;
     double tol = 0.0;
     helm_c128 *u_out = nullptr;
+    uint64_t key = 0;           // hash of grid, slowness, omega, alpha and tol (coalescing)
     size_t footprint = 0;
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
     helm_status status = HELM_OK;
@@ -61,9 +62,22 @@ struct Worker {
     int gdim = 0, gn[3] = {0, 0, 0};
     double gh = 0.0;
     size_t held = 0;            // bytes held by the cached grid (or the running job)
-    std::shared_ptr<Req> job;
+    std::vector<std::shared_ptr<Req>> jobs;   // requests solved together (one lock-step batch)
     bool busy = false;
 };
+
+// FNV-1a over bytes
+uint64_t fnv(uint64_t h, const void *p, size_t n) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+// requests that one lock-step batch may serve together: the same operator and tolerance
+bool same_problem(const Req &a, const Req &b) {
+    return a.key == b.key && a.dim == b.dim && a.n[0] == b.n[0] && a.n[1] == b.n[1] && a.n[2] == b.n[2] &&
+           a.h == b.h && a.omega == b.omega && a.alpha == b.alpha && a.tol == b.tol && a.m == b.m;
+}
 
 bool same_grid(const Worker &w, const Req &r) {
     return w.grid && w.gdim == r.dim && w.gn[0] == r.n[0] && w.gn[1] == r.n[1] && w.gn[2] == r.n[2] &&
@@ -164,6 +178,7 @@ struct helm_server {
     std::map<uint64_t, std::shared_ptr<helm::Req>> reqs;
     std::vector<std::unique_ptr<helm::Worker>> workers;
     size_t budget = 0;
+    int coalesce = 0;           // most right-hand sides of one merged batch (<= 1: off)
     helm_options opt{};
     double beta1 = 1.0, beta2 = 0.5;
     bool stop = false;
@@ -177,7 +192,10 @@ struct helm_server {
 namespace helm {
 namespace {
 
-void run_job(helm_server *S, Worker &w, Req &r) {
+// Solves a group of requests with the same operator as one lock-step batch
+// (a single request directly into its output).
+void run_group(helm_server *S, Worker &w, std::vector<std::shared_ptr<Req>> &grp) {
+    Req &r = *grp[0];
     helm_status s = HELM_OK;
     if (!same_grid(w, r)) {
         if (w.grid) helm_destroy_grid(w.grid);
@@ -194,40 +212,73 @@ void run_job(helm_server *S, Worker &w, Req &r) {
     if (s == HELM_OK) s = helm_set_options(w.grid, &S->opt);
     if (s == HELM_OK) s = helm_set_model(w.grid, r.m.data(), r.omega, r.alpha);
     if (s == HELM_OK) s = helm_set_shift(w.grid, S->beta1, S->beta2);
-    std::vector<int> its(r.nrhs, 0);
-    std::vector<double> rel(r.nrhs, 0.0);
-    if (s == HELM_OK)
-        s = helm_solve_batch(w.grid, r.nrhs, reinterpret_cast<const helm_c128 *>(r.f.data()), r.tol,
-                             r.u_out, its.data(), rel.data());
-    r.status = s;
-    if (s != HELM_OK) r.err = helm_last_error();
-    for (int k = 0; k < r.nrhs; ++k) {
-        r.its_max = std::max(r.its_max, its[k]);
-        r.rel_max = std::max(r.rel_max, rel[k]);
+    const size_t N = r.m.size();
+    int tot = 0;
+    for (auto &q : grp) tot += q->nrhs;
+    std::vector<int> its(tot, 0);
+    std::vector<double> rel(tot, 0.0);
+    if (s == HELM_OK) {
+        if (grp.size() == 1) {
+            s = helm_solve_batch(w.grid, r.nrhs, reinterpret_cast<const helm_c128 *>(r.f.data()), r.tol,
+                                 r.u_out, its.data(), rel.data());
+        } else {
+            // the members' right-hand sides in order, one solve, the solutions back
+            std::vector<double2> f((size_t)tot * N), u((size_t)tot * N);
+            size_t off = 0;
+            for (auto &q : grp) {
+                memcpy(f.data() + off, q->f.data(), q->f.size() * sizeof(double2));
+                off += q->f.size();
+            }
+            s = helm_solve_batch(w.grid, tot, reinterpret_cast<const helm_c128 *>(f.data()), r.tol,
+                                 reinterpret_cast<helm_c128 *>(u.data()), its.data(), rel.data());
+            off = 0;
+            for (auto &q : grp) {
+                const size_t bytes = (size_t)q->nrhs * N * sizeof(double2);
+                if (cudaMemcpy(q->u_out, u.data() + off, bytes, cudaMemcpyDefault) != cudaSuccess && s == HELM_OK) {
+                    cudaGetLastError();
+                    s = fail(HELM_ERR_CUDA, "copy of a merged request's solution");
+                }
+                off += (size_t)q->nrhs * N;
+            }
+        }
+    }
+    const std::string err = s != HELM_OK ? std::string(helm_last_error()) : std::string();
+    int k0 = 0;
+    for (auto &q : grp) {
+        q->status = s;
+        q->err = err;
+        for (int k = 0; k < q->nrhs; ++k) {
+            q->its_max = std::max(q->its_max, its[k0 + k]);
+            q->rel_max = std::max(q->rel_max, rel[k0 + k]);
+        }
+        k0 += q->nrhs;
+        q->f.clear();
+        q->f.shrink_to_fit();
     }
     if (s != HELM_OK && s != HELM_ERR_NOT_CONVERGED && w.grid) {   // do not keep a grid in a bad state
         helm_destroy_grid(w.grid);
         w.grid = nullptr;
     }
-    r.f.clear();
-    r.f.shrink_to_fit();
 }
 
 void worker_loop(helm_server *S, Worker *w) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
-        S->cv_work.wait(lk, [&] { return S->stop || w->job != nullptr; });
-        if (!w->job) break;
-        std::shared_ptr<Req> r = w->job;
+        S->cv_work.wait(lk, [&] { return S->stop || !w->jobs.empty(); });
+        if (w->jobs.empty()) break;
+        std::vector<std::shared_ptr<Req>> grp = w->jobs;
         lk.unlock();
-        run_job(S, *w, *r);
+        run_group(S, *w, grp);
         lk.lock();
-        r->t_done = S->now();
-        r->done = true;
-        w->job = nullptr;
+        const double t = S->now();
+        for (auto &q : grp) {
+            q->t_done = t;
+            q->done = true;
+        }
+        w->jobs.clear();
         w->busy = false;
-        w->held = w->grid ? std::max(w->held, r->footprint) : 0;
+        w->held = w->grid ? std::max(w->held, grp[0]->footprint) : 0;
         S->cv_done.notify_all();
         S->cv_disp.notify_all();
     }
@@ -244,6 +295,21 @@ void dispatch_loop(helm_server *S) {
             continue;
         }
         std::shared_ptr<Req> r = S->queue.front();
+        // the group it leads: queued requests of the same problem, in arrival
+        // order, up to `coalesce` right-hand sides and within the budget
+        std::vector<std::shared_ptr<Req>> grp{r};
+        size_t gfp = r->footprint;
+        if (S->coalesce > 1) {
+            int tot = r->nrhs;
+            for (auto &q : S->queue) {
+                if (q == r || tot + q->nrhs > S->coalesce || !same_problem(*q, *r)) continue;
+                const size_t fp = solve_footprint(r->dim, r->n, tot + q->nrhs, S->opt);
+                if (fp > S->budget) break;
+                grp.push_back(q);
+                tot += q->nrhs;
+                gfp = fp;
+            }
+        }
         // idle worker, preferring one whose resident grid has this size
         Worker *pick = nullptr;
         for (auto &w : S->workers)
@@ -256,7 +322,7 @@ void dispatch_loop(helm_server *S) {
             continue;
         }
         const bool reuse = same_grid(*pick, *r);
-        const size_t need = reuse ? std::max(pick->held, r->footprint) : r->footprint;
+        const size_t need = reuse ? std::max(pick->held, gfp) : gfp;
         size_t others = 0;
         for (auto &w : S->workers)
             if (w.get() != pick) others += w->held;
@@ -304,11 +370,15 @@ void dispatch_loop(helm_server *S) {
             doomed.push_back(pick->grid);
             pick->grid = nullptr;
         }
-        S->queue.pop_front();
-        r->t_admit = S->now();
+        const double ta = S->now();
+        for (auto &q : grp) {
+            S->queue.erase(std::find(S->queue.begin(), S->queue.end(), q));
+            q->t_admit = ta;
+            q->footprint = gfp;
+        }
         pick->held = need;
         pick->busy = true;
-        pick->job = r;
+        pick->jobs = grp;
         S->cv_work.notify_all();
         release();
     }
@@ -332,6 +402,7 @@ helm_status helm_server_create(const helm_server_config *cfg, helm_server **out)
     S->opt = cfg->options;
     S->beta1 = cfg->beta1;
     S->beta2 = cfg->beta2;
+    S->coalesce = cfg->options.block ? 0 : cfg->coalesce;
     S->t0 = clk::now();
     cudaGetDevice(&S->device);
     for (int i = 0; i < cfg->workers; ++i) {
@@ -396,6 +467,13 @@ helm_status helm_server_submit(helm_server *S, const helm_request *q, helm_c128 
     r->tol = q->tol;
     r->u_out = u;
     r->footprint = solve_footprint(r->dim, r->n, r->nrhs, S->opt);
+    uint64_t k = 1469598103934665603ull;
+    k = fnv(k, r->n, sizeof r->n);
+    k = fnv(k, &r->h, sizeof r->h);
+    k = fnv(k, &r->omega, sizeof r->omega);
+    k = fnv(k, &r->alpha, sizeof r->alpha);
+    k = fnv(k, &r->tol, sizeof r->tol);
+    r->key = fnv(k, r->m.data(), r->m.size() * sizeof(double));
     {
         std::lock_guard<std::mutex> lk(S->mu);
         r->id = S->next_id++;

@@ -49,7 +49,8 @@ class helm_options(ctypes.Structure):
 
 class helm_server_config(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int), ("memory_budget", ctypes.c_size_t),
-                ("options", helm_options), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double)]
+                ("options", helm_options), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("coalesce", ctypes.c_int)]
 
 
 class helm_request(ctypes.Structure):
@@ -557,7 +558,7 @@ def helm_server_destroy(s):
 class Server:
     """Request loop on the current CUDA device (see include/helm.h, serving)."""
 
-    def __init__(self, workers=4, memory_budget=64 << 30, beta=(1.0, 0.5), **opts):
+    def __init__(self, workers=4, memory_budget=64 << 30, beta=(1.0, 0.5), coalesce=0, **opts):
         o = helm_default_options()
         for k, v in opts.items():
             if k == "precond":
@@ -566,7 +567,8 @@ class Server:
                 v = PRECISION[v]
             setattr(o, k, int(v) if k != "omega_jacobi" else float(v))
         self.options = o
-        cfg = helm_server_config(int(workers), int(memory_budget), o, float(beta[0]), float(beta[1]))
+        cfg = helm_server_config(int(workers), int(memory_budget), o, float(beta[0]), float(beta[1]),
+                                 int(coalesce))
         self._s = helm_server_create(cfg)
         self._keep = {}
         _live.add(self)

@@ -138,3 +138,36 @@ def test_requests_overlap_when_memory_allows(helm):
     # with three workers some request is admitted before an earlier one is done
     assert any(res[k].t_admit < res[k - 1].t_done for k in range(1, len(res)))
     srv.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed_c64", "f64"])
+def test_coalesced_requests_match_alone(helm, precision):
+    """With coalescing on, queued requests that share grid, medium, frequency,
+    damping and tolerance are solved as one lock-step batch. Each member's
+    result is bit-identical to its solve alone, and members of one batch share
+    their admission and completion times; requests of another medium are not
+    merged with them."""
+    base = make_requests(2, seed=21)
+    reqs = []
+    for k in range(8):                      # two problems, four requests each, interleaved
+        b = dict(base[k % 2])
+        n = b["n"]
+        b["F"] = np.stack([point_sources(n, b["h"], [(3 + 5 * k + 2 * j, 2)]).ravel() for j in range(1 + k % 3)])
+        reqs.append(b)
+    tol = 1e-9
+    alone = [solve_alone(helm, r, precision, tol) for r in reqs]
+    srv = helm.Server(workers=1, memory_budget=16 << 30, precision=precision, coalesce=64)
+    # a first request keeps the single worker busy while the others queue up
+    ids = [srv.submit(r["n"], r["h"], r["m"], r["omega"], r["alpha"], r["F"], tol) for r in reqs]
+    out = [srv.wait(i) for i in ids]
+    srv.close()
+    for k, (st, res, U) in enumerate(out):
+        assert st == 0 and res.true_rel_residual_max <= tol, k
+        assert np.array_equal(U, alone[k]), f"request {k} differs when merged"
+    admits = [res.t_admit for _, res, _ in out]
+    merged = [k for k in range(1, 8) if any(admits[k] == admits[j] for j in range(k))]
+    assert merged, "no request was merged"
+    for k in merged:
+        j = next(j for j in range(k) if admits[j] == admits[k])
+        assert k % 2 == j % 2                  # only requests of the same problem share a batch
+        assert out[k][1].t_done == out[j][1].t_done
