@@ -223,13 +223,16 @@ def oracle_errors(w, F, U_keep, wb, U2_keep, U2b_keep, U2r_keep, plain_keep, ext
 
 def tune_summary(helm, dim, rep):
     """Compact record of an autotuner report: per level the chosen (down, up)
-    tile extents and their speed-up over the default shapes, and the smoother
-    counts with each candidate's time to solution."""
+    tile extents, right-hand sides per block and their speed-up over the
+    default shapes, and the smoother counts with each candidate's time to
+    solution."""
     lv = []
     for k in range(rep["levels"]):
         d, u = rep["down_shape"][k], rep["up_shape"][k]
         lv.append({"down": list(helm.helm_tile_shape(dim, 0, d)[0][:dim]),
                    "up": list(helm.helm_tile_shape(dim, 1, u)[0][:dim]),
+                   "rhs_per_block": [helm.helm_tile_rhs_per_block(dim, 0, d),
+                                     helm.helm_tile_rhs_per_block(dim, 1, u)],
                    "down_us": round(rep["down_us"][k], 2), "up_us": round(rep["up_us"][k], 2),
                    "default_us": [round(rep["down_default_us"][k], 2),
                                   round(rep["up_default_us"][k], 2)]})

@@ -320,7 +320,8 @@ helm_status helm_block_combine(int nv, int s, size_t N, size_t ld, const void *V
  * post-smoothing) are compiled for helm_num_tile_shapes(dim) shapes each
  * (0 for 1D). helm_tile_shape gives a shape's extents and block size: the
  * block's tile of coarse nodes, computed by `threads` threads (one, two, four
- * or 2^d threads per coarse node share its 2^d fine children); for the 3D
+ * or 2^d threads per coarse node share its 2^d fine children) for one or
+ * several right-hand sides (helm_tile_rhs_per_block); for the 3D
  * down kernel that marches along z (the last 3D down shape) the extents are
  * x, y of the tile and the number of coarse planes a block walks, one thread
  * per coarse (x, y) node. The arithmetic per node does not depend on the shape:
@@ -370,9 +371,14 @@ typedef struct {
 
 /* helm_tile_shape: kernel 0 = down, 1 = up; extent[3] (caller-owned) gets the
  * tile's extents in coarse nodes (x, y, z; z = 1 in 2D), *threads the block
- * size. Errors: HELM_ERR_ARG for a dim, kernel or shape out of range. */
+ * size. helm_tile_rhs_per_block: *rb (caller-owned) gets how many right-hand
+ * sides of a batch one block of the shape computes: 1, or 2 or 4 for the 2D
+ * shapes whose threads keep their nodes' positions, boundary tests and D^-1
+ * once for several right-hand sides. Errors (both): HELM_ERR_ARG for a dim,
+ * kernel or shape out of range or a null pointer. */
 int         helm_num_tile_shapes(int dim);
 helm_status helm_tile_shape(int dim, int kernel, int shape, int extent[3], int *threads);
+helm_status helm_tile_rhs_per_block(int dim, int kernel, int shape, int *rb);
 helm_status helm_set_tiles(helm_grid *g, int level, int down_shape, int up_shape);
 helm_status helm_get_tiles(const helm_grid *g, int level, int *down_shape, int *up_shape);
 helm_status helm_autotune(helm_grid *g, int nrhs, const helm_c128 *f, double tol, int flags,

@@ -17,8 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libhelm.so")
-SOURCES = ["setup.cu", "stencil.cu", "stencil_ds.cu", "vfused.cu", "coarse.cu", "coarse_tc.cu", "krylov.cu", "krylov_ds.cu", "krylov_c64.cu", "cycle.cu", "api.cu", "fgmres.cu", "noalloc.cu", "serve.cu", "tune.cu", "block.cu", "recycle.cu"]
-HEADERS = ["helm_internal.cuh", "grid.cuh", "vcycle.cuh", "cycle.cuh", "pipe.cuh", "tc.cuh"]
+SOURCES = ["setup.cu", "stencil.cu", "stencil_ds.cu", "vfused.cu", "vfused_f64.cu", "vfused_mixed.cu", "vfused_c64.cu", "vfused_ds.cu", "coarse.cu", "coarse_tc.cu", "krylov.cu", "krylov_ds.cu", "krylov_c64.cu", "cycle.cu", "api.cu", "fgmres.cu", "noalloc.cu", "serve.cu", "tune.cu", "block.cu", "recycle.cu"]
+HEADERS = ["helm_internal.cuh", "vfused.cuh", "grid.cuh", "vcycle.cuh", "cycle.cuh", "pipe.cuh", "tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]

@@ -219,7 +219,7 @@ void launch_vup(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
 // tile shapes of the fused kernels: count per dimension (down and up lists
 // have equal length) and the extents/threads of one (kernel 0 down, 1 up)
 int num_tile_shapes(int dim);
-bool tile_shape(int dim, int kernel, int shape, int ext[3], int *threads);
+bool tile_shape(int dim, int kernel, int shape, int ext[3], int *threads, int *rb = nullptr);
 // automatic shape for a fine level of `fine` nodes and nb right-hand sides:
 // the first shape in list order whose grid has at least 2 blocks per SM, else
 // the shape with the most blocks (small levels need every SM)

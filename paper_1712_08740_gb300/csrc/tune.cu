@@ -152,6 +152,15 @@ helm_status helm_tile_shape(int dim, int kernel, int shape, int extent[3], int *
     return HELM_OK;
 }
 
+helm_status helm_tile_rhs_per_block(int dim, int kernel, int shape, int *rb) {
+    clear_error();
+    if (!rb) return fail(HELM_ERR_ARG, "null argument");
+    int ext[3], threads;
+    if (!tile_shape(dim, kernel, shape, ext, &threads, rb))
+        return fail(HELM_ERR_ARG, "no tile shape %d for dim %d, kernel %d", shape, dim, kernel);
+    return HELM_OK;
+}
+
 helm_status helm_set_tiles(helm_grid *g, int level, int down_shape, int up_shape) {
     clear_error();
     if (!g) return fail(HELM_ERR_ARG, "null grid");

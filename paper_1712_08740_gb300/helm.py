@@ -35,6 +35,7 @@ EXPORTED = ("helm_default_options", "helm_create_grid", "helm_destroy_grid", "he
             "helm_time_kernel", "helm_true_residual_noalloc", "helm_solve_footprint",
             "helm_server_create", "helm_server_submit", "helm_server_wait", "helm_server_poll",
             "helm_server_clock", "helm_server_destroy", "helm_num_tile_shapes", "helm_tile_shape",
+            "helm_tile_rhs_per_block",
             "helm_set_tiles", "helm_get_tiles", "helm_autotune", "helm_set_wait_limit_ns",
             "helm_set_density", "helm_block_gram", "helm_block_combine")
 
@@ -139,6 +140,7 @@ def _load():
         "helm_server_destroy": (None, [P]),
         "helm_num_tile_shapes": (I, [I]),
         "helm_tile_shape": (I, [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "helm_tile_rhs_per_block": (I, [I, I, I, ctypes.POINTER(I)]),
         "helm_set_tiles": (I, [P, I, I, I]),
         "helm_get_tiles": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "helm_autotune": (I, [P, I, P, D, I, ctypes.POINTER(helm_tune_report)]),
@@ -379,6 +381,13 @@ def helm_tile_shape(dim, kernel, shape):
     ext, nt = (ctypes.c_int * 3)(), ctypes.c_int()
     _check(_lib.helm_tile_shape(int(dim), int(kernel), int(shape), ext, ctypes.byref(nt)))
     return tuple(ext), nt.value
+
+
+def helm_tile_rhs_per_block(dim, kernel, shape):
+    """Right-hand sides one block of a fused-kernel tile shape computes."""
+    rb = ctypes.c_int()
+    _check(_lib.helm_tile_rhs_per_block(int(dim), int(kernel), int(shape), ctypes.byref(rb)))
+    return rb.value
 
 
 def helm_set_tiles(g, level, down_shape, up_shape):

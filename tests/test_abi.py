@@ -83,15 +83,19 @@ def test_tile_shape_queries_without_gpu(lib):
         for kernel in (0, 1):
             for s in range(n):
                 ext, nt = lib.helm_tile_shape(dim, kernel, s)
+                rb = lib.helm_tile_rhs_per_block(dim, kernel, s)
                 assert nt in (64, 128, 256, 512) and all(e >= 1 for e in ext)
+                assert rb in (1, 2, 4) and (dim == 2 or rb == 1)
                 if dim == 2:
                     assert ext[2] == 1
                 if kernel == 1:                      # up tiles start on even fine nodes
                     assert all(e % 2 == 0 for e in ext[:dim])
-                seen.add((kernel, ext, nt))
+                seen.add((kernel, ext, nt, rb))
         assert len(seen) == 2 * n                    # no duplicate shapes
         with pytest.raises(lib.HelmError) as e:
             lib.helm_tile_shape(dim, 0, n)
         assert e.value.status == 1
     with pytest.raises(lib.HelmError):
         lib.helm_tile_shape(2, 2, 0)
+    with pytest.raises(lib.HelmError):
+        lib.helm_tile_rhs_per_block(2, 0, lib.helm_num_tile_shapes(2))
