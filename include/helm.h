@@ -278,8 +278,9 @@ helm_status helm_true_residual(helm_grid *g, const helm_c128 *f, const helm_c128
  *  - nrhs must be 1..64 (the size of that array); larger values return
  *    HELM_ERR_ARG;
  *  - the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture;
+ *    (cudaGetSymbolAddress) with that device current;
+ *  - it must not be called while a stream is being captured into a CUDA
+ *    graph (it copies to host memory and synchronises, see below);
  *  - every call shares the array: calls whose work overlaps on the GPU (for
  *    example on two streams at once) race and give wrong results; calls in
  *    sequence on one stream are safe (each call clears what must start at 0);
