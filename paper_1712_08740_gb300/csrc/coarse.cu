@@ -326,12 +326,13 @@ void gemm_impl(const cplx_t<T> *At, int n, const cplx_t<T> *r, size_t sr, cplx_t
 }  // namespace
 
 void prepare_coarse_kernels() {
-    static bool done = false;
-    if (done) return;
-    const int big = 100 * 1024;
-    cudaFuncSetAttribute(k_coarse_gemm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_coarse_gemm<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    done = true;
+    static const int once = [] {   // thread-safe once per process
+        const int big = 100 * 1024;
+        cudaFuncSetAttribute(k_coarse_gemm<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_coarse_gemm<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        return 1;
+    }();
+    (void)once;
 }
 
 size_t coarse_part_elems(int n, int nb) { return (size_t)nb * gemm_groups(n) * n; }

@@ -52,13 +52,16 @@ int auto_tile_shape(int dim, int kernel, const int fine[3], int nb) {
 }
 
 void prepare_vfused() {
-    static bool done = false;
-    if (done) return;
-    vfused_attr_f64();
-    vfused_attr_mixed();
-    vfused_attr_c64();
-    vfused_attr_ds();
-    done = true;
+    // once per process, also when several threads (server workers) build
+    // their grids at the same time
+    static const int once = [] {
+        vfused_attr_f64();
+        vfused_attr_mixed();
+        vfused_attr_c64();
+        vfused_attr_ds();
+        return 1;
+    }();
+    (void)once;
 }
 
 }  // namespace helm
