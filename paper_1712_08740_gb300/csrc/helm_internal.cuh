@@ -203,8 +203,9 @@ void launch_prolong_add(const LevelView<T> &fine, const LevelView<T> &coarse,
 template <typename C>
 void launch_make_dinv(const LevelView<double> &L, OpShift<double> s, C *dinv, cudaStream_t st);
 
-// Fused V(1,1) level kernels for 2D/3D (vfused.cu). CB: type of the level's
-// right-hand side (complex128 basis vector at level 0 of the mixed form).
+// Fused V(1,1) level kernels for 2D/3D (templates in vfused.cuh, instantiated
+// per type pair in vfused_*.cu). CB: type of the level's right-hand side
+// (complex128 basis vector at level 0 of the mixed form).
 // `finest` only names the launch for the profiler (level 0 is reported apart
 // from the coarser levels).
 template <typename T, typename CB>

@@ -1,8 +1,8 @@
 // Fused V(1,1) multigrid kernels for 2D and 3D levels (Eq. 6 operator M):
-// the templates. vfused.cu holds the shape queries and the level-0 helpers,
-// vfused_*.cu instantiate the kernels for one (arithmetic, right-hand side)
-// type pair each, so the pairs compile in parallel.
-//
+// the templates. vfused.cu holds the shape queries, the inverse diagonal and
+// the one-time set-up; vfused_*.cu instantiate the kernels for one
+// (arithmetic, right-hand side) type pair each, so the pairs compile in
+// parallel.
 //
 // down: from the level's right-hand side b, one kernel computes
 //         u  = wj D^-1 b                          (first Jacobi sweep from 0)
