@@ -115,11 +115,18 @@ constexpr int kPipeThreads = kCons + 32;    // + the producer warp
 
 // multi-dot: a stage is one tile of kDotTile nodes of w and of up to kGroup
 // vectors (9 x 4 KB); the accumulators of a group run over a chunk of
-// kDotTpi consecutive tiles (4 nodes per thread) before the warp reduction.
+// dot_tpi consecutive tiles (one node per thread and tile) before the warp
+// reduction, which costs about as much as the chunk's products.
 constexpr int kDotTile = 256;
 constexpr int kDotStages = 3;
-constexpr int kDotTpi = 4;
 constexpr int kDotBlocksPerSM = 2;
+
+// Tiles per chunk, a function of the tile count alone, so that a batch sums
+// in the same order as one right-hand side. Measured on 64-source 2D batches
+// and a 4-source 3D batch: 8 tiles beat 4 by 1-11 % (the warp reduction runs
+// half as often); 16 beat 8 only on the 3D grid (12.7 M nodes, 4 %) and lost
+// on 801 x 401, so 16 is kept for grids of 2 M nodes and more.
+__host__ __device__ __forceinline__ int dot_tpi(int ntiles) { return ntiles >= 8192 ? 16 : 8; }
 
 struct DotSmem {
     float4 slot[kDotStages][kGroup + 1][kDotTile];
@@ -183,7 +190,7 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
     extern __shared__ __align__(128) unsigned char pipe_raw[];
     DotSmem &S = *reinterpret_cast<DotSmem *>(pipe_raw);
     ring_init(S.full, S.empty, S.abort);
-    const int ntiles = ceil_div(N, kDotTile), nch = ceil_div(ntiles, kDotTpi);
+    const int ntiles = ceil_div(N, kDotTile), nch = ceil_div(ntiles, dot_tpi(ntiles));
     const int items = nrhs * nch;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned k = 0;
@@ -194,7 +201,7 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
             for (int it = blockIdx.x; it < items; it += gridDim.x) {
                 const int r = it / nch, c = it % nch;
                 if (active && !active[r]) continue;
-                const int t0 = c * kDotTpi, t1 = min(t0 + kDotTpi, ntiles);
+                const int t0 = c * dot_tpi(ntiles), t1 = min(t0 + dot_tpi(ntiles), ntiles);
                 const float4 *Vr = V + r * sV, *wr = w + r * sw;
                 for (int i0 = 0; i0 < nvec; i0 += kGroup) {
                     const int nq = min(kGroup, nvec - i0);
@@ -225,7 +232,7 @@ k_multidot_ds(const float4 *__restrict__ V, size_t sV, int nvec, const float4 *_
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         const int r = it / nch, c = it % nch;
         if (active && !active[r]) continue;
-        const int t0 = c * kDotTpi, t1 = min(t0 + kDotTpi, ntiles);
+        const int t0 = c * dot_tpi(ntiles), t1 = min(t0 + dot_tpi(ntiles), ntiles);
         for (int i0 = 0; i0 < nvec; i0 += kGroup) {
             const int nq = min(kGroup, nvec - i0);
             float h[16], l[16];
@@ -449,7 +456,7 @@ k_multidot_sb(const float2 *__restrict__ V, size_t sV, size_t Nv, int nvec, cons
     extern __shared__ __align__(128) unsigned char pipe_raw[];
     DotSmemSB &S = *reinterpret_cast<DotSmemSB *>(pipe_raw);
     ring_init(S.full, S.empty, S.abort);
-    const int ntiles = ceil_div(N, kDotTile), nch = ceil_div(ntiles, kDotTpi);
+    const int ntiles = ceil_div(N, kDotTile), nch = ceil_div(ntiles, dot_tpi(ntiles));
     const int items = nrhs * nch;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned k = 0;
@@ -459,7 +466,7 @@ k_multidot_sb(const float2 *__restrict__ V, size_t sV, size_t Nv, int nvec, cons
             for (int it = blockIdx.x; it < items; it += gridDim.x) {
                 const int r = it / nch, c = it % nch;
                 if (active && !active[r]) continue;
-                const int t0 = c * kDotTpi, t1 = min(t0 + kDotTpi, ntiles);
+                const int t0 = c * dot_tpi(ntiles), t1 = min(t0 + dot_tpi(ntiles), ntiles);
                 const float2 *Vr = V + r * sV;
                 const float4 *wr = w + r * sw;
                 for (int i0 = 0; i0 < nvec; i0 += kGroup) {
@@ -493,7 +500,7 @@ k_multidot_sb(const float2 *__restrict__ V, size_t sV, size_t Nv, int nvec, cons
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         const int r = it / nch, c = it % nch;
         if (active && !active[r]) continue;
-        const int t0 = c * kDotTpi, t1 = min(t0 + kDotTpi, ntiles);
+        const int t0 = c * dot_tpi(ntiles), t1 = min(t0 + dot_tpi(ntiles), ntiles);
         for (int i0 = 0; i0 < nvec; i0 += kGroup) {
             const int nq = min(kGroup, nvec - i0);
             float h[16], l[16];
@@ -823,7 +830,7 @@ cudaError_t set_consumer_wait_ns(unsigned long long ns) {
 }
 
 size_t ds_partial_per_rhs(size_t N, int nvec_max) {
-    const size_t dot = (size_t)nvec_max * ceil_div(ceil_div(N, kDotTile), kDotTpi) * kConsWarps;
+    const size_t dot = (size_t)nvec_max * ceil_div(ceil_div(N, kDotTile), dot_tpi(ceil_div(N, kDotTile))) * kConsWarps;
     const size_t axpy = ((size_t)ceil_div(N, kAxpyTile) * kConsWarps + 1) / 2;   // doubles, in double2 units
     return dot > axpy ? dot : axpy;
 }
@@ -832,7 +839,7 @@ void launch_multidot_ds(const float4 *V, size_t sV, int nvec, const float4 *w, s
                         double2 *out, size_t out_stride, int nrhs, const int *active,
                         KrylovScratch &ks, cudaStream_t st) {
     set_pipe_attrs();
-    const int nch = ceil_div(ceil_div(N, kDotTile), kDotTpi);
+    const int nch = ceil_div(ceil_div(N, kDotTile), dot_tpi(ceil_div(N, kDotTile)));
     const int nb = pipe_grid(nrhs * nch, kDotBlocksPerSM);
     prof_begin(st);
     k_multidot_ds<<<nb, kPipeThreads, sizeof(DotSmem), st>>>(V, sV, nvec, w, sw, N, ks.partial,
@@ -904,7 +911,7 @@ void launch_multidot_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const f
                         double2 *out, size_t out_stride, int nrhs, const int *active, KrylovScratch &ks,
                         cudaStream_t st) {
     set_pipe_attrs();
-    const int nch = ceil_div(ceil_div(N, kDotTile), kDotTpi);
+    const int nch = ceil_div(ceil_div(N, kDotTile), dot_tpi(ceil_div(N, kDotTile)));
     const int nb = pipe_grid(nrhs * nch, kDotBlocksPerSM);
     prof_begin(st);
     k_multidot_sb<<<nb, kPipeThreads, sizeof(DotSmemSB), st>>>(V, sV, Nv, nvec, w, sw, N, ks.partial, ks.nvec_max,
