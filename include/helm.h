@@ -418,7 +418,9 @@ typedef struct {
                              /* grid, slowness values, omega, alpha and tol join it in */
                              /* one helm_solve_batch of at most k right-hand sides     */
                              /* (each keeps its own result: a member of a lock-step    */
-                             /* batch gets the bits of its solve alone). Ignored with  */
+                             /* batch gets the bits of its solve alone, and HELM_OK    */
+                             /* when its own right-hand sides met tol, with side       */
+                             /* RIGHT, even if another member's did not). Ignored with */
                              /* options.block (a shared block space would change the   */
                              /* results).                                              */
 } helm_server_config;

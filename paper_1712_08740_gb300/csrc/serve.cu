@@ -247,9 +247,18 @@ void run_group(helm_server *S, Worker &w, std::vector<std::shared_ptr<Req>> &grp
     for (auto &q : grp) {
         q->status = s;
         q->err = err;
+        bool all_met = true;
         for (int k = 0; k < q->nrhs; ++k) {
             q->its_max = std::max(q->its_max, its[k0 + k]);
             q->rel_max = std::max(q->rel_max, rel[k0 + k]);
+            all_met = all_met && rel[k0 + k] <= q->tol;
+        }
+        // in a merged batch that did not converge as a whole, a member whose
+        // own right-hand sides all met the tolerance gets the status of its
+        // solve alone (right preconditioning stops on this true residual)
+        if (s == HELM_ERR_NOT_CONVERGED && grp.size() > 1 && all_met && S->opt.side == HELM_SIDE_RIGHT) {
+            q->status = HELM_OK;
+            q->err.clear();
         }
         k0 += q->nrhs;
         q->f.clear();

@@ -172,3 +172,41 @@ def test_coalesced_requests_match_alone(helm, precision, workers):
         j = next(j for j in range(k) if admits[j] == admits[k])
         assert k % 2 == j % 2                  # only requests of the same problem share a batch
         assert out[k][1].t_done == out[j][1].t_done
+
+
+def test_merged_member_keeps_its_own_convergence_status(helm):
+    """A merged batch in which one member's source needs more steps than
+    max_iters allows returns NOT_CONVERGED as a whole; the other member, whose
+    sources all met the tolerance, still gets HELM_OK, as it would alone."""
+    r = make_requests(1, seed=5)[0]
+    n, h = r["n"], r["h"]
+    tol = 1e-9
+    srcs = {"a": [(3, 2)], "b": [(n[0] // 2, n[1] // 2)]}
+    its = {}
+    for k, pos in srcs.items():
+        g = helm.Grid(n, h, precision="mixed_c64")
+        g.set_model(r["m"].copy(), r["omega"], r["alpha"])
+        g.set_shift(1.0, 0.5)
+        F = point_sources(n, h, pos).ravel()[None, :]
+        U = np.zeros_like(F)
+        _, it, _ = g.solve_batch(1, F, tol, U)
+        its[k] = int(it[0])
+        g.close()
+    lo, hi = sorted(its.values())
+    if lo == hi:
+        pytest.skip("both sources need the same number of steps")
+    easy = "a" if its["a"] < its["b"] else "b"
+    hard = "b" if easy == "a" else "a"
+    cap = (lo + hi) // 2
+    srv = helm.Server(workers=1, memory_budget=16 << 30, precision="mixed_c64", coalesce=64, max_iters=cap)
+    first = srv.submit(n, h, r["m"], r["omega"], r["alpha"], r["F"], tol)   # keeps the worker busy
+    ids = {k: srv.submit(n, h, r["m"], r["omega"], r["alpha"], point_sources(n, h, srcs[k]).ravel()[None, :], tol)
+           for k in (easy, hard)}
+    srv.wait(first, check=False)
+    st_e, res_e, _ = srv.wait(ids[easy], check=False)
+    st_h, res_h, _ = srv.wait(ids[hard], check=False)
+    srv.close()
+    assert st_h == 4                                  # HELM_ERR_NOT_CONVERGED
+    assert st_e == 0 and res_e.true_rel_residual_max <= tol
+    if res_e.t_admit != res_h.t_admit:
+        pytest.skip("the two requests were not merged in this run")
