@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", default="plain",
-                    choices=["plain", "batched", "3d", "block-tc", "block-ls", "batched-c64", "batched-ds"],
+                    choices=["plain", "batched", "3d", "3d-mid", "block-tc", "block-ls", "batched-c64",
+                             "batched-ds"],
                     help="region bracketed by cudaProfilerStart/Stop for ncu --profile-from-start "
                          "off: the plain timed solves, or one extra (untimed) solve of the "
                          "64-source batch with the complex64 basis; block-tc / block-ls: only "
@@ -332,12 +333,13 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def profile_3d(helm, dev, stream):
-    """--profile 3d: only the 3D workload (tiles tuned, graphs warm), one
-    batched solve bracketed by cudaProfilerStart/Stop for ncu's launch list."""
+def profile_3d(helm, dev, stream, name="3d_smooth"):
+    """--profile 3d / 3d-mid: only the 3D workload (257x257x193) or its
+    129x129x97 version (tiles tuned, graphs warm), one batched solve
+    bracketed by cudaProfilerStart/Stop for ncu."""
     import torch
     from workloads import workload
-    wx = workload("3d_smooth")
+    wx = workload(name)
     mx = torch.from_numpy(wx.slowness().ravel().copy()).to(dev)
     gx = helm.Grid(wx.n, wx.h, restart=wx.restart, precond=wx.precond, precision="mixed_c64")
     gx.set_stream(stream.cuda_stream)
@@ -355,7 +357,7 @@ def profile_3d(helm, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
-    print(json.dumps({"profile": "3d", "grid": list(wx.n), "sources": int(Fx.shape[0]),
+    print(json.dumps({"profile": name, "grid": list(wx.n), "sources": int(Fx.shape[0]),
                       "solve_ms": e0.elapsed_time(e1), "iterations_max": int(itx.max()),
                       "true_rel_residual_max": float(rrx.max())}), flush=True)
     gx.close()
@@ -442,8 +444,9 @@ def main():
     from paper_1712_08740_gb300 import helm
     from workloads import point_sources, workload
 
-    if args.profile == "3d":
-        profile_3d(helm, dev, torch.cuda.current_stream(dev))
+    if args.profile in ("3d", "3d-mid"):
+        profile_3d(helm, dev, torch.cuda.current_stream(dev),
+                   "3d_smooth" if args.profile == "3d" else "3d_smooth_mid")
         return
     if args.profile in ("block-tc", "block-ls"):
         profile_block(helm, dev, args.profile)

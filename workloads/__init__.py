@@ -177,6 +177,13 @@ def workload(name: str) -> Workload:
         return Workload(name, (257, 257, 193), 10.0, (10.0,), 0.01, (1.0, 0.5), 20, 1e-8,
                         "mg", "mixed", [(64, 64, 2), (192, 64, 2), (64, 192, 2), (192, 192, 2)],
                         "smooth")
+    if name == "3d_smooth_mid":
+        # the 3D medium and frequency on 129 x 129 x 97 nodes (same h and points per
+        # wavelength): about 2.5 GB on the device for a 4-source batch, a size for
+        # full-counter profiles
+        return Workload(name, (129, 129, 97), 10.0, (10.0,), 0.01, (1.0, 0.5), 20, 1e-8,
+                        "mg", "mixed", [(32, 32, 2), (96, 32, 2), (32, 96, 2), (96, 96, 2)],
+                        "smooth")
     if name == "3d_smooth_small":
         return Workload(name, (33, 33, 25), 10.0, (10.0,), 0.01, (1.0, 0.5), 20, 1e-8,
                         "mg", "mixed", [(16, 16, 2)], "smooth")
