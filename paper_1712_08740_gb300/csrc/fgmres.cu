@@ -66,6 +66,7 @@ helm_status ensure_workspace(helm_grid *g, int nrhs) {
         ((s = g->rbuf.ensure(R * N * sizeof(double2))) ||
                                        (s = g->hdiag.ensure(N * sizeof(float4)))))
         return s;
+    if (prec == HELM_PREC_MIXED_C64 && (s = g->c64sc.ensure(R * sizeof(float2)))) return s;
     if (left_side(g) && ((s = g->rbuf.ensure(R * N * sizeof(double2))) ||
                          (s = g->tnrm.ensure(2 * R * sizeof(double)))))
         return s;
@@ -142,8 +143,10 @@ KrylovScratch scratch(helm_grid *g) {
     return ks;
 }
 
-// z_j = M^-1 v_j for all flagged right-hand sides
-void apply_precond_j(helm_grid *g, int j, int nrhs, const int *act) {
+// z_j = M^-1 v_j for all flagged right-hand sides. from_w (complex64 basis,
+// j >= 1): v_j is not formed yet; the V-cycle's level-0 kernel forms it from
+// the previous step's w and scale and stores it in basis slot j.
+void apply_precond_j(helm_grid *g, int j, int nrhs, const int *act, bool from_w = false) {
     const size_t N = g->N;
     const int m = g->opt.restart;
     const size_t sV = (size_t)(m + 1) * N, sZ = (size_t)m * N;
@@ -152,6 +155,10 @@ void apply_precond_j(helm_grid *g, int j, int nrhs, const int *act) {
         vcycle<double, double2>(g, vj, sV, g->Z.as<double2>() + (size_t)j * N, sZ, nrhs, act);
     else if (g->opt.precision == HELM_PREC_MIXED)
         vcycle<float, double2>(g, vj, sV, g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act);
+    else if (g->opt.precision == HELM_PREC_MIXED_C64 && from_w && j > 0)
+        vcycle<float, float2>(g, g->V.as<float2>() + (size_t)j * c64_stride(N), (size_t)(m + 1) * c64_stride(N),
+                              g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act, g->rbuf.as<float4>(), N,
+                              g->c64sc.as<float2>(), g->nrm.as<double>());
     else if (g->opt.precision == HELM_PREC_MIXED_C64)
         vcycle<float, float2>(g, g->V.as<float2>() + (size_t)j * c64_stride(N), (size_t)(m + 1) * c64_stride(N),
                               g->Z.as<float2>() + (size_t)j * N, sZ, nrhs, act);
@@ -248,11 +255,14 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
     double *nrm = g->nrm.as<double>();
     const int *act = g->act_it.as<int>();
     const bool left = left_side(g);
+    const bool c64 = g->opt.precision == HELM_PREC_MIXED_C64;
     if (g->opt.precond != HELM_PRECOND_NONE && !(left && g->opt.side == HELM_SIDE_LEFT))
-        apply_precond_j(g, j, nrhs, act);
-    if (g->opt.precision == HELM_PREC_MIXED_C64) {
+        apply_precond_j(g, j, nrhs, act, c64);
+    if (c64) {
         // w = H z_j (double-single, in the residual buffer), orthogonalised
-        // against the complex64 basis, then v_{j+1} = w / ||w|| rounded
+        // against the complex64 basis; v_{j+1} = w / ||w|| rounded is formed
+        // by the next step's level-0 V-cycle kernel from w and the scale pair
+        // that the norm's finalize kernel leaves
         float2 *Vc = g->V.as<float2>();
         float4 *wd = g->rbuf.as<float4>();
         const size_t Nv = c64_stride(N), sVc = (size_t)nv * Nv;
@@ -260,8 +270,7 @@ void arnoldi_step(helm_grid *g, int j, int nrhs, double tol) {
         launch_apply_H_ds(Lv, g->hdiag.as<float4>(), g->Z.as<float2>() + (size_t)j * N, (size_t)m * N, wd, N,
                           nrhs, act, st);
         launch_multidot_sb(Vc, sVc, Nv, j + 1, wd, N, N, hb, 2 * nv, nrhs, act, ks, st);
-        launch_multiaxpy_sb(Vc, sVc, Nv, j + 1, hb, 2 * nv, wd, N, N, nrm, nrhs, act, ks, st);
-        launch_scale_c64(wd, N, nrm, Vc + (size_t)(j + 1) * Nv, sVc, N, nrhs, act, st);
+        launch_multiaxpy_sb(Vc, sVc, Nv, j + 1, hb, 2 * nv, wd, N, N, nrm, nrhs, act, ks, st, g->c64sc.as<float2>());
         launch_givens_scale<double2>(cycle_state(g), j, hb, 2 * nv, 0, nrm, nrhs, tol, g->opt.max_iters, g->hflag,
                                      (double2 *)nullptr, sV, N, st);
         return;
@@ -347,7 +356,7 @@ long long graph_key_of(const helm_grid *g, int nrhs, double tol) {
     mixp(g->act_it.p); mixp(g->act_cy.p); mixp(g->act2.p); mixp(g->Ainv.p); mixp(g->hflag);
     mixp(g->cpart.p); mixp(g->cticket.p);
     mixp(g->cR.p); mixp(g->cg.p); mixp(g->ccs.p); mixp(g->csn.p); mixp(g->cQ.p); mixp(g->cfn.p);
-    mixp(g->ck.p); mixp(g->cits.p); mixp(g->cstat.p); mixp(g->cany.p); mixp(g->hdiag.p); mixp(g->Atc.p); mixp(g->rbuf.p);
+    mixp(g->ck.p); mixp(g->cits.p); mixp(g->cstat.p); mixp(g->cany.p); mixp(g->hdiag.p); mixp(g->Atc.p); mixp(g->rbuf.p); mixp(g->c64sc.p);
     for (const auto &L : g->lv) {
         mixp(L.w64.p); mixp(L.w32.p); mixp(L.dinv.p); mixp(L.u.p); mixp(L.t.p); mixp(L.b.p); mixp(L.r.p);
         mixu((unsigned long long)L.N);

@@ -71,6 +71,7 @@ struct helm_grid {
                                         // before M^-1 (left and two-sided preconditioning)
     helm::DevBuf tnrm;                  // true-residual norms of the left/two-sided sides
     helm::DevBuf hdiag;                 // diagonal of H as double-single pairs
+    helm::DevBuf c64sc;                 // complex64 basis: 1/||w|| per right-hand side, float hi + lo
     bool hdiag_ok = false;              // hdiag matches the current model
     int *hflag = nullptr;               // host-mapped "any right-hand side active" flag
     std::vector<cudaEvent_t> ring;      // look-ahead events of the Arnoldi loop

@@ -355,12 +355,22 @@ inline size_t c64_stride(size_t N) { return (N + 1) & ~(size_t)1; }
 void launch_multidot_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const float4 *w, size_t sw, size_t N,
                         double2 *out, size_t out_stride, int nrhs, const int *active, KrylovScratch &ks,
                         cudaStream_t st);
+// scale (nullable, with norm2): per right-hand side 1/sqrt(norm2) as float hi + lo
 void launch_multiaxpy_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const double2 *c, size_t c_stride,
                          float4 *w, size_t sw, size_t N, double *norm2, int nrhs, const int *active,
-                         KrylovScratch &ks, cudaStream_t st);
+                         KrylovScratch &ks, cudaStream_t st, float2 *scale = nullptr);
 // v = w / sqrt(norm2[k]) rounded to complex64
 void launch_scale_c64(const float4 *w, size_t sw, const double *norm2, float2 *v, size_t sv, size_t N, int nrhs,
                       const int *active, cudaStream_t st);
+// The level-0 down kernel of the complex64-basis form that takes w (double-
+// single) and the scale pair sc of launch_multiaxpy_sb instead of v: it forms
+// v = w * (sc.x + sc.y) rounded to complex64 with the arithmetic of
+// launch_scale_c64, writes v of its own nodes to vout (stride svout), and
+// goes on as launch_vdown. 2D levels only: returns false, launching nothing,
+// for a 3D level (the caller then scales w on its own first).
+bool launch_vdown_c64w(const LevelView<float> &F, const LevelView<float> &Cv, float wj, const float4 *w,
+                       size_t sw, const float2 *sc, float2 *vout, size_t svout, float2 *u, size_t su, float2 *bc,
+                       size_t sbc, int nb, const int *active, cudaStream_t st, int shape);
 
 // diagonal of H on the fine grid as double-single pairs, and w = H z in
 // double-single arithmetic (z complex64, w double-single)

@@ -1,7 +1,10 @@
 // The scaling step of the complex64-basis form (precision
 // HELM_PREC_MIXED_C64): v_{j+1} = w / ||w|| from the double-single w,
-// rounded once to complex64. The streamed multi-dot and multi-axpy of that
-// form sit beside their double-single counterparts in krylov_ds.cu.
+// rounded once to complex64. On 2D grids the next step's level-0 down kernel
+// forms v_{j+1} itself with the same arithmetic (launch_vdown_c64w); this
+// kernel serves 3D grids and the V-cycles that cannot take w. The streamed
+// multi-dot and multi-axpy of that form sit beside their double-single
+// counterparts in krylov_ds.cu.
 #include "helm_internal.cuh"
 
 namespace helm {

@@ -660,10 +660,13 @@ k_multiaxpy_sb(const float2 *__restrict__ V, size_t sV, size_t Nv, int nvec, con
     __syncthreads();
 }
 
-// norm2[r] = sum of the n partials of r (fixed order, as k_dot_finalize)
+// norm2[r] = sum of the n partials of r (fixed order, as k_dot_finalize);
+// with sc, also the scale 1/sqrt(norm2[r]) split into float hi + lo parts
+// (the complex64 basis's v = w / ||w||, formed by the next level-0 V-cycle
+// kernel)
 __global__ void __launch_bounds__(256)
 k_norm_finalize(const double *__restrict__ partial_d, int n, double *__restrict__ norm2,
-                const int *__restrict__ active) {
+                float2 *__restrict__ sc, const int *__restrict__ active) {
     const int r = blockIdx.x;
     if (active && !active[r]) return;
     const double *p = partial_d + (size_t)r * n;
@@ -677,6 +680,11 @@ k_norm_finalize(const double *__restrict__ partial_d, int n, double *__restrict_
         double a = red[0];
         for (int q = 1; q < 8; ++q) a += red[q];
         norm2[r] = a;
+        if (sc) {
+            const double t = 1.0 / sqrt(a);
+            const float th = (float)t;
+            sc[r] = make_float2(th, (float)(t - (double)th));
+        }
     }
 }
 
@@ -863,7 +871,7 @@ void launch_multiaxpy_ds(const float4 *V, size_t sV, int nvec, const double2 *c,
         V, sV, nvec, c, c_stride, w, sw, N, pd, nrhs, active);
     count_launch();
     if (norm2) {
-        k_norm_finalize<<<nrhs, 256, 0, st>>>(pd, ntiles * kConsWarps, norm2, active);
+        k_norm_finalize<<<nrhs, 256, 0, st>>>(pd, ntiles * kConsWarps, norm2, nullptr, active);
         count_launch();
     }
     if (prof_on())
@@ -924,7 +932,7 @@ void launch_multidot_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const f
 
 void launch_multiaxpy_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const double2 *c, size_t c_stride,
                          float4 *w, size_t sw, size_t N, double *norm2, int nrhs, const int *active,
-                         KrylovScratch &ks, cudaStream_t st) {
+                         KrylovScratch &ks, cudaStream_t st, float2 *scale) {
     set_pipe_attrs();
     const int ntiles = ceil_div(N, kAxpyTile);
     const int nb = pipe_grid(nrhs * ntiles, kAxpyBlocksPerSM);
@@ -934,7 +942,7 @@ void launch_multiaxpy_sb(const float2 *V, size_t sV, size_t Nv, int nvec, const 
         V, sV, Nv, nvec, c, c_stride, w, sw, N, pd, nrhs, active);
     count_launch();
     if (norm2) {
-        k_norm_finalize<<<nrhs, 256, 0, st>>>(pd, ntiles * kConsWarps, norm2, active);
+        k_norm_finalize<<<nrhs, 256, 0, st>>>(pd, ntiles * kConsWarps, norm2, scale, active);
         count_launch();
     }
     if (prof_on()) prof_end("multiaxpy_c64", st, (nvec * 8.0 + 32.0) * N * nrhs, 0.0);

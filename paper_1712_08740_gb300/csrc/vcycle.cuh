@@ -100,10 +100,17 @@ inline void coarse_product(helm_grid *g, const cplx_t<T> *r, size_t sr, cplx_t<T
                              g->cticket.template as<unsigned>(), st);
 }
 
+// With w0 (complex64 basis only: T = float, CB0 = float2) the level-0
+// right-hand side is not yet in b0: it is v = w0 / ||w0|| rounded to
+// complex64 (sc0: the scale as float hi + lo, nrm0: ||w0||^2), which the
+// level-0 down kernel forms as it loads w0 and writes to b0 (a basis slot);
+// kernels that cannot take w0 get v from launch_scale_c64 first.
 template <typename T, typename CB0>
 void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, int nb,
-            const int *act) {
+            const int *act, const float4 *w0 = nullptr, size_t sw0 = 0, const float2 *sc0 = nullptr,
+            const double *nrm0 = nullptr) {
     using C = cplx_t<T>;
+    constexpr bool kC64 = std::is_same<T, float>::value && std::is_same<CB0, float2>::value;
     const int L = (int)g->lv.size();
     const OpShift<T> sM = shift_M<T>(g);
     const T wj = (T)g->opt.omega_jacobi;
@@ -111,15 +118,33 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
     cudaStream_t st = g->st;
     // the fused level kernels carry the constant-density stencil only
     const bool fused = L > 1 && g->dim >= 2 && nu1 == 1 && nu2 == 1 && !g->has_rho;
+    bool v_done = w0 == nullptr;
+    auto make_v = [&] {
+        if constexpr (kC64) {
+            if (!v_done) launch_scale_c64(w0, sw0, nrm0, const_cast<float2 *>(b0), sb0, g->lv[0].N, nb, act, st);
+        }
+        v_done = true;
+    };
     if (fused) {
         // down: u_l (pre-smoothed, into the level's scratch) and b_{l+1}
         for (int l = 0; l < L - 1; ++l) {
             const LevelView<T> F = level_view<T>(g, l), Cv = level_view<T>(g, l + 1);
             C *bc = g->lv[l + 1].b.template as<C>();
-            if (l == 0)
+            if (l == 0) {
+                if constexpr (kC64) {
+                    if (!v_done) {
+                        if (launch_vdown_c64w(F, Cv, wj, w0, sw0, sc0, const_cast<float2 *>(b0), sb0,
+                                              g->lv[0].t.template as<C>(), g->lv[0].N, bc, g->lv[1].N, nb, act, st,
+                                              tile_down(g, 0, nb))) {
+                            v_done = true;
+                            continue;
+                        }
+                        make_v();
+                    }
+                }
                 launch_vdown<T, CB0>(F, Cv, wj, b0, sb0, g->lv[0].t.template as<C>(), g->lv[0].N,
                                      bc, g->lv[1].N, nb, act, st, tile_down(g, 0, nb), true);
-            else
+            } else
                 launch_vdown<T, C>(F, Cv, wj, g->lv[l].b.template as<C>(), g->lv[l].N,
                                    g->lv[l].t.template as<C>(), g->lv[l].N, bc, g->lv[l + 1].N, nb,
                                    act, st, tile_down(g, l, nb));
@@ -142,6 +167,7 @@ void vcycle(helm_grid *g, const CB0 *b0, size_t sb0, cplx_t<T> *u0, size_t su0, 
         return;
     }
     // general path: level-0 right-hand side in the V-cycle's own type
+    make_v();
     const C *b0c;
     size_t sb0c;
     if constexpr (std::is_same<CB0, C>::value) {

@@ -36,6 +36,7 @@
 #include "helm_internal.cuh"
 
 #include <tuple>
+#include <type_traits>
 #include <utility>
 
 namespace helm {
@@ -185,13 +186,24 @@ __device__ __forceinline__ void shell_pos(int h, int &lx, int &ly, int &lz) {
 // INT: the block's whole box lies strictly inside the level, so no node of it
 // needs a boundary test, a doubled neighbour or a mirrored restriction point
 // (the same arithmetic as the general body on those nodes).
-template <typename T, typename CB, int DIM, typename TL, bool INT>
+// SC (complex64 basis, level 0): b is the double-single w of the Arnoldi
+// step (CB = float4) and sc the per-right-hand-side scale 1/||w|| as float
+// hi + lo; the kernel uses v = w (sc.x + sc.y) rounded to complex64 (the
+// arithmetic of k_scale_c64) and writes v of its own nodes to vout.
+__device__ __forceinline__ float2 scaled_c64(float4 x, float2 s) {
+    return make_float2(fmaf(x.x, s.x, fmaf(x.x, s.y, x.y * s.x)), fmaf(x.z, s.x, fmaf(x.z, s.y, x.w * s.x)));
+}
+
+template <typename T, typename CB, int DIM, typename TL, bool INT, bool SC = false>
 __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView<T> &Cv, T wj,
                                           const CB *__restrict__ b, size_t sb,
                                           cplx_t<T> *__restrict__ u, size_t su,
                                           cplx_t<T> *__restrict__ bc, size_t sbc, int nb,
-                                          const int *__restrict__ active) {
+                                          const int *__restrict__ active, const float2 *__restrict__ sc = nullptr,
+                                          float2 *__restrict__ vout = nullptr, size_t svout = 0) {
     using C = cplx_t<T>;
+    static_assert(!SC || (std::is_same<CB, float4>::value && std::is_same<C, float2>::value),
+                  "the scaled input is the double-single w of the complex64 basis");
     constexpr int SX = TL::SX, SY = TL::SY, SZ = DIM == 3 ? TL::SZ : 1;
     // local box of u: fine [2 I0 - 2, 2 I0 + 2 SX] per axis; own children at [2, U - 1)
     constexpr int UX = 2 * SX + 3, UY = 2 * SY + 3, UZ = DIM == 3 ? 2 * SZ + 3 : 1;
@@ -216,6 +228,17 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
     b += r0 * sb;
     u += r0 * su;
     bc += r0 * sbc;
+    float2 scr[RB];
+    if constexpr (SC) {
+        vout += r0 * svout;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) scr[r] = on[r] ? sc[r0 + r] : make_float2(0.f, 0.f);
+    }
+    // the right-hand side value of right-hand side r in the level's type
+    auto cv = [&](int r, CB braw) -> C {
+        if constexpr (SC) return scaled_c64(braw, scr[r]);
+        else return cvt<C>(braw);
+    };
     const int I0 = blockIdx.x * SX, J0 = blockIdx.y * SY, K0 = bz * SZ;
     const int X0 = 2 * I0 - 2, Y0 = 2 * J0 - 2, Z0 = DIM == 3 ? 2 * K0 - 2 : 0;
     constexpr int QP = TL::QP;
@@ -273,7 +296,7 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
     // u = wj D^-1 b (first Jacobi sweep from zero) on the whole box; b goes to
     // shared memory only for the halo (own children keep it in registers)
     auto put_u = [&](int r, int t, CB braw, C di, bool keep_b) {
-        const C bp = cvt<C>(braw);
+        const C bp = cv(r, braw);
         C up;
         up.x = wj * fmaT(di.x, bp.x, -(di.y * bp.y));
         up.y = wj * fmaT(di.x, bp.y, di.y * bp.x);
@@ -305,6 +328,7 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
                 if (on[r]) {
                     const C up = put_u(r, t, bq[r][k], dq[k], false);
                     u[r * su + pq[k]] = up;
+                    if constexpr (SC) vout[r * svout + pq[k]] = cv(r, bq[r][k]);
                     if constexpr (RREG) uo[r][k] = up;
                 }
         }
@@ -368,7 +392,7 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
                 sx = fmaT(T(1), ev.x, sx); sy = fmaT(T(1), ev.y, sy);
                 sx = fmaT(T(1), sv.x, sx); sy = fmaT(T(1), sv.y, sy);
                 sx = fmaT(T(1), nv.x, sx); sy = fmaT(T(1), nv.y, sy);
-                const C bp = cvt<C>(bq[r][k]);
+                const C bp = cv(r, bq[r][k]);
                 const T omw = T(1) - wj;
                 C o;
                 o.x = fmaT(F.inv_h2, sx, omw * bp.x);
@@ -376,7 +400,7 @@ __device__ __forceinline__ void down_tile(const LevelView<T> &F, const LevelView
                 sr_[r * BOX + t] = o;
                 ro[r][k] = o;
             } else if (iq[k]) {
-                put_r(r, x - X0, y - Y0, z - Z0, cvt<C>(bq[r][k]));
+                put_r(r, x - X0, y - Y0, z - Z0, cv(r, bq[r][k]));
             }
         }
     }
@@ -632,11 +656,11 @@ __device__ __forceinline__ void up_tile(const LevelView<T> &F, const LevelView<T
     }
 }
 
-template <typename T, typename CB, int DIM, typename TL>
+template <typename T, typename CB, int DIM, typename TL, bool SC = false>
 __global__ void __launch_bounds__(TL::NT)
 k_down(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t sb,
        cplx_t<T> *__restrict__ u, size_t su, cplx_t<T> *__restrict__ bc, size_t sbc, int nb,
-       const int *__restrict__ active) {
+       const int *__restrict__ active, const float2 *__restrict__ sc, float2 *__restrict__ vout, size_t svout) {
     // the box of u spans fine [2 I0 - 2, 2 I0 + 2 S] per axis
     const int gz = DIM == 3 ? (Cv.nz + TL::SZ - 1) / TL::SZ : 1;
     const int bz = blockIdx.z % gz;
@@ -645,8 +669,10 @@ k_down(LevelView<T> F, LevelView<T> Cv, T wj, const CB *__restrict__ b, size_t s
     const bool inside = x0 >= 0 && x0 + 2 * TL::SX + 2 <= F.nx - 1 && y0 >= 0 &&
                         y0 + 2 * TL::SY + 2 <= F.ny - 1 &&
                         (DIM != 3 || (z0 >= 0 && z0 + 2 * TL::SZ + 2 <= F.nz - 1));
-    if (inside) down_tile<T, CB, DIM, TL, true>(F, Cv, wj, b, sb, u, su, bc, sbc, nb, active);
-    else down_tile<T, CB, DIM, TL, false>(F, Cv, wj, b, sb, u, su, bc, sbc, nb, active);
+    if (inside)
+        down_tile<T, CB, DIM, TL, true, SC>(F, Cv, wj, b, sb, u, su, bc, sbc, nb, active, sc, vout, svout);
+    else
+        down_tile<T, CB, DIM, TL, false, SC>(F, Cv, wj, b, sb, u, su, bc, sbc, nb, active, sc, vout, svout);
 }
 
 template <typename T, typename CB, int DIM, typename TL>
@@ -902,7 +928,7 @@ void down_impl(const LevelView<T> &F, const LevelView<T> &Cv, T wj, const CB *b,
                                                         bc + r0 * sbc, sbc, act);
         } else {
             k_down<T, CB, DIM, TL><<<g, TL::NT, sm, st>>>(F, Cv, wj, b + r0 * sb, sb, u + r0 * su,
-                                                          su, bc + r0 * sbc, sbc, n, act);
+                                                          su, bc + r0 * sbc, sbc, n, act, nullptr, nullptr, 0);
         }
         count_launch();
     }
@@ -937,6 +963,44 @@ void down_sel(int shape, std::index_sequence<I...>, const LevelView<T> &F, const
           : void()),
      ...);
 }
+// the level-0 down kernel of the complex64 basis taking w and the scale pair
+// (the z-marching 3D kernel cannot take w)
+template <int DIM, typename TL>
+bool down_c64w_impl(const LevelView<float> &F, const LevelView<float> &Cv, float wj, const float4 *w, size_t sw,
+                    const float2 *sc, float2 *vout, size_t svout, float2 *u, size_t su, float2 *bc, size_t sbc,
+                    int nb, const int *active, cudaStream_t st) {
+    if constexpr (TL::MARCH) {
+        return false;
+    } else {
+        const size_t sm = down_smem<DIM, TL>(sizeof(float2));
+        const int gz = DIM == 3 ? (Cv.nz + TL::SZ - 1) / TL::SZ : 1;
+        const int chunk = rhs_per_launch(gz, TL::RB, nb);
+        for (int r0 = 0; r0 < nb; r0 += chunk) {
+            const int n = nb - r0 < chunk ? nb - r0 : chunk;
+            dim3 g((Cv.nx + TL::SX - 1) / TL::SX, (Cv.ny + TL::SY - 1) / TL::SY,
+                   gz * ((n + TL::RB - 1) / TL::RB));
+            k_down<float, float4, DIM, TL, true><<<g, TL::NT, sm, st>>>(
+                F, Cv, wj, w + r0 * sw, sw, u + r0 * su, su, bc + r0 * sbc, sbc, n, active ? active + r0 : nullptr,
+                sc + r0, vout + r0 * svout, svout);
+            count_launch();
+        }
+        return true;
+    }
+}
+
+template <int DIM, size_t... I>
+bool down_c64w_sel(int shape, std::index_sequence<I...>, const LevelView<float> &F, const LevelView<float> &Cv,
+                   float wj, const float4 *w, size_t sw, const float2 *sc, float2 *vout, size_t svout, float2 *u,
+                   size_t su, float2 *bc, size_t sbc, int nb, const int *active, cudaStream_t st) {
+    bool ok = false;
+    ((shape == (int)I
+          ? (void)(ok = down_c64w_impl<DIM, std::tuple_element_t<I, typename Shapes<DIM>::Down>>(
+                       F, Cv, wj, w, sw, sc, vout, svout, u, su, bc, sbc, nb, active, st))
+          : void()),
+     ...);
+    return ok;
+}
+
 template <typename T, typename CB, int DIM, size_t... I>
 void up_sel(int shape, std::index_sequence<I...>, const LevelView<T> &F, const LevelView<T> &Cv,
             T wj, const cplx_t<T> *uin, size_t sin, const cplx_t<T> *ec, size_t sec, const CB *b,
@@ -946,6 +1010,16 @@ void up_sel(int shape, std::index_sequence<I...>, const LevelView<T> &F, const L
                 F, Cv, wj, uin, sin, ec, sec, b, sb, uout, sout, nb, active, st)
           : void()),
      ...);
+}
+
+template <int DIM, typename TL> void set_attr_down_c64w() {
+    if constexpr (!TL::MARCH)
+        cudaFuncSetAttribute(k_down<float, float4, DIM, TL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)down_smem<DIM, TL>(sizeof(float2)));
+}
+
+template <int DIM, size_t... I> void set_attr_all_c64w(std::index_sequence<I...>) {
+    (set_attr_down_c64w<DIM, std::tuple_element_t<I, typename Shapes<DIM>::Down>>(), ...);
 }
 
 template <typename T, typename CB, int DIM, typename TL> void set_attr_down() {
